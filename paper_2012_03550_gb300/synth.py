@@ -1,0 +1,335 @@
+"""Seeded synthetic inputs for SGD_Tucker workloads.
+
+This module only manufactures inputs: sparse coordinates, their values, the
+train/test split and initial parameter values.  It holds none of the SGD_Tucker
+update arithmetic, imports nothing else from this package, and is the single
+source of inputs for both the CUDA path and the FP64 oracle, so the two always
+see bit-identical arrays.
+
+The paper's datasets (MovieLens, Netflix, Yahoo-music; Sec. 5.1, Table 3) are
+not available, so seeded stand-ins with the same shapes are drawn here:
+
+* mode indices are uniform or Zipf(s) distributed (rank r in [1, I] with
+  probability proportional to r**-s, drawn by inverse CDF over an FP64 table,
+  rank r mapped to index r-1);
+* coordinates are distinct: duplicates are rejected and redrawn in draw order
+  (vectorised, equivalent to sequential rejection);
+* values come from a planted dense Tucker model (Def. 6) with core and factors
+  i.i.d. N(0,1)/sqrt(J), plus Gaussian noise; the rating-like workload maps
+  them affinely to mean 3 and rounds half-to-even into {1..5} (Table 3 range).
+
+All randomness comes from numpy's PCG64 seeded through SeedSequence, one
+independent child stream per purpose, so every array is reproducible on any
+machine from (seed, purpose).
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+from typing import List, Optional, Sequence
+
+import numpy as np
+
+# Purposes of the child streams spawned from the data seed.
+_STREAM_COORDS = 0
+_STREAM_MODEL = 1
+_STREAM_NOISE = 2
+_STREAM_SPLIT = 3
+
+
+@dataclasses.dataclass
+class SparseTensor:
+    """A sparse N-order tensor in COO form with a train/test split.
+
+    coords: int32 [nnz, N], 0-based; values: float32 [nnz].
+    train / test: int64 index arrays into coords (ascending).
+    """
+
+    shape: tuple
+    coords: np.ndarray
+    values: np.ndarray
+    train: np.ndarray
+    test: np.ndarray
+    meta: dict
+
+    @property
+    def order(self) -> int:
+        return len(self.shape)
+
+    def split(self, which: str):
+        idx = self.train if which == "train" else self.test
+        return (np.ascontiguousarray(self.coords[idx]),
+                np.ascontiguousarray(self.values[idx]))
+
+
+def _children(seed: int, n: int = 4):
+    return np.random.SeedSequence(seed).spawn(n)
+
+
+def zipf_table(size: int, s: float) -> np.ndarray:
+    """FP64 cumulative table of p(r) ~ r**-s over ranks 1..size."""
+    w = np.arange(1, size + 1, dtype=np.float64) ** (-float(s))
+    c = np.cumsum(w)
+    c /= c[-1]
+    c[-1] = 1.0
+    return c
+
+
+def draw_mode_indices(rng: np.random.Generator, count: int, size: int,
+                      dist: str = "uniform", s: float = 0.0,
+                      table: Optional[np.ndarray] = None) -> np.ndarray:
+    """Draw `count` indices in [0, size) uniformly or Zipf(s) by inverse CDF."""
+    if dist == "uniform":
+        return rng.integers(0, size, size=count, dtype=np.int64)
+    if dist == "zipf":
+        if table is None:
+            table = zipf_table(size, s)
+        u = rng.random(count)
+        r = np.searchsorted(table, u, side="right")
+        return np.minimum(r, size - 1).astype(np.int64)
+    raise ValueError(f"unknown distribution {dist!r}")
+
+
+def distinct_coords(rng: np.random.Generator, shape: Sequence[int], nnz: int,
+                    dists: Sequence[tuple]) -> np.ndarray:
+    """Draw `nnz` distinct coordinates; duplicates are rejected in draw order.
+
+    dists[n] is ("uniform",) or ("zipf", s).  Returns int32 [nnz, N].
+    """
+    N = len(shape)
+    cells = 1
+    for d in shape:
+        cells *= int(d)
+    if nnz > cells:
+        raise ValueError("more nonzeros than cells")
+    tables = [zipf_table(int(shape[n]), dists[n][1]) if dists[n][0] == "zipf" else None
+              for n in range(N)]
+    strides = np.ones(N, dtype=np.int64)
+    for n in range(1, N):
+        strides[n] = strides[n - 1] * int(shape[n - 1])
+    accepted_keys = np.empty(0, dtype=np.int64)      # sorted, for membership
+    out_chunks: List[np.ndarray] = []
+    have = 0
+    rounds = 0
+    while have < nnz:
+        need = nnz - have
+        draw = int(need * 1.2) + 1024
+        cols = [draw_mode_indices(rng, draw, int(shape[n]), dists[n][0],
+                                  dists[n][1] if len(dists[n]) > 1 else 0.0, tables[n])
+                for n in range(N)]
+        keys = np.zeros(draw, dtype=np.int64)
+        for n in range(N):
+            keys += cols[n] * strides[n]
+        _, first = np.unique(keys, return_index=True)
+        first.sort()                                  # keep draw order
+        k = keys[first]
+        if accepted_keys.size:
+            pos = np.searchsorted(accepted_keys, k)
+            pos = np.minimum(pos, accepted_keys.size - 1)
+            fresh = accepted_keys[pos] != k
+            first = first[fresh]
+            k = k[fresh]
+        first = first[:need]
+        k = k[:need]
+        chunk = np.stack([cols[n][first] for n in range(N)], axis=1).astype(np.int32)
+        out_chunks.append(chunk)
+        accepted_keys = np.union1d(accepted_keys, k)
+        have += chunk.shape[0]
+        rounds += 1
+        if rounds > 200:
+            raise RuntimeError("coordinate rejection did not converge")
+    return np.concatenate(out_chunks, axis=0)
+
+
+def planted_tucker(rng: np.random.Generator, shape: Sequence[int], ranks: Sequence[int]):
+    """Dense core G (J_1 x ... x J_N, numpy C order [j1, j2, ...]) and factors
+    A_n (I_n x J_n), all i.i.d. N(0,1)/sqrt(J) with J = J_n (core: mean rank)."""
+    N = len(shape)
+    jbar = float(np.mean(ranks))
+    core = rng.standard_normal(tuple(int(j) for j in ranks)) / math.sqrt(jbar)
+    factors = [rng.standard_normal((int(shape[n]), int(ranks[n]))) / math.sqrt(float(ranks[n]))
+               for n in range(N)]
+    return core, factors
+
+
+def planted_values(core: np.ndarray, factors: Sequence[np.ndarray], coords: np.ndarray,
+                   chunk: int = 1 << 20) -> np.ndarray:
+    """Evaluate the planted dense Tucker model at `coords` in FP64 (numpy
+    contractions, chunked): sum over j of core[j] * prod_n factors[n][i_n, j_n]."""
+    N = coords.shape[1]
+    out = np.empty(coords.shape[0], dtype=np.float64)
+    J0 = core.shape[0]
+    core0 = core.reshape(J0, -1)
+    for lo in range(0, coords.shape[0], chunk):
+        hi = min(lo + chunk, coords.shape[0])
+        c = coords[lo:hi]
+        t = factors[0][c[:, 0]] @ core0                 # [m, J2*...*JN]
+        t = t.reshape((hi - lo,) + core.shape[1:])
+        for n in range(1, N):
+            a = factors[n][c[:, n]]                     # [m, Jn]
+            t = np.einsum("sj...,sj->s...", t, a)
+        out[lo:hi] = t
+    return out
+
+
+def split_indices(rng: np.random.Generator, nnz: int, test_frac: float):
+    n_test = int(round(test_frac * nnz))
+    perm = rng.permutation(nnz)
+    test = np.sort(perm[:n_test])
+    train = np.sort(perm[n_test:])
+    return train.astype(np.int64), test.astype(np.int64)
+
+
+def make_tensor(shape, nnz, dists, ranks, noise_sd, test_frac, seed=0,
+                rating=False) -> SparseTensor:
+    """Generic planted-Tucker sparse tensor.
+
+    rating=True: y = 3 + z/sd(z) + N(0, noise_sd^2), rounded half-to-even
+    and clamped into {1..5}; otherwise y = z + N(0, noise_sd^2).
+    """
+    ch = _children(seed)
+    rc = np.random.Generator(np.random.PCG64(ch[_STREAM_COORDS]))
+    rm = np.random.Generator(np.random.PCG64(ch[_STREAM_MODEL]))
+    rn = np.random.Generator(np.random.PCG64(ch[_STREAM_NOISE]))
+    rs = np.random.Generator(np.random.PCG64(ch[_STREAM_SPLIT]))
+    coords = distinct_coords(rc, shape, nnz, dists)
+    core, factors = planted_tucker(rm, shape, ranks)
+    z = planted_values(core, factors, coords)
+    if rating:
+        sd = float(np.std(z))
+        y = 3.0 + z / (sd if sd > 0 else 1.0) + noise_sd * rn.standard_normal(z.shape[0])
+        y = np.clip(np.rint(y), 1.0, 5.0)
+    else:
+        y = z + noise_sd * rn.standard_normal(z.shape[0])
+    train, test = split_indices(rs, coords.shape[0], test_frac)
+    meta = dict(shape=tuple(int(s) for s in shape), nnz=int(nnz), dists=[tuple(d) for d in dists],
+                ranks=tuple(int(j) for j in ranks), noise_sd=float(noise_sd), rating=bool(rating),
+                seed=int(seed), test_frac=float(test_frac))
+    return SparseTensor(tuple(int(s) for s in shape), coords, y.astype(np.float32), train, test, meta)
+
+
+# ---------------------------------------------------------------------------
+# The named workloads (shapes from Table 3 of the paper; planted models as the
+# workload definitions state).  `scale` < 1 shrinks nnz and mode sizes together
+# (same distributions) for oracle-sized parity runs.
+# ---------------------------------------------------------------------------
+
+@dataclasses.dataclass
+class Workload:
+    name: str
+    tensor: SparseTensor
+    ranks: tuple
+    r_core: int
+    minibatch: int
+    lr: float
+    lam: float
+    epochs: int
+
+
+def _scaled(v, scale, lo=2):
+    return max(lo, int(round(v * scale)))
+
+
+def config1(seed: int = 0) -> Workload:
+    """500x400x300, 50,000 distinct uniform coordinates, planted J=(5,5,5),
+    noise N(0, 0.01^2), 90/10 split, M=256, lr=lambda=1e-3, 10 epochs, R=5."""
+    t = make_tensor((500, 400, 300), 50_000, [("uniform",)] * 3, (5, 5, 5), 0.01, 0.1, seed)
+    return Workload("uniform-500x400x300-50k", t, (5, 5, 5), 5, 256, 1e-3, 1e-3, 10)
+
+
+def config2(scale: float = 1.0, seed: int = 0) -> Workload:
+    """Netflix-shaped rating tensor 480,189 x 17,770 x 2,182 with 100M nonzeros;
+    Zipf 1.1 (users), Zipf 1.3 (items), uniform (time); planted J=(10,10,10),
+    values quantised into {1..5} with N(0, 0.3^2) noise; 99/1 split; J=10, R=5,
+    M=4096, lr=lambda=1e-3, 20 epochs."""
+    shape = (_scaled(480_189, scale), _scaled(17_770, scale), _scaled(2_182, math.sqrt(scale) if scale < 1 else 1.0))
+    nnz = _scaled(100_000_000, scale, lo=1000)
+    t = make_tensor(shape, nnz, [("zipf", 1.1), ("zipf", 1.3), ("uniform",)], (10, 10, 10),
+                    0.3, 0.01, seed, rating=True)
+    return Workload(f"netflix-like-{shape[0]}x{shape[1]}x{shape[2]}-{nnz}", t, (10, 10, 10), 5,
+                    4096, 1e-3, 1e-3, 20)
+
+
+def config3(scale: float = 1.0, seed: int = 0) -> Workload:
+    """4-order 200,000 x 100,000 x 500 x 24 with 50M nonzeros; Zipf 1.2 on the
+    first two modes, uniform on the last two; planted J=(8,8,8,8) + N(0,0.05^2);
+    M=8192, 90/10 split, R=5, 10 epochs."""
+    shape = (_scaled(200_000, scale), _scaled(100_000, scale), _scaled(500, math.sqrt(scale) if scale < 1 else 1.0), 24)
+    nnz = _scaled(50_000_000, scale, lo=1000)
+    t = make_tensor(shape, nnz, [("zipf", 1.2), ("zipf", 1.2), ("uniform",), ("uniform",)],
+                    (8, 8, 8, 8), 0.05, 0.1, seed)
+    return Workload(f"4order-{shape[0]}x{shape[1]}x{shape[2]}x{shape[3]}-{nnz}", t, (8, 8, 8, 8), 5,
+                    8192, 1e-3, 1e-3, 10)
+
+
+def config4_specs(count: int = 256, seed: int = 0, nnz_scale: float = 1.0):
+    """Shapes of the batched workload: `count` independent 3-order tensors with
+    mode sizes lognormal(ln 7000, 1) clipped to [1e3, 5e4], nonzeros
+    lognormal(ln 1.5e5, 1) clipped to [1e4, 2e6] (capped by 40% of the cells),
+    J drawn from {4, 8, 16}, R = min(5, J)."""
+    rng = np.random.Generator(np.random.PCG64(np.random.SeedSequence([seed, 4])))
+    specs = []
+    for t in range(count):
+        dims = np.clip(np.exp(rng.normal(math.log(7000.0), 1.0, size=3)), 1e3, 5e4).astype(np.int64)
+        nnz = float(np.clip(math.exp(rng.normal(math.log(1.5e5), 1.0)), 1e4, 2e6))
+        nnz = int(min(nnz * nnz_scale, 0.4 * float(np.prod(dims.astype(np.float64)))))
+        J = int(rng.choice([4, 8, 16]))
+        specs.append(dict(shape=tuple(int(d) for d in dims), nnz=max(nnz, 64), J=J, R=min(5, J),
+                          seed=int(seed * 100003 + t + 1)))
+    return specs
+
+
+def config4_tensor(spec) -> SparseTensor:
+    J = spec["J"]
+    return make_tensor(spec["shape"], spec["nnz"], [("uniform",)] * 3, (J, J, J), 0.05, 0.1,
+                       spec["seed"])
+
+
+# ---------------------------------------------------------------------------
+# Initial parameters.  The paper initialises everything from N(0.5, 0.1^2)
+# (Sec. 5.1); for zero-mean planted data the default is N(0, 1/J).
+# ---------------------------------------------------------------------------
+
+def init_params(shape, ranks, r_core, mode="normal", seed=1, mean_value=None,
+                mu=0.5, sigma=0.1):
+    """Initial factor matrices A_n (I_n x J_n) and Kruskal matrices B_n (J_n x R),
+    float32, row-major.
+
+    mode "normal": A, B i.i.d. N(0, 1/J_n).
+    mode "paper":  everything N(mu, sigma^2) (paper: 0.5, 0.1).
+    mode "rating": N(m, (m/5)^2) with m = (mean_value/R)^(1/(2N)) / sqrt(J), so
+                   that the initial prediction is close to mean_value.
+    """
+    N = len(shape)
+    rng = np.random.Generator(np.random.PCG64(np.random.SeedSequence([seed, 7])))
+    A, B = [], []
+    for n in range(N):
+        I, J = int(shape[n]), int(ranks[n])
+        if mode == "normal":
+            a = rng.standard_normal((I, J)) / math.sqrt(J)
+            b = rng.standard_normal((J, r_core)) / math.sqrt(J)
+        elif mode == "paper":
+            a = mu + sigma * rng.standard_normal((I, J))
+            b = mu + sigma * rng.standard_normal((J, r_core))
+        elif mode == "rating":
+            if mean_value is None:
+                raise ValueError("rating init needs mean_value")
+            m = (float(mean_value) / r_core) ** (1.0 / (2 * N)) / math.sqrt(J)
+            a = m + (m / 5.0) * rng.standard_normal((I, J))
+            b = m + (m / 5.0) * rng.standard_normal((J, r_core))
+        else:
+            raise ValueError(f"unknown init mode {mode!r}")
+        A.append(np.ascontiguousarray(a, dtype=np.float32))
+        B.append(np.ascontiguousarray(b, dtype=np.float32))
+    return A, B
+
+
+def random_coords(shape, k, seed=5, dist=None) -> np.ndarray:
+    """k query coordinates (int32 [k, N]); uniform unless dist gives per-mode
+    ("zipf", s) entries."""
+    rng = np.random.Generator(np.random.PCG64(np.random.SeedSequence([seed, 11])))
+    cols = []
+    for n, I in enumerate(shape):
+        d = dist[n] if dist is not None else ("uniform",)
+        cols.append(draw_mode_indices(rng, k, int(I), d[0], d[1] if len(d) > 1 else 0.0))
+    return np.stack(cols, axis=1).astype(np.int32)

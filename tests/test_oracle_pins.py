@@ -1,0 +1,442 @@
+"""Pins of the FP64 oracle against things other than itself.
+
+Each test checks the oracle against what the paper or plain mathematics fixes:
+the paper's worked unfolding example, dense brute-force reconstruction with
+numpy n-mode products, the CP identity of a Kruskal core, central finite
+differences of the sampled loss, the textbook matrix-factorisation special
+case, descent for small steps, permutation invariants of the sampler and the
+library stable sort.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _rng(seed):
+    return np.random.default_rng(seed)
+
+
+def _random_model(shape, ranks, R, seed, scale=1.0):
+    g = _rng(seed)
+    A = [scale * g.standard_normal((I, J)) for I, J in zip(shape, ranks)]
+    B = [scale * g.standard_normal((J, R)) for J in ranks]
+    return O.Model(shape, ranks, R, A, B)
+
+
+def _random_batch(shape, m, seed, distinct=True):
+    g = _rng(seed)
+    if distinct:
+        cells = int(np.prod(shape))
+        lin = g.choice(cells, size=m, replace=False)
+        coords = np.stack(np.unravel_index(lin, shape, order="F"), axis=1).astype(np.int32)
+    else:
+        coords = np.stack([g.integers(0, I, size=m) for I in shape], axis=1).astype(np.int32)
+    x = g.standard_normal(m).astype(np.float32)
+    return coords, x
+
+
+def _dense_reconstruction(G, A):
+    """G x_1 A1 x_2 A2 ... x_N AN by successive n-mode products (Def. 4, Def. 6),
+    standard reading (Kolda & Bader): contract core index j_n with A_n[i_n, j_n]."""
+    X = G
+    for n, a in enumerate(A):
+        X = np.tensordot(a, X, axes=([1], [n]))      # new axis 0 = i_n
+        X = np.moveaxis(X, 0, n)
+    return X
+
+
+def _kruskal_core_numpy(B):
+    """Core sum_r b1_r o ... o bN_r written with numpy outer products."""
+    R = B[0].shape[1]
+    G = None
+    for r in range(R):
+        t = B[0][:, r]
+        for b in B[1:]:
+            t = np.multiply.outer(t, b[:, r])
+        G = t if G is None else G + t
+    return G
+
+
+# ---------------------------------------------------------------------------
+# Index conventions
+# ---------------------------------------------------------------------------
+
+def test_unfolding_matches_paper_worked_example():
+    rows = []
+    dims = None
+    with open(os.path.join(GOLDEN, "unfolding_worked_example.txt")) as fh:
+        for line in fh:
+            if line.startswith("# dims:"):
+                parts = line.split()
+                dims = [int(parts[2]), int(parts[3]), int(parts[4])]
+                mode = int(parts[6])
+            elif line.strip() and not line.startswith("#"):
+                rows.append([int(v) for v in line.split()])
+    assert dims == [3, 3, 3] and len(rows) == 4
+    for i1, i2, i3, col in rows:
+        c = O.unfold_column(dims, mode - 1, [i1 - 1, i2 - 1, i3 - 1])
+        assert c + 1 == col
+        # the digit decoder used inside the oracle is the inverse of that map
+        d = O.unfold_digits(dims, mode - 1, c)
+        assert list(d[1:]) == [i2 - 1, i3 - 1]
+
+
+@pytest.mark.parametrize("ranks,n", [((3, 4, 5), 0), ((3, 4, 5), 1), ((3, 4, 5), 2), ((2, 3, 2, 4), 2)])
+def test_unfold_digits_roundtrip(ranks, n):
+    P = int(np.prod(ranks)) // ranks[n]
+    seen = set()
+    for c in range(P):
+        d = O.unfold_digits(ranks, n, c)
+        idx = [0 if k == n else int(d[k]) for k in range(len(ranks))]
+        assert O.unfold_column(ranks, n, idx) == c
+        seen.add(tuple(idx))
+    assert len(seen) == P
+
+
+# ---------------------------------------------------------------------------
+# Model value x-hat
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("shape,ranks,R", [((4, 3, 5), (2, 3, 2), 2), ((3, 2, 4, 2), (2, 2, 3, 2), 3),
+                                          ((5, 6), (3, 2), 4)])
+def test_predict_equals_dense_bruteforce(shape, ranks, R):
+    md = _random_model(shape, ranks, R, seed=11)
+    G = _kruskal_core_numpy(md.B)
+    X = _dense_reconstruction(G, md.A)
+    coords = np.stack(np.unravel_index(np.arange(int(np.prod(shape))), shape), axis=1).astype(np.int32)
+    got = md.predict(coords)
+    want = X[tuple(coords.T)]
+    np.testing.assert_allclose(got, want, rtol=1e-12, atol=1e-12)
+    # the oracle's core equals the numpy Kruskal core
+    np.testing.assert_allclose(md.core_tensor(), G, rtol=1e-13, atol=1e-13)
+
+
+def test_predict_cp_identity():
+    """A Kruskal core makes the model CP with factors A_n B_n:
+    x-hat = sum_r prod_n (A_n B_n)[i_n, r]."""
+    shape, ranks, R = (30, 20, 10, 5), (4, 3, 5, 2), 3
+    md = _random_model(shape, ranks, R, seed=3)
+    coords, _ = _random_batch(shape, 500, seed=4)
+    C = [md.A[n] @ md.B[n] for n in range(4)]
+    want = np.ones((500, R))
+    for n in range(4):
+        want *= C[n][coords[:, n]]
+    np.testing.assert_allclose(md.predict(coords), want.sum(axis=1), rtol=1e-11, atol=1e-12)
+
+
+def test_core_one_hot_columns():
+    """Eq. 4 with one-hot Kruskal columns puts a 1 at each selected cell."""
+    ranks, R = (3, 4, 2), 2
+    B = [np.zeros((J, R)) for J in ranks]
+    cells = [(2, 1, 0), (0, 3, 1)]
+    for r, cell in enumerate(cells):
+        for n in range(3):
+            B[n][cell[n], r] = 1.0
+    md = O.Model((5, 5, 5), ranks, R, [np.zeros((5, J)) for J in ranks], B)
+    G = md.core_tensor()
+    want = np.zeros(ranks)
+    for cell in cells:
+        want[cell] = 1.0
+    assert np.array_equal(G, want)
+
+
+# ---------------------------------------------------------------------------
+# Gradients (Eq. 15, Eq. 18) against central finite differences of the loss
+#   f = (1/(2m)) sum_s (x-hat_s - x_s)^2 + (lambda/2) ||block||^2
+# which is quadratic in each block, so central differences are exact up to
+# rounding.
+# ---------------------------------------------------------------------------
+
+def _loss(md, coords, x, lam, block):
+    e = md.predict(coords) - x.astype(np.float64)
+    return 0.5 * float(np.dot(e, e)) / coords.shape[0] + 0.5 * lam * float(np.dot(block, block))
+
+
+@pytest.mark.parametrize("literal", [False, True])
+@pytest.mark.parametrize("shape,ranks,R", [((6, 5, 4), (3, 2, 4), 3), ((4, 3, 3, 5), (2, 3, 2, 2), 2)])
+def test_core_gradient_finite_differences(shape, ranks, R, literal):
+    md = _random_model(shape, ranks, R, seed=21, scale=0.7)
+    coords, x = _random_batch(shape, 17, seed=22)
+    lam, h = 0.3, 1e-4
+    for n in range(len(shape)):
+        for r in range(R):
+            g = md.core_gradient(coords, x, n, r, lam, literal=literal)
+            fd = np.empty_like(g)
+            for j in range(ranks[n]):
+                b0 = md.B[n][j, r]
+                md.B[n][j, r] = b0 + h
+                fp = _loss(md, coords, x, lam, md.B[n][:, r])
+                md.B[n][j, r] = b0 - h
+                fm = _loss(md, coords, x, lam, md.B[n][:, r])
+                md.B[n][j, r] = b0
+                fd[j] = (fp - fm) / (2 * h)
+            np.testing.assert_allclose(g, fd, rtol=1e-7, atol=1e-9)
+
+
+@pytest.mark.parametrize("norm_mode", [0, 1])
+@pytest.mark.parametrize("shape,ranks,R", [((6, 5, 4), (3, 2, 4), 3), ((4, 3, 3, 5), (2, 3, 2, 2), 2)])
+def test_factor_gradient_finite_differences(shape, ranks, R, norm_mode):
+    md = _random_model(shape, ranks, R, seed=31, scale=0.7)
+    coords, x = _random_batch(shape, 23, seed=32, distinct=False)
+    lam, h = 0.2, 1e-4
+    m = coords.shape[0]
+    for n in range(len(shape)):
+        for row in np.unique(coords[:, n]):
+            sel = coords[:, n] == row
+            cnt = int(sel.sum())
+            g = md.factor_gradient(coords, x, n, int(row), lam, norm_mode)
+            fd = np.empty_like(g)
+            for j in range(ranks[n]):
+                a0 = md.A[n][row, j]
+                md.A[n][row, j] = a0 + h
+                fp = _loss(md, coords[sel], x[sel], lam, md.A[n][row])
+                md.A[n][row, j] = a0 - h
+                fm = _loss(md, coords[sel], x[sel], lam, md.A[n][row])
+                md.A[n][row, j] = a0
+                fd[j] = (fp - fm) / (2 * h)
+            # _loss normalises by the row's own count; Eq. 18 by M (mode 0)
+            denom = m if norm_mode == 0 else cnt
+            data_fd = fd - lam * md.A[n][row]
+            np.testing.assert_allclose(g - lam * md.A[n][row], data_fd * cnt / denom,
+                                       rtol=1e-7, atol=1e-9)
+
+
+def test_literal_and_closed_form_steps_agree():
+    """W_r = H O_r (Algorithm 1 lines 2-5, Eq. 7) equals the closed form."""
+    shape, ranks, R = (5, 4, 6), (3, 2, 3), 2
+    coords, x = _random_batch(shape, 19, seed=41, distinct=False)
+    a = _random_model(shape, ranks, R, seed=42)
+    b = a.copy()
+    Va, Fa, Sa = a.step(coords, x, 0.05, 0.05, 0.01, 0.02, literal=False, probe=True)
+    Vb, Fb, Sb = b.step(coords, x, 0.05, 0.05, 0.01, 0.02, literal=True, probe=True)
+    np.testing.assert_allclose(Va, Vb, rtol=1e-12, atol=1e-12)
+    np.testing.assert_allclose(Fa, Fb, rtol=1e-12, atol=1e-12)
+    assert np.array_equal(Sa, Sb)
+    for n in range(3):
+        np.testing.assert_allclose(a.A[n], b.A[n], rtol=1e-12, atol=1e-13)
+        np.testing.assert_allclose(a.B[n], b.B[n], rtol=1e-12, atol=1e-13)
+
+
+def test_step_probe_matches_gradient_functions():
+    """The V recorded for (mode 1, r_core 1) of a step is the Eq. 15 bracket at
+    the start of the step; the factor F of mode 1 uses the core after the core
+    phase (Algorithm 1 line 16)."""
+    shape, ranks, R = (6, 5, 4), (3, 2, 4), 3
+    coords, x = _random_batch(shape, 21, seed=43, distinct=False)
+    md = _random_model(shape, ranks, R, seed=44)
+    lam_b = 0.01
+    g00 = md.core_gradient(coords, x, 0, 0, lam_b)
+    V, F, S = md.copy().step(coords, x, 0.1, 0.1, 0.0, lam_b, probe=True)
+    np.testing.assert_allclose(V[0, 0, :3] / coords.shape[0] + lam_b * md.B[0][:, 0], g00, rtol=1e-12)
+
+
+# ---------------------------------------------------------------------------
+# Whole step: the N=2, B(1)=B(2)=I special case is textbook alternating
+# matrix-factorisation SGD on the rows u = a^(1)_i, v = a^(2)_k.
+# ---------------------------------------------------------------------------
+
+def test_matrix_factorisation_special_case():
+    J = 3
+    g = _rng(7)
+    U = g.standard_normal((5, J))
+    Vm = g.standard_normal((4, J))
+    md = O.Model((5, 4), (J, J), J, [U, Vm], [np.eye(J), np.eye(J)])
+    coords = np.array([[2, 1], [2, 3], [0, 1]], dtype=np.int32)
+    x = np.array([0.7, -1.2, 0.4], dtype=np.float32)
+    gam, lam = 0.3, 0.05
+    md.step(coords, x, gam, 0.0, lam, 0.0)
+    # textbook: for each user row, u <- u + gamma*(sum_k err_k v_k / M - lam u)
+    M = 3
+    u, v = U.copy(), Vm.copy()
+    for i in np.unique(coords[:, 0]):
+        grad = np.zeros(J)
+        for s in np.where(coords[:, 0] == i)[0]:
+            k = coords[s, 1]
+            err = float(x[s]) - u[i] @ v[k]
+            grad += err * v[k]
+        u[i] = u[i] + gam * (grad / M - lam * u[i])
+    v_new = v.copy()
+    for k in np.unique(coords[:, 1]):
+        grad = np.zeros(J)
+        for s in np.where(coords[:, 1] == k)[0]:
+            i = coords[s, 0]
+            err = float(x[s]) - u[i] @ v[k]
+            grad += err * u[i]
+        v_new[k] = v[k] + gam * (grad / M - lam * v[k])
+    np.testing.assert_allclose(md.A[0], u, rtol=1e-13, atol=1e-14)
+    np.testing.assert_allclose(md.A[1], v_new, rtol=1e-13, atol=1e-14)
+    np.testing.assert_array_equal(md.B[0], np.eye(J))
+
+
+# ---------------------------------------------------------------------------
+# Descent (Theorem 3): each block step is a small gradient step on a convex
+# quadratic, so the sampled objective decreases.
+# ---------------------------------------------------------------------------
+
+def test_step_decreases_sampled_objective():
+    shape, ranks, R = (8, 7, 6), (3, 3, 3), 2
+    coords, x = _random_batch(shape, 64, seed=51)
+    md = _random_model(shape, ranks, R, seed=52, scale=0.6)
+    lam = 0.01
+
+    def objective(m):
+        e = m.predict(coords) - x
+        reg = sum(float(np.sum(b * b)) for b in m.B)
+        for n in range(3):
+            rows = np.unique(coords[:, n])
+            reg += float(np.sum(m.A[n][rows] ** 2))
+        return 0.5 * float(e @ e) / 64 + 0.5 * lam * reg
+
+    prev = objective(md)
+    for _ in range(5):
+        md.step(coords, x, 0.05, 0.05, lam, lam)
+        cur = objective(md)
+        assert cur < prev
+        prev = cur
+
+
+# ---------------------------------------------------------------------------
+# Sampler and tiler
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("n", [1, 2, 3, 4, 5, 7, 8, 9, 100, 1023, 1024, 1025, 4097, 65536, 65537, 200003])
+def test_sampler_is_a_permutation(n):
+    p = O.epoch_schedule(n, seed=2, epoch=3)
+    assert p.shape == (n,)
+    assert np.array_equal(np.sort(p), np.arange(n))
+
+
+def test_sampler_depends_on_seed_and_epoch():
+    n = 10007
+    a = O.epoch_schedule(n, 2, 0)
+    b = O.epoch_schedule(n, 2, 1)
+    c = O.epoch_schedule(n, 3, 0)
+    assert np.array_equal(a, O.epoch_schedule(n, 2, 0))
+    assert (a != b).mean() > 0.99 and (a != c).mean() > 0.99
+    assert O.perm(n, 2, 1, 17) == b[17]
+
+
+def test_sampler_positions_are_uniform():
+    """Where entry 0 lands over many epochs is uniform over [0, n) (chi-square)."""
+    n, epochs = 64, 6400
+    hits = np.zeros(n)
+    for e in range(epochs):
+        p = O.epoch_schedule(n, 9, e)
+        hits[int(np.where(p == 0)[0][0])] += 1
+    exp = epochs / n
+    chi2 = float(((hits - exp) ** 2 / exp).sum())
+    assert chi2 < 120.0          # 63 dof: P(chi2 > 120) ~ 1e-5
+    # consecutive positions are not correlated with the identity
+    p = O.epoch_schedule(100000, 1, 0)
+    assert abs(np.corrcoef(np.arange(100000), p)[0, 1]) < 0.02
+
+
+@pytest.mark.parametrize("m,hi", [(1, 5), (17, 3), (256, 50), (4096, 500000), (3000, 1)])
+def test_stable_order_matches_library_stable_sort(m, hi):
+    keys = _rng(m).integers(0, hi, size=m).astype(np.int32)
+    order, seg = O.stable_order(keys)
+    assert np.array_equal(order, np.argsort(keys, kind="stable"))
+    uniq, first = np.unique(keys, return_index=True)
+    starts = np.searchsorted(keys[order], uniq, side="left")
+    assert np.array_equal(seg[:-1], starts) and seg[-1] == m
+
+
+# ---------------------------------------------------------------------------
+# RMSE / MAE (Eq. 19) on residual patterns with closed-form answers.
+# ---------------------------------------------------------------------------
+
+def test_rmse_mae_closed_form():
+    shape, ranks = (4, 4, 4), (2, 2, 2)
+    md = O.Model(shape, ranks, 1, [np.zeros((4, 2))] * 3, [np.ones((2, 1))] * 3)
+    coords = np.array([[0, 0, 0], [1, 2, 3]], dtype=np.int32)
+    r, a = md.rmse_mae(coords, np.array([3.0, -4.0], dtype=np.float32))
+    assert r == pytest.approx(math.sqrt(12.5), rel=1e-15)
+    assert a == pytest.approx(3.5, rel=1e-15)
+    # an exact model has zero error
+    md2 = _random_model(shape, ranks, 2, seed=5)
+    c, _ = _random_batch(shape, 30, seed=6)
+    vals = md2.predict(c)
+    r2, a2 = md2.rmse_mae(c, vals.astype(np.float32))
+    assert r2 < 1e-6 and a2 < 1e-6
+
+
+# ---------------------------------------------------------------------------
+# Epoch driver: minibatch b is pi_e([bM, bM+M)) and the last batch is ragged.
+# ---------------------------------------------------------------------------
+
+def test_epoch_equals_manual_minibatches():
+    shape, ranks, R = (9, 8, 7), (3, 2, 3), 2
+    coords, x = _random_batch(shape, 103, seed=61)
+    M, seed, ep = 16, 2, 4
+    a = _random_model(shape, ranks, R, seed=62)
+    b = a.copy()
+    a.epoch(coords, x, M, seed, ep, 0.05, 0.04, 0.01, 0.02)
+    sched = O.epoch_schedule(103, seed, ep)
+    for t0 in range(0, 103, M):
+        ids = sched[t0:t0 + M]
+        b.step(coords[ids], x[ids], 0.05, 0.04, 0.01, 0.02)
+    for n in range(3):
+        np.testing.assert_array_equal(a.A[n], b.A[n])
+        np.testing.assert_array_equal(a.B[n], b.B[n])
+
+
+# ---------------------------------------------------------------------------
+# Iteration as a whole: recover a planted, exactly representable model
+# (Kruskal core, J=4, R=3) from half of a 30x30x30 tensor with N(0, 0.01^2)
+# noise; the held-out RMSE must reach the noise floor (<= 2 sigma).
+# ---------------------------------------------------------------------------
+
+def test_planted_kruskal_core_recovery():
+    g = np.random.default_rng(0)
+    shape, ranks, R, sigma = (30, 30, 30), (4, 4, 4), 3, 0.01
+    truth = O.Model(shape, ranks, R, [g.standard_normal((30, 4)) / 2 for _ in range(3)],
+                    [g.standard_normal((4, R)) for _ in range(3)])
+    lin = g.choice(27000, size=13500, replace=False)
+    coords = np.stack(np.unravel_index(lin, shape), axis=1).astype(np.int32)
+    x = (truth.predict(coords) + sigma * g.standard_normal(13500)).astype(np.float32)
+    tr, te = slice(0, 12150), slice(12150, 13500)
+    g2 = np.random.default_rng(5)
+    md = O.Model(shape, ranks, R, [0.3 * g2.standard_normal((30, 4)) for _ in range(3)],
+                 [g2.standard_normal((4, R)) for _ in range(3)])
+    start = md.rmse_mae(coords[te], x[te])[0]
+    for ep in range(150):
+        md.epoch(coords[tr], x[tr], 1, 2, ep, 0.002, 0.002, 1e-4, 1e-4)
+    end = md.rmse_mae(coords[te], x[te])[0]
+    assert start > 50 * sigma
+    assert end <= 2 * sigma
+
+
+@pytest.mark.parametrize("norm_mode", [0, 1])
+def test_step_is_cyclic_block_sgd(norm_mode):
+    """Algorithm 1 order: for n = 1..N, r = 1..R, b^(n)_r takes an SGD step on
+    its Eq. 15 gradient at the current state (Gauss-Seidel across r and n);
+    then for n = 1..N every touched row of A(n) takes an SGD step on its
+    Eq. 18 gradient at the state after modes < n (rows of one mode jointly).
+    Rebuilt here from the finite-difference-pinned gradient functions."""
+    shape, ranks, R = (7, 6, 5), (3, 2, 3), 3
+    coords, x = _random_batch(shape, 29, seed=71, distinct=False)
+    md = _random_model(shape, ranks, R, seed=72, scale=0.8)
+    ref = md.copy()
+    ga, gb, la, lb = 0.07, 0.05, 0.02, 0.03
+    V, F, nseg = md.step(coords, x, ga, gb, la, lb, norm_mode=norm_mode, probe=True)
+    m = coords.shape[0]
+    for n in range(3):
+        for r in range(R):
+            g = ref.core_gradient(coords, x, n, r, lb)
+            np.testing.assert_allclose(V[n, r, :ranks[n]] / m + lb * ref.B[n][:, r], g, rtol=1e-12, atol=1e-13)
+            ref.B[n][:, r] = ref.B[n][:, r] - gb * g
+    for n in range(3):
+        rows = np.unique(coords[:, n])
+        assert nseg[n] == rows.size
+        grads = [ref.factor_gradient(coords, x, n, int(i), la, norm_mode) for i in rows]
+        for i, g in zip(rows, grads):
+            ref.A[n][i] = ref.A[n][i] - ga * g
+    for n in range(3):
+        np.testing.assert_allclose(md.B[n], ref.B[n], rtol=1e-12, atol=1e-13)
+        np.testing.assert_allclose(md.A[n], ref.A[n], rtol=1e-12, atol=1e-13)
