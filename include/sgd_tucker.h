@@ -1,0 +1,195 @@
+/*
+ * sgd_tucker.h — C ABI of the GB300 SGD_Tucker library (libsgdtucker.so).
+ *
+ * SGD_Tucker (Li et al., arXiv 2012.03550) decomposes a sparse N-order tensor
+ * X (I_1 x ... x I_N, given as COO nonzeros) into factor matrices
+ * A(n) in R^{I_n x J_n} and a core G-hat that is itself a Kruskal product of
+ * matrices B(n) in R^{J_n x R_core} (Sec. 4.1, Eq. 4):
+ *     G-hat = sum_r b(1)_{:,r} o ... o b(N)_{:,r},
+ *     x-hat(i_1..i_N) = G-hat x_1 a(1)_{i_1,:} ... x_N a(N)_{i_N,:}   (Def. 6).
+ * Training is the minibatch SGD of Algorithm 1 (Sec. 4.3, Eqs. 13-18): for
+ * each minibatch Psi of M sampled nonzeros, a core phase that updates every
+ * column b(n)_{:,r} cyclically (Eq. 15), the rebuild of G-hat (Eq. 4), and a
+ * factor phase that updates every touched row a(n)_{i,:} (Eq. 18), mode after
+ * mode.  All kernels run on one GPU (sm_103a).
+ *
+ * Conventions for every call:
+ *  - Every function returns STD_OK (0) or a negative status; none aborts.
+ *    std_last_error() returns a thread-local message for the last failure.
+ *  - Indices are 0-based (the paper is 1-based).  Coordinates are int32,
+ *    row-major [k][N].  Factor matrices cross the ABI dense row-major
+ *    (I_n x J_n), Kruskal matrices row-major (J_n x R_core), the core as a
+ *    vector of prod J_n floats with mode 1 fastest (Vec_1 of Def. 2).
+ *  - Pointer arguments are host pointers when std_options.ptr_kind = 0 and
+ *    device pointers (e.g. torch data_ptr()) when ptr_kind = 1.  The library
+ *    never takes ownership of caller memory; buffers may be freed after the
+ *    call returns.  Output buffers are owned by the caller.
+ *  - A context owns all device memory it allocates and runs every kernel on
+ *    std_options.stream.  Calls on one context must not overlap; distinct
+ *    contexts are independent.  All calls are synchronous with respect to the
+ *    host unless noted.
+ */
+#ifndef SGD_TUCKER_H
+#define SGD_TUCKER_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Status codes. */
+#define STD_OK            0
+#define STD_EINVAL      (-1)  /* bad argument: N, I_n, J_n, M, index >= I_n, null pointer */
+#define STD_ENOMEM      (-2)  /* device allocation failed or the HBM budget was exceeded */
+#define STD_ECUDA       (-3)  /* a CUDA runtime call failed (message has the CUDA error) */
+#define STD_ETIMEOUT    (-4)  /* a device grid barrier exceeded its watchdog budget */
+#define STD_ENUMERIC    (-5)  /* NaN or Inf met in a reduction */
+#define STD_EUNSUPPORTED (-6) /* shape beyond the kernels' compiled limits (see below) */
+
+/* Kernel limits (checked by std_create / std_sgd_epoch, STD_EUNSUPPORTED):
+ * 2 <= N <= STD_MAX_ORDER, 1 <= J_n <= STD_MAX_RANK, 1 <= R_core <= STD_MAX_RANK,
+ * prod J_n <= STD_MAX_CORE, minibatch M <= STD_MAX_MINIBATCH. */
+#define STD_MAX_ORDER     6
+#define STD_MAX_RANK      32
+#define STD_MAX_CORE      16384
+#define STD_MAX_MINIBATCH 16384
+
+typedef struct std_ctx std_ctx;
+
+/* Options of a context; initialise with std_default_options(). */
+typedef struct {
+    int32_t  r_core;      /* R_core >= 1, Kruskal rank of the core (Eq. 4); default 5 (Sec. 5.3) */
+    int32_t  precision;   /* 0: FP32 everywhere; 1: BF16 copies of A and G-hat for gathers and
+                             the core contraction, FP32 accumulation and FP32 master A, B */
+    int32_t  norm_mode;   /* factor-row normaliser: 0 = minibatch size M (Eq. 18, default),
+                             1 = |Psi_i|, the row's sample count (Algorithm 1, factor update) */
+    int32_t  init_mode;   /* initial A, B: 0 = N(init_mu, init_sigma^2) (Sec. 5.1: 0.5, 0.1),
+                             1 = N(0, 1/J_n); drawn on the device from seed_init */
+    double   init_mu;
+    double   init_sigma;
+    uint64_t seed_init;   /* initial-parameter stream */
+    uint64_t seed_sched;  /* minibatch-sampler key: epoch e visits the training entries in the
+                             order of a keyed permutation of [0, nnz) (see std_sgd_epoch) */
+    int32_t  ptr_kind;    /* 0: pointers are host memory; 1: pointers are device memory */
+    int32_t  ctas;        /* CTAs of the persistent epoch kernel; 0 = chosen by the library */
+    void*    stream;      /* cudaStream_t for every kernel and copy; NULL = the legacy stream */
+    uint64_t watchdog_ns; /* grid-barrier wait budget in ns; 0 = 2e9 (2 s) */
+    uint64_t hbm_budget_bytes; /* cap on the context's device allocations; 0 = none */
+} std_options;
+
+/* Fill *opt with the defaults listed above. */
+void std_default_options(std_options* opt);
+
+/*
+ * Create a context holding the training tensor and the model.
+ *   order        N (2..STD_MAX_ORDER)
+ *   mode_sizes   I_n, n < N (each >= 1, < 2^31)
+ *   ranks        J_n, n < N (1..STD_MAX_RANK)
+ *   nnz          number of training nonzeros (>= 1, < 2^31)
+ *   indices      nnz x N int32 coordinates, 0-based, row-major (host or device per ptr_kind)
+ *   values       nnz float values
+ *   opt          options (NULL = defaults)
+ * The COO is copied into library-owned device memory (coordinates checked
+ * against I_n: STD_EINVAL on an index outside [0, I_n)).  A and B are drawn
+ * per init_mode.  Errors: STD_EINVAL, STD_EUNSUPPORTED, STD_ENOMEM, STD_ECUDA;
+ * on error *out is NULL and nothing is leaked.
+ */
+int std_create(std_ctx** out, int32_t order, const int64_t* mode_sizes, const int32_t* ranks,
+               int64_t nnz, const int32_t* indices, const float* values, const std_options* opt);
+
+/* Release every resource of the context (NULL is a no-op). */
+int std_destroy(std_ctx* ctx);
+
+/* Per-epoch statistics (nullable output of std_sgd_epoch). */
+typedef struct {
+    double  seconds;     /* device time of the epoch (sampler, tiler and update kernels) */
+    double  nnz_per_s;   /* nnz / seconds */
+    int64_t nnz;         /* training nonzeros visited */
+    int64_t batches;     /* minibatches in the epoch (the last one may be short) */
+    int64_t epoch;       /* index of the epoch just run */
+} std_epoch_stats;
+
+/*
+ * One training epoch (Algorithm 1 over every minibatch).  Epoch e visits the
+ * training entries in the order pi_e(0), pi_e(1), ... where pi_e is a keyed
+ * permutation of [0, nnz) (a balanced 6-round Feistel network with SplitMix64
+ * rounds, restricted to [0, nnz) by cycle walking, keyed by seed_sched and e);
+ * minibatch b is positions [bM, min(bM+M, nnz)), and a short last minibatch
+ * uses its own size as M in every normaliser.  Per minibatch:
+ *   core phase, n = 1..N, r = 1..R_core in order (Algorithm 1 lines 1-15):
+ *     b(n)_r <- b(n)_r - lr_b (V / M + lambda_b b(n)_r),  V of Eq. 15;
+ *   G-hat from B (line 16, Eq. 4);
+ *   factor phase, n = 1..N in order (lines 17-25): every row i touched by the
+ *     minibatch, all rows of a mode reading the state before that mode's update:
+ *     a(n)_i <- a(n)_i - lr_a (F / M_i + lambda_a a(n)_i),  F of Eq. 18,
+ *     M_i = M (norm_mode 0) or the row's sample count (norm_mode 1).
+ * minibatch: 1..STD_MAX_MINIBATCH.  The epoch counter then advances.
+ * Errors: STD_EINVAL, STD_EUNSUPPORTED, STD_ENOMEM, STD_ECUDA, STD_ETIMEOUT.
+ */
+int std_sgd_epoch(std_ctx* ctx, float lr_a, float lr_b, float lambda_a, float lambda_b,
+                  int32_t minibatch, std_epoch_stats* out);
+
+/* Gradient probe of std_sgd_batches: host buffers filled for the first
+ * minibatch of the range (any member may be NULL). */
+typedef struct {
+    float*   core_V;    /* [N][R_core][STD_MAX_RANK]: V of Algorithm 1 line 13 (the bracket of
+                           Eq. 15) for each mode n and column r, in update order */
+    float*   factor_F;  /* [N][M][STD_MAX_RANK]: F of Algorithm 1 line 22 (the bracket of
+                           Eq. 18) for each mode n and each touched row, rows ascending */
+    int64_t* nseg;      /* [N]: touched rows per mode */
+} std_probe;
+
+/*
+ * Minibatches [batch_begin, batch_end) of the current epoch's schedule (same
+ * definition as std_sgd_epoch), without advancing the epoch counter.  With a
+ * probe, the gradients of the first minibatch of the range are recorded.
+ */
+int std_sgd_batches(std_ctx* ctx, float lr_a, float lr_b, float lambda_a, float lambda_b,
+                    int32_t minibatch, int64_t batch_begin, int64_t batch_end, std_probe* probe);
+
+/*
+ * The sampler and tiler output of the current epoch for minibatches
+ * [batch_begin, batch_end): for the `count` positions t of those minibatches,
+ *   sample_ids[t]            training-entry index pi_e(t)                 (int32[count])
+ *   order[n][t]              batch position of the q-th entry after the stable
+ *                            sort of the minibatch by i_n                  (int32[N][count])
+ *   seg_start[n][t], seg_end[n][t]  first and last sorted position (within the
+ *                            minibatch) of the run of equal i_n holding sorted
+ *                            position q                                    (int32[N][count])
+ * where t = (minibatch start) + q.  Any output may be NULL.  Host buffers.
+ */
+int std_schedule(std_ctx* ctx, int32_t minibatch, int64_t batch_begin, int64_t batch_end,
+                 int32_t* sample_ids, int32_t* order, int32_t* seg_start, int32_t* seg_end);
+
+/* x-hat at k coordinates (Def. 6 with the Kruskal core of Eq. 4); out[k]. */
+int std_predict(std_ctx* ctx, int64_t k, const int32_t* coords, float* out);
+
+/*
+ * RMSE and MAE (Eq. 19) of the model over k entries (coords k x N, values k),
+ * accumulated in FP64 in a fixed order (bit-reproducible).  mae may be NULL.
+ * k = 0 gives 0.  STD_ENUMERIC when the sum is NaN or Inf.
+ */
+int std_rmse(std_ctx* ctx, int64_t k, const int32_t* coords, const float* values,
+             double* rmse, double* mae);
+
+/*
+ * Copy the model out: A[n] (I_n x J_n), B[n] (J_n x R_core), core (prod J_n,
+ * mode 1 fastest, built from B by Eq. 4) and the epoch counter.  Any array or
+ * entry may be NULL.  Buffers per ptr_kind.
+ */
+int std_get_params(std_ctx* ctx, float* const* A, float* const* B, float* core, int64_t* epoch);
+
+/* Overwrite the model (A[n], B[n] as in std_get_params; NULL entries are left
+ * unchanged) and the epoch counter (ignored when < 0). */
+int std_set_params(std_ctx* ctx, const float* const* A, const float* const* B, int64_t epoch);
+
+/* Thread-local description of the last error ("" if none). */
+const char* std_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SGD_TUCKER_H */

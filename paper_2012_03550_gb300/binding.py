@@ -1,0 +1,298 @@
+"""Thin ctypes binding of libsgdtucker.so (include/sgd_tucker.h).
+
+Functions keep the C names (std_create, std_sgd_epoch, ...) and only marshal
+arguments: numpy arrays are passed as host pointers, torch tensors as their
+device pointers (create the context with ptr_kind=1 for those).  Every
+computation runs in the library's CUDA kernels; there is no fallback, and
+importing this module fails loudly when the library has not been built.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional, Sequence
+
+import numpy as np
+
+from . import build as _build
+
+STD_OK = 0
+STD_EINVAL = -1
+STD_ENOMEM = -2
+STD_ECUDA = -3
+STD_ETIMEOUT = -4
+STD_ENUMERIC = -5
+STD_EUNSUPPORTED = -6
+STD_MAX_ORDER = 6
+STD_MAX_RANK = 32
+STD_MAX_CORE = 16384
+STD_MAX_MINIBATCH = 16384
+
+_NAMES = {STD_EINVAL: "STD_EINVAL", STD_ENOMEM: "STD_ENOMEM", STD_ECUDA: "STD_ECUDA",
+          STD_ETIMEOUT: "STD_ETIMEOUT", STD_ENUMERIC: "STD_ENUMERIC", STD_EUNSUPPORTED: "STD_EUNSUPPORTED"}
+
+
+class StdError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{_NAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+class std_options(ctypes.Structure):
+    _fields_ = [
+        ("r_core", ctypes.c_int32),
+        ("precision", ctypes.c_int32),
+        ("norm_mode", ctypes.c_int32),
+        ("init_mode", ctypes.c_int32),
+        ("init_mu", ctypes.c_double),
+        ("init_sigma", ctypes.c_double),
+        ("seed_init", ctypes.c_uint64),
+        ("seed_sched", ctypes.c_uint64),
+        ("ptr_kind", ctypes.c_int32),
+        ("ctas", ctypes.c_int32),
+        ("stream", ctypes.c_void_p),
+        ("watchdog_ns", ctypes.c_uint64),
+        ("hbm_budget_bytes", ctypes.c_uint64),
+    ]
+
+
+class std_epoch_stats(ctypes.Structure):
+    _fields_ = [
+        ("seconds", ctypes.c_double),
+        ("nnz_per_s", ctypes.c_double),
+        ("nnz", ctypes.c_int64),
+        ("batches", ctypes.c_int64),
+        ("epoch", ctypes.c_int64),
+    ]
+
+
+class std_probe(ctypes.Structure):
+    _fields_ = [
+        ("core_V", ctypes.c_void_p),
+        ("factor_F", ctypes.c_void_p),
+        ("nseg", ctypes.c_void_p),
+    ]
+
+
+_lib = None
+
+# Every symbol the header declares, with its ctypes signature.
+_P = ctypes.c_void_p
+SIGNATURES = {
+    "std_default_options": (None, [_P]),
+    "std_create": (ctypes.c_int, [_P, ctypes.c_int32, _P, _P, ctypes.c_int64, _P, _P, _P]),
+    "std_destroy": (ctypes.c_int, [_P]),
+    "std_sgd_epoch": (ctypes.c_int, [_P, ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_float,
+                                     ctypes.c_int32, _P]),
+    "std_sgd_batches": (ctypes.c_int, [_P, ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_float,
+                                       ctypes.c_int32, ctypes.c_int64, ctypes.c_int64, _P]),
+    "std_schedule": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_int64, ctypes.c_int64, _P, _P, _P, _P]),
+    "std_predict": (ctypes.c_int, [_P, ctypes.c_int64, _P, _P]),
+    "std_rmse": (ctypes.c_int, [_P, ctypes.c_int64, _P, _P, _P, _P]),
+    "std_get_params": (ctypes.c_int, [_P, _P, _P, _P, _P]),
+    "std_set_params": (ctypes.c_int, [_P, _P, _P, ctypes.c_int64]),
+    "std_last_error": (ctypes.c_char_p, []),
+}
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def lib():
+    """Load libsgdtucker.so (raises if it is missing)."""
+    global _lib
+    if _lib is None:
+        path = library_path()
+        if not os.path.exists(path):
+            raise RuntimeError(f"{path} is missing: build it with __graft_entry__.build() "
+                               "(paper_2012_03550_gb300.build.build())")
+        L = ctypes.CDLL(path)
+        for name, (res, args) in SIGNATURES.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def std_last_error() -> str:
+    return lib().std_last_error().decode()
+
+
+def _check(rc: int):
+    if rc != STD_OK:
+        raise StdError(rc, std_last_error())
+
+
+def _addr(x) -> Optional[int]:
+    """Host pointer of a numpy array or device pointer of a torch tensor."""
+    if x is None:
+        return None
+    if isinstance(x, np.ndarray):
+        if not x.flags["C_CONTIGUOUS"]:
+            raise ValueError("arrays must be C-contiguous")
+        return x.ctypes.data
+    if hasattr(x, "data_ptr"):
+        if not x.is_contiguous():
+            raise ValueError("tensors must be contiguous")
+        return x.data_ptr()
+    raise TypeError(f"unsupported buffer type {type(x)!r}")
+
+
+def _ptr_array(items):
+    arr = (ctypes.c_void_p * len(items))(*[_addr(x) for x in items])
+    return arr
+
+
+def std_default_options() -> std_options:
+    o = std_options()
+    lib().std_default_options(ctypes.byref(o))
+    return o
+
+
+def std_create(order: int, mode_sizes: Sequence[int], ranks: Sequence[int], nnz: int, indices, values,
+               opt: Optional[std_options] = None):
+    """Returns an opaque context handle (ctypes.c_void_p)."""
+    ms = np.ascontiguousarray(mode_sizes, dtype=np.int64)
+    rk = np.ascontiguousarray(ranks, dtype=np.int32)
+    ctx = ctypes.c_void_p()
+    _check(lib().std_create(ctypes.byref(ctx), int(order), ms.ctypes.data, rk.ctypes.data, int(nnz),
+                            _addr(indices), _addr(values), ctypes.byref(opt) if opt is not None else None))
+    return ctx
+
+
+def std_destroy(ctx) -> None:
+    _check(lib().std_destroy(ctx))
+
+
+def std_sgd_epoch(ctx, lr_a: float, lr_b: float, lambda_a: float, lambda_b: float, minibatch: int) -> dict:
+    st = std_epoch_stats()
+    _check(lib().std_sgd_epoch(ctx, lr_a, lr_b, lambda_a, lambda_b, int(minibatch), ctypes.byref(st)))
+    return dict(seconds=st.seconds, nnz_per_s=st.nnz_per_s, nnz=st.nnz, batches=st.batches, epoch=st.epoch)
+
+
+def std_sgd_batches(ctx, lr_a, lr_b, lambda_a, lambda_b, minibatch, batch_begin, batch_end, probe=None):
+    """probe: None or a dict with numpy arrays 'core_V' [N,R,32], 'factor_F' [N,M,32], 'nseg' [N]."""
+    p = None
+    if probe is not None:
+        p = std_probe(_addr(probe.get("core_V")), _addr(probe.get("factor_F")), _addr(probe.get("nseg")))
+    _check(lib().std_sgd_batches(ctx, lr_a, lr_b, lambda_a, lambda_b, int(minibatch), int(batch_begin),
+                                 int(batch_end), ctypes.byref(p) if p is not None else None))
+
+
+def std_schedule(ctx, minibatch, batch_begin, batch_end, sample_ids=None, order=None, seg_start=None,
+                 seg_end=None):
+    _check(lib().std_schedule(ctx, int(minibatch), int(batch_begin), int(batch_end), _addr(sample_ids),
+                              _addr(order), _addr(seg_start), _addr(seg_end)))
+
+
+def std_predict(ctx, k: int, coords, out) -> None:
+    _check(lib().std_predict(ctx, int(k), _addr(coords), _addr(out)))
+
+
+def std_rmse(ctx, k: int, coords, values):
+    r = ctypes.c_double()
+    a = ctypes.c_double()
+    _check(lib().std_rmse(ctx, int(k), _addr(coords), _addr(values), ctypes.byref(r), ctypes.byref(a)))
+    return r.value, a.value
+
+
+def std_get_params(ctx, A=None, B=None, core=None):
+    """Fill the given buffers (lists of arrays / tensors, or None); returns the epoch counter."""
+    ep = ctypes.c_int64()
+    Ap = _ptr_array(A) if A is not None else None
+    Bp = _ptr_array(B) if B is not None else None
+    _check(lib().std_get_params(ctx, Ap, Bp, _addr(core), ctypes.byref(ep)))
+    return ep.value
+
+
+def std_set_params(ctx, A=None, B=None, epoch: int = -1) -> None:
+    Ap = _ptr_array(A) if A is not None else None
+    Bp = _ptr_array(B) if B is not None else None
+    _check(lib().std_set_params(ctx, Ap, Bp, int(epoch)))
+
+
+class Tucker:
+    """Owning wrapper of one context (host-pointer or device-pointer mode)."""
+
+    def __init__(self, shape, ranks, coords, values, r_core=5, ptr_kind=0, **opts):
+        o = std_default_options()
+        o.r_core = int(r_core)
+        o.ptr_kind = int(ptr_kind)
+        for k, v in opts.items():
+            setattr(o, k, v)
+        self.shape = tuple(int(s) for s in shape)
+        self.ranks = tuple(int(j) for j in ranks)
+        self.R = int(r_core)
+        self.N = len(self.shape)
+        self.ptr_kind = int(ptr_kind)
+        if ptr_kind == 0:
+            coords = np.ascontiguousarray(coords, dtype=np.int32)
+            values = np.ascontiguousarray(values, dtype=np.float32)
+        self.nnz = int(coords.shape[0])
+        self.ctx = std_create(self.N, self.shape, self.ranks, self.nnz, coords, values, o)
+
+    def close(self):
+        if self.ctx is not None:
+            std_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def epoch(self, lr_a, lr_b, lam_a, lam_b, minibatch):
+        return std_sgd_epoch(self.ctx, lr_a, lr_b, lam_a, lam_b, minibatch)
+
+    def batches(self, lr_a, lr_b, lam_a, lam_b, minibatch, b0, b1, probe=False):
+        if not probe:
+            std_sgd_batches(self.ctx, lr_a, lr_b, lam_a, lam_b, minibatch, b0, b1)
+            return None
+        pr = dict(core_V=np.zeros((self.N, self.R, STD_MAX_RANK), np.float32),
+                  factor_F=np.zeros((self.N, minibatch, STD_MAX_RANK), np.float32),
+                  nseg=np.zeros(self.N, np.int64))
+        std_sgd_batches(self.ctx, lr_a, lr_b, lam_a, lam_b, minibatch, b0, b1, pr)
+        return pr
+
+    def schedule(self, minibatch, b0, b1):
+        t0 = b0 * minibatch
+        t1 = min(b1 * minibatch, self.nnz)
+        cnt = max(0, t1 - t0)
+        sid = np.zeros(cnt, np.int32)
+        order = np.zeros((self.N, cnt), np.int32)
+        s0 = np.zeros((self.N, cnt), np.int32)
+        s1 = np.zeros((self.N, cnt), np.int32)
+        std_schedule(self.ctx, minibatch, b0, b1, sid, order, s0, s1)
+        return sid, order, s0, s1
+
+    def predict(self, coords):
+        coords = np.ascontiguousarray(coords, dtype=np.int32)
+        out = np.zeros(coords.shape[0], np.float32)
+        std_predict(self.ctx, coords.shape[0], coords, out)
+        return out
+
+    def rmse(self, coords, values):
+        coords = np.ascontiguousarray(coords, dtype=np.int32)
+        values = np.ascontiguousarray(values, dtype=np.float32)
+        return std_rmse(self.ctx, coords.shape[0], coords, values)
+
+    def get_params(self):
+        A = [np.zeros((I, J), np.float32) for I, J in zip(self.shape, self.ranks)]
+        B = [np.zeros((J, self.R), np.float32) for J in self.ranks]
+        core = np.zeros(int(np.prod(self.ranks)), np.float32)
+        ep = std_get_params(self.ctx, A, B, core)
+        return A, B, core, ep
+
+    def set_params(self, A=None, B=None, epoch=-1):
+        A = [np.ascontiguousarray(a, dtype=np.float32) for a in A] if A is not None else None
+        B = [np.ascontiguousarray(b, dtype=np.float32) for b in B] if B is not None else None
+        std_set_params(self.ctx, A, B, epoch)

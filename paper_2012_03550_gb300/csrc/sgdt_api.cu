@@ -1,0 +1,669 @@
+// Host side of the C ABI declared in include/sgd_tucker.h: argument checks,
+// device memory of a context, and the launch sequence of each call.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "sgdt_internal.cuh"
+
+using namespace sgdt;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+int set_error(int code, const std::string& msg) {
+  g_last_error = msg;
+  return code;
+}
+
+int cuda_error(cudaError_t e, const char* what) {
+  if (e == cudaErrorMemoryAllocation) {
+    cudaGetLastError();
+    return set_error(STD_ENOMEM, std::string(what) + ": " + cudaGetErrorString(e));
+  }
+  return set_error(STD_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define STD_CUDA(call, what)                       \
+  do {                                             \
+    cudaError_t e_ = (call);                       \
+    if (e_ != cudaSuccess) return cuda_error(e_, what); \
+  } while (0)
+
+}  // namespace
+
+struct std_ctx {
+  Geometry g{};
+  std_options opt{};
+  cudaStream_t stream = nullptr;
+  int sms = 0;
+  int64_t nnz = 0;
+  int cs = 0;                       // 32-bit words per packed COO record
+  uint32_t* coo = nullptr;
+  float* A[kMaxN] = {};
+  float* B = nullptr;
+  float* core = nullptr;
+  int* err = nullptr;
+  unsigned long long* bar = nullptr;
+  // schedule of the current epoch
+  Schedule sched{};
+  void* sched_mem = nullptr;
+  size_t sched_bytes = 0;
+  int64_t sched_epoch = -1;
+  int sched_M = 0;
+  // epoch scratch
+  float* part = nullptr;
+  size_t part_floats = 0;
+  float* red = nullptr;
+  size_t red_floats = 0;
+  float* bpart = nullptr;
+  unsigned* bcnt = nullptr;
+  int scratch_ctas = 0;
+  // probe
+  float* probe_mem = nullptr;
+  size_t probe_floats = 0;
+  // staging for host inputs of predict / rmse
+  void* stage = nullptr;
+  size_t stage_bytes = 0;
+  double* rpart = nullptr;
+  int rpart_blocks = 0;
+  double* result = nullptr;
+  int64_t epoch = 0;
+  size_t allocated = 0;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+};
+
+namespace {
+
+int dev_alloc(std_ctx* c, void** p, size_t bytes, const char* what) {
+  *p = nullptr;
+  if (bytes == 0) bytes = 16;
+  if (c->opt.hbm_budget_bytes && c->allocated + bytes > c->opt.hbm_budget_bytes)
+    return set_error(STD_ENOMEM, std::string(what) + ": HBM budget exceeded");
+  cudaError_t e = cudaMalloc(p, bytes);
+  if (e != cudaSuccess) {
+    *p = nullptr;
+    return cuda_error(e, what);
+  }
+  c->allocated += bytes;
+  return STD_OK;
+}
+
+void dev_free(std_ctx* c, void* p, size_t bytes) {
+  if (p) {
+    cudaFree(p);
+    c->allocated -= (bytes == 0 ? 16 : bytes);
+  }
+}
+
+int read_err(std_ctx* c, const char* what) {
+  int h = 0;
+  STD_CUDA(cudaMemcpyAsync(&h, c->err, sizeof(int), cudaMemcpyDeviceToHost, c->stream), what);
+  STD_CUDA(cudaStreamSynchronize(c->stream), what);
+  if (h != 0) {
+    STD_CUDA(cudaMemsetAsync(c->err, 0, sizeof(int), c->stream), what);
+    STD_CUDA(cudaStreamSynchronize(c->stream), what);
+    if (h == STD_EINVAL) return set_error(STD_EINVAL, std::string(what) + ": coordinate outside [0, I_n)");
+    if (h == STD_ETIMEOUT) return set_error(STD_ETIMEOUT, std::string(what) + ": grid barrier watchdog expired");
+    return set_error(h, std::string(what) + ": device error");
+  }
+  return STD_OK;
+}
+
+int ensure_stage(std_ctx* c, size_t bytes) {
+  if (bytes <= c->stage_bytes) return STD_OK;
+  dev_free(c, c->stage, c->stage_bytes);
+  c->stage = nullptr;
+  c->stage_bytes = 0;
+  int rc = dev_alloc(c, &c->stage, bytes, "staging buffer");
+  if (rc) return rc;
+  c->stage_bytes = bytes;
+  return STD_OK;
+}
+
+int payload_floats(const Geometry& g) {
+  int mx = 0;
+  for (int n = 0; n < g.N; ++n) {
+    const int Jn = g.J[n];
+    const int P = g.R * Jn + (g.R * (g.R - 1) / 2) * (Jn * (Jn + 1) / 2);
+    if (P > mx) mx = P;
+  }
+  return mx;
+}
+
+int ensure_schedule(std_ctx* c, int M) {
+  if (c->sched_mem && c->sched_M == M && c->sched_epoch == c->epoch) return STD_OK;
+  const int N = c->g.N;
+  const int64_t nb = (c->nnz + M - 1) / M;
+  const int64_t npad = nb * M;
+  const size_t words = (size_t)npad * ((size_t)N * (N + 3) + 1);
+  const size_t bytes = words * 4;
+  if (bytes > c->sched_bytes) {
+    dev_free(c, c->sched_mem, c->sched_bytes);
+    c->sched_mem = nullptr;
+    c->sched_bytes = 0;
+    int rc = dev_alloc(c, &c->sched_mem, bytes, "epoch schedule");
+    if (rc) return rc;
+    c->sched_bytes = bytes;
+  }
+  int32_t* base = static_cast<int32_t*>(c->sched_mem);
+  Schedule s{};
+  s.crd = base;
+  s.val = reinterpret_cast<float*>(base + (size_t)npad * N * N);
+  s.pos = base + (size_t)npad * (N * N + N);
+  s.seg = reinterpret_cast<uint32_t*>(base + (size_t)npad * (N * N + 2 * N));
+  s.sid = base + (size_t)npad * (N * N + 3 * N);
+  s.npad = npad;
+  s.n = c->nnz;
+  s.M = M;
+  const Feistel f = make_feistel((uint64_t)c->nnz, c->opt.seed_sched, (uint64_t)c->epoch);
+  STD_CUDA(launch_schedule(c->g, c->coo, c->cs, f, s, 0, nb, c->stream), "sampler/tiler launch");
+  c->sched = s;
+  c->sched_M = M;
+  c->sched_epoch = c->epoch;
+  return STD_OK;
+}
+
+int choose_ctas(std_ctx* c, int M, int* ctas, int* chunk_max, size_t* smem) {
+  const int payload = payload_floats(c->g);
+  if (payload > kMaxCorePayload)
+    return set_error(STD_EUNSUPPORTED, "core reduction payload R*J + R(R-1)/2*J(J+1)/2 exceeds 8192 floats");
+  int G = c->opt.ctas;
+  if (G <= 0) {
+    G = (M + 15) / 16;
+    if (G > c->sms) G = c->sms;
+    const int need = (M + kMaxChunk - 1) / kMaxChunk;
+    if (G < need) G = need;
+  }
+  if (G < 1) G = 1;
+  int ch = (M + G - 1) / G;
+  if (ch > kMaxChunk) return set_error(STD_EUNSUPPORTED, "minibatch too large for the chosen CTA count");
+  size_t sm = epoch_smem_bytes(c->g, ch, payload);
+  if (sm > 227 * 1024) return set_error(STD_EUNSUPPORTED, "shape needs more shared memory than a CTA has");
+  STD_CUDA(epoch_kernel_setup(sm), "epoch kernel attributes");
+  const int maxG = epoch_max_ctas(sm);
+  if (maxG < 1) return set_error(STD_EUNSUPPORTED, "epoch kernel cannot be resident");
+  if (G > maxG) {
+    if (c->opt.ctas > 0) return set_error(STD_EINVAL, "requested CTA count exceeds co-resident capacity");
+    G = maxG;
+    ch = (M + G - 1) / G;
+    if (ch > kMaxChunk) return set_error(STD_EUNSUPPORTED, "minibatch too large for the co-resident CTAs");
+    sm = epoch_smem_bytes(c->g, ch, payload);
+  }
+  *ctas = G;
+  *chunk_max = ch;
+  *smem = sm;
+  return STD_OK;
+}
+
+int ensure_scratch(std_ctx* c, int G, int payload) {
+  const size_t pf = (size_t)G * payload;
+  if (pf > c->part_floats) {
+    dev_free(c, c->part, c->part_floats * 4);
+    c->part = nullptr;
+    c->part_floats = 0;
+    int rc = dev_alloc(c, (void**)&c->part, pf * 4, "core partials");
+    if (rc) return rc;
+    c->part_floats = pf;
+  }
+  if ((size_t)payload > c->red_floats) {
+    dev_free(c, c->red, c->red_floats * 4);
+    c->red = nullptr;
+    c->red_floats = 0;
+    int rc = dev_alloc(c, (void**)&c->red, (size_t)payload * 4, "core reduction");
+    if (rc) return rc;
+    c->red_floats = payload;
+  }
+  if (G > c->scratch_ctas) {
+    dev_free(c, c->bpart, (size_t)c->scratch_ctas * 2 * kMaxJ * 4);
+    dev_free(c, c->bcnt, (size_t)c->scratch_ctas * 4);
+    c->bpart = nullptr;
+    c->bcnt = nullptr;
+    c->scratch_ctas = 0;
+    int rc = dev_alloc(c, (void**)&c->bpart, (size_t)G * 2 * kMaxJ * 4, "run pieces");
+    if (rc) return rc;
+    rc = dev_alloc(c, (void**)&c->bcnt, (size_t)G * 4, "run counters");
+    if (rc) return rc;
+    c->scratch_ctas = G;
+  }
+  return STD_OK;
+}
+
+int check_hyper(float lr_a, float lr_b, float lam_a, float lam_b, int32_t M) {
+  if (!(std::isfinite(lr_a) && std::isfinite(lr_b) && std::isfinite(lam_a) && std::isfinite(lam_b)))
+    return set_error(STD_EINVAL, "learning rates and lambdas must be finite");
+  if (M < 1) return set_error(STD_EINVAL, "minibatch must be >= 1");
+  if (M > STD_MAX_MINIBATCH) return set_error(STD_EUNSUPPORTED, "minibatch exceeds STD_MAX_MINIBATCH");
+  return STD_OK;
+}
+
+// Runs minibatches [b0, b1) of the current schedule.  With record_end, ev1
+// is recorded on the stream right after the kernel (the caller records ev0).
+int run_batches(std_ctx* c, float lr_a, float lr_b, float lam_a, float lam_b, int32_t M, int64_t b0, int64_t b1,
+                bool probe, bool record_end) {
+  int rc = ensure_schedule(c, M);
+  if (rc) return rc;
+  int G = 0, chunk = 0;
+  size_t smem = 0;
+  rc = choose_ctas(c, M, &G, &chunk, &smem);
+  if (rc) return rc;
+  const int payload = payload_floats(c->g);
+  rc = ensure_scratch(c, G, payload);
+  if (rc) return rc;
+  float* pV = nullptr;
+  float* pF = nullptr;
+  if (probe) {
+    const size_t need = (size_t)c->g.N * c->g.R * kMaxJ + (size_t)c->g.N * M * kMaxJ;
+    if (need > c->probe_floats) {
+      dev_free(c, c->probe_mem, c->probe_floats * 4);
+      c->probe_mem = nullptr;
+      c->probe_floats = 0;
+      rc = dev_alloc(c, (void**)&c->probe_mem, need * 4, "gradient probe");
+      if (rc) return rc;
+      c->probe_floats = need;
+    }
+    STD_CUDA(cudaMemsetAsync(c->probe_mem, 0, need * 4, c->stream), "probe clear");
+    pV = c->probe_mem;
+    pF = c->probe_mem + (size_t)c->g.N * c->g.R * kMaxJ;
+  }
+  EpochArgs a{};
+  a.g = c->g;
+  for (int n = 0; n < c->g.N; ++n) a.A[n] = c->A[n];
+  a.B = c->B;
+  a.core = c->core;
+  a.s = c->sched;
+  a.b0 = b0;
+  a.b1 = b1;
+  a.lr_a = lr_a;
+  a.lr_b = lr_b;
+  a.lam_a = lam_a;
+  a.lam_b = lam_b;
+  a.norm_mode = c->opt.norm_mode;
+  a.chunk_max = chunk;
+  a.payload_max = payload;
+  a.part = c->part;
+  a.red = c->red;
+  a.bpart = c->bpart;
+  a.bcnt = c->bcnt;
+  a.bar = c->bar;
+  a.err = c->err;
+  a.watchdog_ns = c->opt.watchdog_ns ? c->opt.watchdog_ns : 2000000000ULL;
+  a.probe_batch = probe ? b0 : -1;
+  a.probeV = pV;
+  a.probeF = pF;
+  STD_CUDA(cudaMemsetAsync(c->bcnt, 0, (size_t)G * 4, c->stream), "run counters clear");
+  STD_CUDA(cudaMemsetAsync(c->bar, 0, sizeof(unsigned long long), c->stream), "barrier clear");
+  if (b1 > b0) STD_CUDA(launch_epoch(a, G, smem, c->stream), "epoch kernel launch");
+  if (record_end) STD_CUDA(cudaEventRecord(c->ev1, c->stream), "event");
+  return read_err(c, "epoch kernel");
+}
+
+const int32_t* stage_coords(std_ctx* c, const int32_t* coords, const float* values, int64_t k,
+                            const float** dvalues, int* rc) {
+  *rc = STD_OK;
+  *dvalues = values;
+  if (c->opt.ptr_kind == 1) return coords;
+  const size_t cb = (size_t)k * c->g.N * 4;
+  const size_t vb = values ? (size_t)k * 4 : 0;
+  *rc = ensure_stage(c, cb + vb + 16);
+  if (*rc) return nullptr;
+  int32_t* dc = static_cast<int32_t*>(c->stage);
+  cudaError_t e = cudaMemcpyAsync(dc, coords, cb, cudaMemcpyDefault, c->stream);
+  if (e == cudaSuccess && values) {
+    float* dv = reinterpret_cast<float*>(dc + (size_t)k * c->g.N);
+    e = cudaMemcpyAsync(dv, values, vb, cudaMemcpyDefault, c->stream);
+    *dvalues = dv;
+  }
+  if (e != cudaSuccess) {
+    *rc = cuda_error(e, "staging copy");
+    return nullptr;
+  }
+  return dc;
+}
+
+}  // namespace
+
+extern "C" {
+
+void std_default_options(std_options* opt) {
+  if (!opt) return;
+  std::memset(opt, 0, sizeof(*opt));
+  opt->r_core = 5;
+  opt->precision = 0;
+  opt->norm_mode = 0;
+  opt->init_mode = 1;
+  opt->init_mu = 0.5;
+  opt->init_sigma = 0.1;
+  opt->seed_init = 1;
+  opt->seed_sched = 2;
+  opt->ptr_kind = 0;
+  opt->ctas = 0;
+  opt->stream = nullptr;
+  opt->watchdog_ns = 0;
+  opt->hbm_budget_bytes = 0;
+}
+
+const char* std_last_error(void) { return g_last_error.c_str(); }
+
+int std_destroy(std_ctx* c) {
+  if (!c) return STD_OK;
+  cudaStreamSynchronize(c->stream);
+  for (int n = 0; n < kMaxN; ++n)
+    if (c->A[n]) cudaFree(c->A[n]);
+  void* ptrs[] = {c->coo, c->B, c->core, c->err, c->bar, c->sched_mem, c->part, c->red,
+                  c->bpart, c->bcnt, c->probe_mem, c->stage, c->rpart, c->result};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  if (c->ev0) cudaEventDestroy(c->ev0);
+  if (c->ev1) cudaEventDestroy(c->ev1);
+  delete c;
+  return STD_OK;
+}
+
+int std_create(std_ctx** out, int32_t order, const int64_t* mode_sizes, const int32_t* ranks, int64_t nnz,
+               const int32_t* indices, const float* values, const std_options* opt_in) {
+  if (!out) return set_error(STD_EINVAL, "out is NULL");
+  *out = nullptr;
+  std_options opt;
+  std_default_options(&opt);
+  if (opt_in) opt = *opt_in;
+  if (order < 2) return set_error(STD_EINVAL, "order must be >= 2");
+  if (order > STD_MAX_ORDER) return set_error(STD_EUNSUPPORTED, "order exceeds STD_MAX_ORDER");
+  if (!mode_sizes || !ranks || !indices || !values) return set_error(STD_EINVAL, "NULL array argument");
+  if (nnz < 1 || nnz >= 2147483647LL) return set_error(STD_EINVAL, "nnz must be in [1, 2^31 - 1)");
+  if (opt.r_core < 1) return set_error(STD_EINVAL, "r_core must be >= 1");
+  if (opt.r_core > STD_MAX_RANK) return set_error(STD_EUNSUPPORTED, "r_core exceeds STD_MAX_RANK");
+  if (opt.precision != 0 && opt.precision != 1) return set_error(STD_EINVAL, "precision must be 0 or 1");
+  if (opt.precision == 1) return set_error(STD_EUNSUPPORTED, "BF16 storage is not built into this library");
+  if (opt.norm_mode != 0 && opt.norm_mode != 1) return set_error(STD_EINVAL, "norm_mode must be 0 or 1");
+  if (opt.init_mode != 0 && opt.init_mode != 1) return set_error(STD_EINVAL, "init_mode must be 0 or 1");
+  if (opt.ptr_kind != 0 && opt.ptr_kind != 1) return set_error(STD_EINVAL, "ptr_kind must be 0 or 1");
+  if (opt.ctas < 0) return set_error(STD_EINVAL, "ctas must be >= 0");
+  Geometry g{};
+  g.N = order;
+  g.R = opt.r_core;
+  int64_t prodJ = 1;
+  int sumJ = 0, Jmax = 0, boff = 0;
+  for (int n = 0; n < order; ++n) {
+    if (mode_sizes[n] < 1 || mode_sizes[n] >= 2147483647LL) return set_error(STD_EINVAL, "mode size out of range");
+    if (ranks[n] < 1) return set_error(STD_EINVAL, "rank must be >= 1");
+    if (ranks[n] > STD_MAX_RANK) return set_error(STD_EUNSUPPORTED, "rank exceeds STD_MAX_RANK");
+    g.I[n] = mode_sizes[n];
+    g.J[n] = ranks[n];
+    g.Jp[n] = (ranks[n] + 3) & ~3;
+    g.boff[n] = boff;
+    boff += ranks[n] * g.R;
+    g.joff[n] = sumJ;
+    sumJ += ranks[n];
+    g.gstride[n] = (int)prodJ;
+    prodJ *= ranks[n];
+    if (ranks[n] > Jmax) Jmax = ranks[n];
+    if (prodJ > STD_MAX_CORE) return set_error(STD_EUNSUPPORTED, "prod J_n exceeds STD_MAX_CORE");
+  }
+  g.sumJ = sumJ;
+  g.prodJ = (int)prodJ;
+  g.Jmax = Jmax;
+
+  std_ctx* c = new std_ctx();
+  c->g = g;
+  c->opt = opt;
+  c->stream = static_cast<cudaStream_t>(opt.stream);
+  c->nnz = nnz;
+  c->cs = (order + 1 <= 4) ? 4 : 8;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) {
+    int rc = cuda_error(e, "device query");
+    delete c;
+    return rc;
+  }
+  int rc = STD_OK;
+#define TRY(x)                 \
+  do {                         \
+    rc = (x);                  \
+    if (rc) {                  \
+      std_destroy(c);          \
+      return rc;               \
+    }                          \
+  } while (0)
+  TRY(cudaEventCreate(&c->ev0) == cudaSuccess ? STD_OK : cuda_error(cudaGetLastError(), "event create"));
+  TRY(cudaEventCreate(&c->ev1) == cudaSuccess ? STD_OK : cuda_error(cudaGetLastError(), "event create"));
+  TRY(dev_alloc(c, (void**)&c->err, 16, "error word"));
+  TRY(dev_alloc(c, (void**)&c->bar, 16, "barrier word"));
+  TRY(dev_alloc(c, (void**)&c->result, 16, "result"));
+  TRY(dev_alloc(c, (void**)&c->coo, (size_t)nnz * c->cs * 4, "COO"));
+  for (int n = 0; n < order; ++n) TRY(dev_alloc(c, (void**)&c->A[n], (size_t)g.I[n] * g.Jp[n] * 4, "factor matrix"));
+  TRY(dev_alloc(c, (void**)&c->B, (size_t)boff * 4, "Kruskal matrices"));
+  TRY(dev_alloc(c, (void**)&c->core, (size_t)g.prodJ * 4, "core"));
+  TRY(cudaMemsetAsync(c->err, 0, 16, c->stream) == cudaSuccess ? STD_OK : cuda_error(cudaGetLastError(), "memset"));
+  const int32_t* dcoords = indices;
+  const float* dvalues = values;
+  if (opt.ptr_kind == 0) {
+    TRY(ensure_stage(c, (size_t)nnz * (order + 1) * 4 + 16));
+    int32_t* sc = static_cast<int32_t*>(c->stage);
+    float* sv = reinterpret_cast<float*>(sc + (size_t)nnz * order);
+    e = cudaMemcpyAsync(sc, indices, (size_t)nnz * order * 4, cudaMemcpyDefault, c->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(sv, values, (size_t)nnz * 4, cudaMemcpyDefault, c->stream);
+    TRY(e == cudaSuccess ? STD_OK : cuda_error(e, "COO upload"));
+    dcoords = sc;
+    dvalues = sv;
+  }
+  e = launch_pack_coo(g, dcoords, dvalues, nnz, c->coo, c->cs, c->err, c->stream);
+  TRY(e == cudaSuccess ? STD_OK : cuda_error(e, "COO pack"));
+  e = launch_init_params(g, c->A, c->B, opt.init_mode, opt.init_mu, opt.init_sigma, opt.seed_init, c->stream);
+  TRY(e == cudaSuccess ? STD_OK : cuda_error(e, "parameter init"));
+  e = launch_build_core(g, c->B, c->core, c->stream);
+  TRY(e == cudaSuccess ? STD_OK : cuda_error(e, "core build"));
+  TRY(read_err(c, "std_create"));
+  if (opt.ptr_kind == 0) {
+    // the staging buffer held the whole COO; give it back
+    dev_free(c, c->stage, c->stage_bytes);
+    c->stage = nullptr;
+    c->stage_bytes = 0;
+  }
+#undef TRY
+  *out = c;
+  return STD_OK;
+}
+
+int std_sgd_epoch(std_ctx* c, float lr_a, float lr_b, float lambda_a, float lambda_b, int32_t minibatch,
+                  std_epoch_stats* out) {
+  if (!c) return set_error(STD_EINVAL, "context is NULL");
+  int rc = check_hyper(lr_a, lr_b, lambda_a, lambda_b, minibatch);
+  if (rc) return rc;
+  const int64_t nb = (c->nnz + minibatch - 1) / minibatch;
+  // the epoch time covers the sampler/tiler and the update kernel
+  STD_CUDA(cudaEventRecord(c->ev0, c->stream), "event");
+  rc = ensure_schedule(c, minibatch);
+  if (!rc) rc = run_batches(c, lr_a, lr_b, lambda_a, lambda_b, minibatch, 0, nb, false, true);
+  if (rc) return rc;
+  float ms = 0.f;
+  STD_CUDA(cudaEventElapsedTime(&ms, c->ev0, c->ev1), "event time");
+  if (out) {
+    out->seconds = ms * 1e-3;
+    out->nnz = c->nnz;
+    out->batches = nb;
+    out->nnz_per_s = ms > 0.f ? (double)c->nnz / (ms * 1e-3) : 0.0;
+    out->epoch = c->epoch;
+  }
+  c->epoch += 1;
+  return STD_OK;
+}
+
+int std_sgd_batches(std_ctx* c, float lr_a, float lr_b, float lambda_a, float lambda_b, int32_t minibatch,
+                    int64_t batch_begin, int64_t batch_end, std_probe* probe) {
+  if (!c) return set_error(STD_EINVAL, "context is NULL");
+  int rc = check_hyper(lr_a, lr_b, lambda_a, lambda_b, minibatch);
+  if (rc) return rc;
+  const int64_t nb = (c->nnz + minibatch - 1) / minibatch;
+  if (batch_begin < 0 || batch_end > nb || batch_begin > batch_end)
+    return set_error(STD_EINVAL, "batch range outside the epoch");
+  const bool want = probe && (probe->core_V || probe->factor_F || probe->nseg) && batch_end > batch_begin;
+  rc = run_batches(c, lr_a, lr_b, lambda_a, lambda_b, minibatch, batch_begin, batch_end, want, false);
+  if (rc || !want) return rc;
+  const int N = c->g.N, R = c->g.R, M = minibatch;
+  const int64_t t0 = batch_begin * (int64_t)M;
+  const int m = (int)((c->nnz - t0) < M ? (c->nnz - t0) : M);
+  std::vector<float> hv((size_t)N * R * kMaxJ), hf((size_t)N * M * kMaxJ);
+  std::vector<uint32_t> seg((size_t)m);
+  STD_CUDA(cudaMemcpy(hv.data(), c->probe_mem, hv.size() * 4, cudaMemcpyDeviceToHost), "probe copy");
+  STD_CUDA(cudaMemcpy(hf.data(), c->probe_mem + hv.size(), hf.size() * 4, cudaMemcpyDeviceToHost), "probe copy");
+  if (probe->core_V) std::memcpy(probe->core_V, hv.data(), hv.size() * 4);
+  for (int n = 0; n < N; ++n) {
+    STD_CUDA(cudaMemcpy(seg.data(), c->sched.seg + (size_t)n * c->sched.npad + t0, (size_t)m * 4,
+                        cudaMemcpyDeviceToHost), "segment copy");
+    int64_t u = 0;
+    for (int q = 0; q < m; ++q) {
+      const int st = (int)(seg[q] & 0xffffu);
+      if (st != q) continue;
+      if (probe->factor_F)
+        std::memcpy(probe->factor_F + ((size_t)n * M + u) * kMaxJ, hf.data() + ((size_t)n * M + q) * kMaxJ,
+                    kMaxJ * 4);
+      ++u;
+    }
+    if (probe->factor_F)
+      for (int64_t v = u; v < M; ++v) std::memset(probe->factor_F + ((size_t)n * M + v) * kMaxJ, 0, kMaxJ * 4);
+    if (probe->nseg) probe->nseg[n] = u;
+  }
+  return STD_OK;
+}
+
+int std_schedule(std_ctx* c, int32_t minibatch, int64_t batch_begin, int64_t batch_end, int32_t* sample_ids,
+                 int32_t* order, int32_t* seg_start, int32_t* seg_end) {
+  if (!c) return set_error(STD_EINVAL, "context is NULL");
+  if (minibatch < 1) return set_error(STD_EINVAL, "minibatch must be >= 1");
+  if (minibatch > STD_MAX_MINIBATCH) return set_error(STD_EUNSUPPORTED, "minibatch exceeds STD_MAX_MINIBATCH");
+  const int64_t nb = (c->nnz + minibatch - 1) / minibatch;
+  if (batch_begin < 0 || batch_end > nb || batch_begin > batch_end)
+    return set_error(STD_EINVAL, "batch range outside the epoch");
+  int rc = ensure_schedule(c, minibatch);
+  if (rc) return rc;
+  const int64_t t0 = batch_begin * (int64_t)minibatch;
+  int64_t t1 = batch_end * (int64_t)minibatch;
+  if (t1 > c->nnz) t1 = c->nnz;
+  const int64_t cnt = t1 - t0;
+  if (cnt <= 0) return STD_OK;
+  const int N = c->g.N;
+  if (sample_ids)
+    STD_CUDA(cudaMemcpy(sample_ids, c->sched.sid + t0, (size_t)cnt * 4, cudaMemcpyDefault), "schedule copy");
+  std::vector<uint32_t> seg;
+  for (int n = 0; n < N; ++n) {
+    if (order)
+      STD_CUDA(cudaMemcpy(order + (size_t)n * cnt, c->sched.pos + (size_t)n * c->sched.npad + t0, (size_t)cnt * 4,
+                          cudaMemcpyDefault), "schedule copy");
+    if (seg_start || seg_end) {
+      seg.resize((size_t)cnt);
+      STD_CUDA(cudaMemcpy(seg.data(), c->sched.seg + (size_t)n * c->sched.npad + t0, (size_t)cnt * 4,
+                          cudaMemcpyDeviceToHost), "schedule copy");
+      for (int64_t q = 0; q < cnt; ++q) {
+        if (seg_start) seg_start[(size_t)n * cnt + q] = (int32_t)(seg[q] & 0xffffu);
+        if (seg_end) seg_end[(size_t)n * cnt + q] = (int32_t)(seg[q] >> 16);
+      }
+    }
+  }
+  return STD_OK;
+}
+
+int std_predict(std_ctx* c, int64_t k, const int32_t* coords, float* out) {
+  if (!c) return set_error(STD_EINVAL, "context is NULL");
+  if (k < 0) return set_error(STD_EINVAL, "k must be >= 0");
+  if (k == 0) return STD_OK;
+  if (!coords || !out) return set_error(STD_EINVAL, "NULL array argument");
+  const int32_t* dc = coords;
+  float* dout = out;
+  if (c->opt.ptr_kind == 0) {
+    const size_t cb = (size_t)k * c->g.N * 4;
+    int rc = ensure_stage(c, cb + (size_t)k * 4 + 16);
+    if (rc) return rc;
+    int32_t* sc = static_cast<int32_t*>(c->stage);
+    STD_CUDA(cudaMemcpyAsync(sc, coords, cb, cudaMemcpyDefault, c->stream), "predict staging");
+    dc = sc;
+    dout = reinterpret_cast<float*>(sc + (size_t)k * c->g.N);
+  }
+  AParams A{};
+  for (int n = 0; n < c->g.N; ++n) A.A[n] = c->A[n];
+  STD_CUDA(launch_predict(c->g, A, c->B, dc, nullptr, k, dout, nullptr, predict_blocks(k), c->err, c->stream),
+           "predict launch");
+  if (c->opt.ptr_kind == 0)
+    STD_CUDA(cudaMemcpyAsync(out, dout, (size_t)k * 4, cudaMemcpyDefault, c->stream), "predict copy");
+  return read_err(c, "std_predict");
+}
+
+int std_rmse(std_ctx* c, int64_t k, const int32_t* coords, const float* values, double* rmse, double* mae) {
+  if (!c) return set_error(STD_EINVAL, "context is NULL");
+  if (k < 0 || !rmse) return set_error(STD_EINVAL, "bad arguments");
+  if (k == 0) {
+    *rmse = 0.0;
+    if (mae) *mae = 0.0;
+    return STD_OK;
+  }
+  if (!coords || !values) return set_error(STD_EINVAL, "NULL array argument");
+  int rc = STD_OK;
+  const float* dv = nullptr;
+  const int32_t* dc = stage_coords(c, coords, values, k, &dv, &rc);
+  if (rc) return rc;
+  const int blocks = predict_blocks(k);
+  if (blocks > c->rpart_blocks) {
+    dev_free(c, c->rpart, (size_t)c->rpart_blocks * 16);
+    c->rpart = nullptr;
+    c->rpart_blocks = 0;
+    rc = dev_alloc(c, (void**)&c->rpart, (size_t)blocks * 16, "rmse partials");
+    if (rc) return rc;
+    c->rpart_blocks = blocks;
+  }
+  AParams A{};
+  for (int n = 0; n < c->g.N; ++n) A.A[n] = c->A[n];
+  STD_CUDA(launch_predict(c->g, A, c->B, dc, dv, k, nullptr, c->rpart, blocks, c->err, c->stream), "rmse launch");
+  STD_CUDA(launch_rmse_finish(c->rpart, blocks, c->result, c->stream), "rmse finish");
+  double h[2] = {0.0, 0.0};
+  STD_CUDA(cudaMemcpyAsync(h, c->result, 16, cudaMemcpyDeviceToHost, c->stream), "rmse copy");
+  rc = read_err(c, "std_rmse");
+  if (rc) return rc;
+  if (!std::isfinite(h[0]) || !std::isfinite(h[1])) return set_error(STD_ENUMERIC, "std_rmse: NaN or Inf in the sums");
+  *rmse = std::sqrt(h[0] / (double)k);
+  if (mae) *mae = h[1] / (double)k;
+  return STD_OK;
+}
+
+int std_get_params(std_ctx* c, float* const* A, float* const* B, float* core, int64_t* epoch) {
+  if (!c) return set_error(STD_EINVAL, "context is NULL");
+  const Geometry& g = c->g;
+  for (int n = 0; n < g.N; ++n) {
+    if (A && A[n])
+      STD_CUDA(cudaMemcpy2DAsync(A[n], (size_t)g.J[n] * 4, c->A[n], (size_t)g.Jp[n] * 4, (size_t)g.J[n] * 4,
+                                 (size_t)g.I[n], cudaMemcpyDefault, c->stream), "get A");
+    if (B && B[n])
+      STD_CUDA(cudaMemcpyAsync(B[n], c->B + g.boff[n], (size_t)g.J[n] * g.R * 4, cudaMemcpyDefault, c->stream),
+               "get B");
+  }
+  if (core) {
+    STD_CUDA(launch_build_core(g, c->B, c->core, c->stream), "core build");
+    STD_CUDA(cudaMemcpyAsync(core, c->core, (size_t)g.prodJ * 4, cudaMemcpyDefault, c->stream), "get core");
+  }
+  STD_CUDA(cudaStreamSynchronize(c->stream), "get params sync");
+  if (epoch) *epoch = c->epoch;
+  return STD_OK;
+}
+
+int std_set_params(std_ctx* c, const float* const* A, const float* const* B, int64_t epoch) {
+  if (!c) return set_error(STD_EINVAL, "context is NULL");
+  const Geometry& g = c->g;
+  for (int n = 0; n < g.N; ++n) {
+    if (A && A[n])
+      STD_CUDA(cudaMemcpy2DAsync(c->A[n], (size_t)g.Jp[n] * 4, A[n], (size_t)g.J[n] * 4, (size_t)g.J[n] * 4,
+                                 (size_t)g.I[n], cudaMemcpyDefault, c->stream), "set A");
+    if (B && B[n])
+      STD_CUDA(cudaMemcpyAsync(c->B + g.boff[n], B[n], (size_t)g.J[n] * g.R * 4, cudaMemcpyDefault, c->stream),
+               "set B");
+  }
+  STD_CUDA(launch_build_core(g, c->B, c->core, c->stream), "core build");
+  STD_CUDA(cudaStreamSynchronize(c->stream), "set params sync");
+  if (epoch >= 0) c->epoch = epoch;
+  return STD_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,157 @@
+// Internal declarations of the GB300 SGD_Tucker library (not part of the ABI).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "sgd_tucker.h"
+
+namespace sgdt {
+
+constexpr int kMaxN = STD_MAX_ORDER;
+constexpr int kMaxJ = STD_MAX_RANK;
+constexpr int kEpochThreads = 256;
+constexpr int kScheduleThreads = 512;
+constexpr int kMaxChunk = 128;          // samples per CTA per phase in the epoch kernel
+constexpr int kMaxCorePayload = 8192;   // floats of the per-mode core reduction
+
+// ---------------------------------------------------------------------------
+// Minibatch sampler: keyed permutation pi_e of [0, n) used to visit the
+// training entries in epoch e.  Balanced Feistel network on 2h bits (Luby &
+// Rackoff), 2h the smallest even width with 2^(2h) >= n (h >= 1), six rounds
+// (L, R) -> (R, L ^ (F(R ^ K_i) & (2^h - 1))) with F the SplitMix64 output
+// function (Steele, Lea & Flood 2014) and K_i = F(seed + (8 e + i + 1) * 0x9E3779B97F4A7C15);
+// values >= n are re-encrypted until they fall in [0, n) (cycle walking,
+// Black & Rogaway 2002).  Integer-only, so host and device agree bit for bit.
+// ---------------------------------------------------------------------------
+struct Feistel {
+  uint64_t key[6];
+  uint64_t n;
+  int h;
+};
+
+__host__ __device__ __forceinline__ uint64_t splitmix_out(uint64_t z) {
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+  return z ^ (z >> 31);
+}
+
+inline Feistel make_feistel(uint64_t n, uint64_t seed, uint64_t epoch) {
+  Feistel f;
+  f.n = n;
+  int bits = 0;
+  if (n > 1) {
+    uint64_t v = n - 1;
+    while (v) { ++bits; v >>= 1; }
+  }
+  f.h = (bits + 1) / 2;
+  if (f.h < 1) f.h = 1;
+  for (int i = 0; i < 6; ++i)
+    f.key[i] = splitmix_out(seed + (8ULL * epoch + (uint64_t)i + 1ULL) * 0x9E3779B97F4A7C15ULL);
+  return f;
+}
+
+__host__ __device__ __forceinline__ uint64_t feistel_encrypt(const Feistel& f, uint64_t x) {
+  const uint64_t mask = (1ULL << f.h) - 1ULL;
+  uint64_t L = x >> f.h, R = x & mask;
+#pragma unroll
+  for (int i = 0; i < 6; ++i) {
+    uint64_t t = L ^ (splitmix_out(R ^ f.key[i]) & mask);
+    L = R;
+    R = t;
+  }
+  return (L << f.h) | R;
+}
+
+__host__ __device__ __forceinline__ uint64_t feistel_perm(const Feistel& f, uint64_t t) {
+  uint64_t y = feistel_encrypt(f, t);
+  while (y >= f.n) y = feistel_encrypt(f, y);
+  return y;
+}
+
+// ---------------------------------------------------------------------------
+// Geometry of a model shared by all kernels.
+// ---------------------------------------------------------------------------
+struct Geometry {
+  int N;
+  int R;
+  int J[kMaxN];
+  int Jp[kMaxN];        // row stride of the FP32 factor matrices (J_n rounded up to 4)
+  int boff[kMaxN];      // offset of B(n) (J_n x R, row-major) in the concatenated B
+  int joff[kMaxN];      // offset of mode n's row inside a sample's concatenated rows
+  int gstride[kMaxN];   // stride of j_n in G-hat (mode 1 fastest)
+  int sumJ;
+  int prodJ;
+  int Jmax;
+  int64_t I[kMaxN];
+};
+
+// Sorted per-mode copies of one epoch's minibatches (output of the tiler).
+// For mode n and epoch position t (minibatch b occupies [bM, bM+m)):
+//   coord(n, k, t) = crd[((size_t)n * N + k) * npad + t]
+//   val(n, t)      = val[(size_t)n * npad + t]
+//   pos(n, t)      = pos[(size_t)n * npad + t]        (batch position before sorting)
+//   seg(n, t)      = seg[(size_t)n * npad + t]        (run start | run end << 16, within the minibatch)
+// and sid[t] the training-entry index pi_e(t).
+struct Schedule {
+  int32_t* crd;
+  float* val;
+  int32_t* pos;
+  uint32_t* seg;
+  int32_t* sid;
+  int64_t npad;
+  int64_t n;
+  int M;
+};
+
+struct EpochArgs {
+  Geometry g;
+  float* A[kMaxN];       // FP32 factor masters, I_n x Jp_n
+  float* B;              // concatenated Kruskal matrices (read at start, written at end)
+  float* core;           // G-hat output (prod J), written at end
+  Schedule s;
+  int64_t b0, b1;        // minibatch range
+  float lr_a, lr_b, lam_a, lam_b;
+  int norm_mode;
+  int chunk_max;
+  int payload_max;       // floats per CTA partial
+  // scratch
+  float* part;           // [G][payload_max]
+  float* red;            // [payload_max]
+  float* bpart;          // [G][2][kMaxJ]
+  unsigned* bcnt;        // [G]
+  unsigned long long* bar;
+  int* err;
+  unsigned long long watchdog_ns;
+  // probe
+  int64_t probe_batch;
+  float* probeV;         // [N][R][kMaxJ]
+  float* probeF;         // [N][M][kMaxJ], indexed by the run's first sorted position
+};
+
+// Factor-matrix pointers passed to kernels by value.
+struct AParams {
+  float* A[kMaxN];
+};
+
+// Launchers (host side, defined in the .cu files).
+cudaError_t launch_schedule(const Geometry& g, const uint32_t* coo, int cs, const Feistel& f,
+                            const Schedule& s, int64_t b0, int64_t b1, cudaStream_t st);
+size_t epoch_smem_bytes(const Geometry& g, int chunk_max, int payload_max);
+cudaError_t epoch_kernel_setup(size_t smem);
+int epoch_max_ctas(size_t smem);
+cudaError_t launch_epoch(const EpochArgs& a, int ctas, size_t smem, cudaStream_t st);
+cudaError_t launch_init_params(const Geometry& g, float* const* A, float* B, int mode, double mu,
+                               double sigma, uint64_t seed, cudaStream_t st);
+cudaError_t launch_check_coords(const Geometry& g, const int32_t* coords, int64_t k, int* err,
+                                cudaStream_t st);
+cudaError_t launch_pack_coo(const Geometry& g, const int32_t* coords, const float* values, int64_t k,
+                            uint32_t* coo, int cs, int* err, cudaStream_t st);
+cudaError_t launch_build_core(const Geometry& g, const float* B, float* core, cudaStream_t st);
+int predict_blocks(int64_t k);
+cudaError_t launch_predict(const Geometry& g, const AParams& A, const float* B, const int32_t* coords,
+                           const float* values, int64_t k, float* out, double* partials, int blocks,
+                           int* err, cudaStream_t st);
+cudaError_t launch_rmse_finish(const double* partials, int blocks, double* result, cudaStream_t st);
+
+}  // namespace sgdt

@@ -1,0 +1,271 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Bars: sampled indices, sort permutations and run boundaries bit-exact;
+one minibatch's core and factor gradients within 1e-5 relative in FP32,
+norm-wise over each mode's gradient (FP32 residuals x-hat - x lose relative
+accuracy when x-hat is close to x, so single small rows are held to a mixed
+relative/absolute bound instead); per-epoch train/test RMSE within 1e-3 absolute over
+10 epochs.  Parameters after a step are compared with a tolerance derived from
+FP32 rounding of the same arithmetic (1e-5 relative to the parameter scale).
+"""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def B():
+    import __graft_entry__ as ge
+    ge.build()
+    from paper_2012_03550_gb300 import binding
+    return binding
+
+
+@pytest.fixture(scope="module")
+def synth():
+    from paper_2012_03550_gb300 import synth as s
+    return s
+
+
+@pytest.fixture(scope="module")
+def cfg1(synth):
+    return synth.config1()
+
+
+def _gpu(B, shape, ranks, R, coords, vals, A0=None, B0=None, **opts):
+    t = B.Tucker(shape, ranks, coords, vals, r_core=R, **opts)
+    if A0 is not None:
+        t.set_params(A0, B0, epoch=0)
+    return t
+
+
+def _rel(a, b):
+    d = float(np.linalg.norm(np.asarray(a, np.float64) - np.asarray(b, np.float64)))
+    s = float(np.linalg.norm(np.asarray(b, np.float64)))
+    return d / s if s > 0 else d
+
+
+# ---------------------------------------------------------------------------
+# Sampler + tiler: bit-exact
+# ---------------------------------------------------------------------------
+
+def _check_schedule(B, gpu, coords, M, batches, seed=2, epoch=0):
+    n = coords.shape[0]
+    sid, order, s0, s1 = gpu.schedule(M, batches[0], batches[1])
+    t0 = batches[0] * M
+    ref = O.perm_range(n, seed, epoch, t0, sid.shape[0])
+    assert np.array_equal(sid.astype(np.int64), ref)
+    for b in range(batches[0], batches[1]):
+        lo, hi = b * M - t0, min((b + 1) * M, n) - t0
+        ids = ref[lo:hi]
+        for mode in range(coords.shape[1]):
+            keys = coords[ids, mode]
+            o_ref, seg = O.stable_order(keys)
+            assert np.array_equal(order[mode, lo:hi], o_ref)
+            st = np.repeat(seg[:-1], np.diff(seg))
+            en = np.repeat(seg[1:] - 1, np.diff(seg))
+            assert np.array_equal(s0[mode, lo:hi], st)
+            assert np.array_equal(s1[mode, lo:hi], en)
+
+
+def test_schedule_bitexact_uniform(B, cfg1):
+    c, v = cfg1.tensor.split("train")
+    with B.Tucker(cfg1.tensor.shape, cfg1.ranks, c, v, r_core=5) as g:
+        nb = (c.shape[0] + 255) // 256
+        _check_schedule(B, g, c, 256, (0, nb))
+
+
+@pytest.mark.parametrize("M", [1, 7, 4096, 8192])
+def test_schedule_bitexact_zipf_ragged(B, synth, M):
+    # rating-like, Zipf-hot rows (long runs), ragged last minibatch
+    t = synth.make_tensor((5000, 800, 60), 50_001, [("zipf", 1.1), ("zipf", 1.3), ("uniform",)],
+                          (4, 4, 4), 0.1, 0.0, seed=9)
+    c, v = t.split("train")
+    with B.Tucker(t.shape, (4, 4, 4), c, v, r_core=2) as g:
+        nb = (c.shape[0] + M - 1) // M
+        rng = (0, nb) if M >= 4096 else (nb - 3, nb)
+        _check_schedule(B, g, c, M, rng)
+
+
+# ---------------------------------------------------------------------------
+# Prediction and RMSE/MAE
+# ---------------------------------------------------------------------------
+
+def test_predict_and_rmse_parity(B, synth, cfg1):
+    c, v = cfg1.tensor.split("train")
+    tc, tv = cfg1.tensor.split("test")
+    A0, B0 = synth.init_params(cfg1.tensor.shape, cfg1.ranks, 5, mode="normal", seed=1)
+    with _gpu(B, cfg1.tensor.shape, cfg1.ranks, 5, c, v, A0, B0) as g:
+        ref = O.Model(cfg1.tensor.shape, cfg1.ranks, 5, A0, B0)
+        got = g.predict(tc)
+        want = ref.predict(tc)
+        np.testing.assert_allclose(got, want, rtol=2e-5, atol=2e-6 * np.abs(want).max())
+        r, a = g.rmse(tc, tv)
+        rr, ra = ref.rmse_mae(tc, tv)
+        assert abs(r - rr) <= 1e-5 * rr and abs(a - ra) <= 1e-5 * ra
+        # k = 0 and the fixed reduction order are deterministic
+        assert g.rmse(tc[:0], tv[:0]) == (0.0, 0.0)
+        assert g.rmse(tc, tv) == (r, a)
+
+
+def test_predict_rejects_out_of_range(B, cfg1):
+    c, v = cfg1.tensor.split("train")
+    with B.Tucker(cfg1.tensor.shape, cfg1.ranks, c, v, r_core=5) as g:
+        bad = np.array([[0, 0, 0], [500, 0, 0]], np.int32)
+        with pytest.raises(B.StdError) as ei:
+            g.predict(bad)
+        assert ei.value.code == B.STD_EINVAL
+        # the context stays usable
+        assert np.isfinite(g.predict(bad[:1])).all()
+
+
+def test_create_rejects_out_of_range_index(B):
+    coords = np.array([[0, 0, 0], [1, 9, 0]], np.int32)
+    vals = np.ones(2, np.float32)
+    with pytest.raises(B.StdError) as ei:
+        B.Tucker((4, 4, 4), (2, 2, 2), coords, vals, r_core=2)
+    assert ei.value.code == B.STD_EINVAL
+
+
+# ---------------------------------------------------------------------------
+# One minibatch: gradients and parameters
+# ---------------------------------------------------------------------------
+
+def _step_case(B, synth, tensor, ranks, R, M, batch, lr=(0.3, 0.2), lam=(0.01, 0.02), norm_mode=0, init="normal"):
+    """Probe minibatch `batch` of epoch 0 from one state on both sides.  For
+    batch > 0 the state is the oracle's FP64 state after batches [0, batch),
+    rounded to FP32 and given to both sides (a one-step comparison)."""
+    c, v = tensor.split("train")
+    A0, B0 = synth.init_params(tensor.shape, ranks, R, mode=init, seed=1,
+                               mean_value=float(np.mean(v)))
+    if batch > 0:
+        adv = O.Model(tensor.shape, ranks, R, A0, B0)
+        adv.epoch(c, v, M, 2, 0, lr[0], lr[1], lam[0], lam[1], norm_mode, 0, batch)
+        A0 = [a.astype(np.float32) for a in adv.A]
+        B0 = [b.astype(np.float32) for b in adv.B]
+    ref = O.Model(tensor.shape, ranks, R, A0, B0)
+    with _gpu(B, tensor.shape, ranks, R, c, v, A0, B0, norm_mode=norm_mode) as g:
+        sched = O.perm_range(c.shape[0], 2, 0, batch * M, min(M, c.shape[0] - batch * M))
+        pr = g.batches(lr[0], lr[1], lam[0], lam[1], M, batch, batch + 1, probe=True)
+        V, F, nseg = ref.step(c[sched], v[sched], lr[0], lr[1], lam[0], lam[1], norm_mode=norm_mode, probe=True)
+        Ag, Bg, core, _ = g.get_params()
+    # Norm-wise relative error of each mode's gradient (all R columns of B(n);
+    # all touched rows of A(n)); each row also within a mixed bound so a
+    # single wrong row cannot hide in the norm.
+    N = len(ranks)
+    worst_v = worst_f = 0.0
+    for n in range(N):
+        Jn = ranks[n]
+        worst_v = max(worst_v, _rel(pr["core_V"][n, :R, :Jn], V[n, :R, :Jn]))
+        assert pr["nseg"][n] == nseg[n]
+        U = int(nseg[n])
+        Fg, Fo = pr["factor_F"][n, :U, :Jn], F[n, :U, :Jn]
+        worst_f = max(worst_f, _rel(Fg, Fo))
+        row_err = np.linalg.norm(Fg - Fo, axis=1)
+        row_tol = 1e-5 * np.linalg.norm(Fo, axis=1) + 1e-6 * np.linalg.norm(Fo, axis=1).max()
+        assert np.all(row_err <= row_tol), float((row_err / row_tol).max())
+    assert worst_v <= 1e-5, worst_v
+    assert worst_f <= 1e-5, worst_f
+    for n in range(N):
+        sa = float(np.abs(ref.A[n]).max())
+        sb = float(np.abs(ref.B[n]).max())
+        assert float(np.abs(Ag[n] - ref.A[n]).max()) <= 1e-5 * sa
+        assert float(np.abs(Bg[n] - ref.B[n]).max()) <= 1e-5 * sb
+    np.testing.assert_allclose(core, ref.build_core(), rtol=1e-4, atol=1e-5 * np.abs(ref.G).max())
+    return worst_v, worst_f
+
+
+def test_step_gradients_config1(B, synth, cfg1):
+    _step_case(B, synth, cfg1.tensor, cfg1.ranks, 5, 256, batch=0)
+
+
+def test_step_gradients_config1_later_batch_and_last(B, synth, cfg1):
+    _step_case(B, synth, cfg1.tensor, cfg1.ranks, 5, 256, batch=3)
+    nb = (cfg1.tensor.train.shape[0] + 255) // 256
+    _step_case(B, synth, cfg1.tensor, cfg1.ranks, 5, 256, batch=nb - 1)
+
+
+def test_step_gradients_rating_zipf_4096(B, synth):
+    # Netflix-like distributions scaled down: hot rows span many CTA chunks
+    w = synth.config2(scale=0.004)
+    _step_case(B, synth, w.tensor, w.ranks, 5, 4096, batch=1, init="rating", lr=(0.05, 0.05))
+
+
+def test_step_gradients_4order_8192(B, synth):
+    w = synth.config3(scale=0.004)
+    _step_case(B, synth, w.tensor, w.ranks, 5, 8192, batch=0)
+
+
+@pytest.mark.parametrize("norm_mode", [1])
+def test_step_gradients_row_count_normaliser(B, synth, cfg1, norm_mode):
+    _step_case(B, synth, cfg1.tensor, cfg1.ranks, 5, 256, batch=2, norm_mode=norm_mode)
+
+
+@pytest.mark.parametrize("shape,ranks,R,M,nnz", [
+    ((50, 40), (3, 5), 2, 17, 300),              # N = 2
+    ((30, 20, 10, 8, 6), (2, 3, 2, 2, 3), 3, 64, 2000),   # N = 5, mixed ranks
+    ((9, 8, 7), (1, 1, 1), 1, 1, 40),             # rank 1, M = 1
+    ((12, 11, 10), (6, 5, 4), 7, 500, 333),       # one short minibatch (M > nnz)
+])
+def test_step_gradients_edge_shapes(B, synth, shape, ranks, R, M, nnz):
+    t = synth.make_tensor(shape, nnz, [("uniform",)] * len(shape), ranks, 0.1, 0.0, seed=17)
+    _step_case(B, synth, t, ranks, R, M, batch=0)
+
+
+# ---------------------------------------------------------------------------
+# Epochs: per-epoch train/test RMSE within 1e-3 absolute over 10 epochs
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("lr", [1e-3, 0.5])
+def test_epoch_rmse_parity_config1(B, synth, cfg1, lr):
+    c, v = cfg1.tensor.split("train")
+    tc, tv = cfg1.tensor.split("test")
+    A0, B0 = synth.init_params(cfg1.tensor.shape, cfg1.ranks, 5, mode="normal", seed=1)
+    ref = O.Model(cfg1.tensor.shape, cfg1.ranks, 5, A0, B0)
+    worst = 0.0
+    with _gpu(B, cfg1.tensor.shape, cfg1.ranks, 5, c, v, A0, B0) as g:
+        for ep in range(cfg1.epochs):
+            g.epoch(lr, lr, cfg1.lam, cfg1.lam, cfg1.minibatch)
+            ref.epoch(c, v, cfg1.minibatch, 2, ep, lr, lr, cfg1.lam, cfg1.lam)
+            for cc, vv in ((c, v), (tc, tv)):
+                r_g, m_g = g.rmse(cc, vv)
+                r_o, m_o = ref.rmse_mae(cc, vv)
+                worst = max(worst, abs(r_g - r_o), abs(m_g - m_o))
+    assert worst <= 1e-3, worst
+
+
+def test_epochs_are_deterministic(B, synth, cfg1):
+    c, v = cfg1.tensor.split("train")
+    A0, B0 = synth.init_params(cfg1.tensor.shape, cfg1.ranks, 5, mode="normal", seed=1)
+    outs = []
+    for _ in range(2):
+        with _gpu(B, cfg1.tensor.shape, cfg1.ranks, 5, c, v, A0, B0) as g:
+            for ep in range(2):
+                g.epoch(0.5, 0.5, 1e-3, 1e-3, 256)
+            outs.append(g.get_params())
+    for x, y in zip(outs[0][0] + outs[0][1], outs[1][0] + outs[1][1]):
+        assert np.array_equal(x, y)
+
+
+def test_checkpoint_resume_is_bit_identical(B, synth, cfg1):
+    c, v = cfg1.tensor.split("train")
+    A0, B0 = synth.init_params(cfg1.tensor.shape, cfg1.ranks, 5, mode="normal", seed=1)
+    with _gpu(B, cfg1.tensor.shape, cfg1.ranks, 5, c, v, A0, B0) as g:
+        for _ in range(3):
+            g.epoch(0.5, 0.5, 1e-3, 1e-3, 256)
+        full = g.get_params()
+    with _gpu(B, cfg1.tensor.shape, cfg1.ranks, 5, c, v, A0, B0) as g:
+        g.epoch(0.5, 0.5, 1e-3, 1e-3, 256)
+        A1, B1, _, ep = g.get_params()
+    assert ep == 1
+    with _gpu(B, cfg1.tensor.shape, cfg1.ranks, 5, c, v) as g:
+        g.set_params(A1, B1, epoch=ep)
+        g.epoch(0.5, 0.5, 1e-3, 1e-3, 256)
+        g.epoch(0.5, 0.5, 1e-3, 1e-3, 256)
+        resumed = g.get_params()
+    for x, y in zip(full[0] + full[1], resumed[0] + resumed[1]):
+        assert np.array_equal(x, y)
+    assert resumed[3] == 3
