@@ -1,0 +1,343 @@
+#!/usr/bin/env python3
+"""Benchmark of the SGD_Tucker hot path on one GB300.
+
+Workload (default): the Netflix-shaped rating tensor 480,189 x 17,770 x 2,182
+with 100M nonzeros (Zipf 1.1 users, Zipf 1.3 items, uniform time; values in
+{1..5} from a planted J=10 Tucker model), 99/1 train/test split, ranks J=10,
+R_core=5, minibatch 4096.  Synthetic data of that shape stands in for the
+Netflix dataset.  One step = one SGD epoch over the training nonzeros (sampler,
+tiler, core phase, core rebuild and factor phase of every minibatch) plus the
+RMSE/MAE pass over the test entries.  The metric is sampled nonzeros per
+second per epoch.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gpu|reference]
+
+`--impl reference` times the FP64 CPU oracle (the only other implementation of
+this path) on the host cores over a bounded sample of the same workload.
+Under torchrun (N > 1) every rank runs an independent replica (the strict
+minibatch sequence has no data-parallel split without a per-phase exchange, so
+N GPUs run N replicas; scaling is weak).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "sampled nonzeros/s per SGD epoch at oracle RMSE, BF16 vs FP32; serve p99 latency"
+
+
+def _args():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=5)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", choices=["gpu", "reference"], default="gpu")
+    p.add_argument("--scale", type=float, default=1.0, help="workload scale (1.0 = 100M nonzeros)")
+    p.add_argument("--cpu-batches", type=int, default=200,
+                   help="minibatches in the oracle's timed sample (cpu_baseline of the GPU leg)")
+    p.add_argument("--ref-batches", type=int, default=48,
+                   help="minibatches per step of --impl reference")
+    p.add_argument("--e2e-steps", type=int, default=2)
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-e2e", action="store_true")
+    return p.parse_args()
+
+
+def _peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def _workload(scale):
+    from paper_2012_03550_gb300 import synth
+    t0 = time.time()
+    w = synth.config2(scale=scale)
+    gen_s = time.time() - t0
+    return w, gen_s
+
+
+def _bytes_per_nnz(N, J, s_f=4):
+    # (N+1) passes each read the COO entry ((N+1) words) and N factor rows;
+    # the N factor modes each write and read back one FP32 gradient row.
+    return (N + 1) * ((4 * N + 4) + N * J * s_f) + N * J * 8
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples (200 ms) while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.idx = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        sm, mx, reasons = [], [], set()
+        names = ["active", "hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as fh:
+            for line in fh:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    mx.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for name, val in zip(names[1:], parts[5:9]):
+                    if val.lower().startswith("active"):
+                        reasons.add(name)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+def _dist():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def run_reference(a):
+    """FP64 oracle on the host cores over bounded samples of the workload."""
+    world, rank, _ = _dist()
+    if rank != 0:
+        return 0
+    import numpy as np
+    from oracle import oracle as O
+    from paper_2012_03550_gb300 import synth
+    w, _ = _workload(a.scale)
+    c, v = w.tensor.split("train")
+    A0, B0 = synth.init_params(w.tensor.shape, w.ranks, w.r_core, mode="rating", seed=1,
+                               mean_value=float(np.mean(v)))
+    md = O.Model(w.tensor.shape, w.ranks, w.r_core, A0, B0)
+    M = w.minibatch
+    nb = a.ref_batches
+    times = []
+    for step in range(a.warmup + a.steps):
+        b0 = (step * nb) % max(1, (c.shape[0] // M) - nb)
+        t0 = time.perf_counter()
+        md.epoch(c, v, M, 2, 0, w.lr, w.lr, w.lam, w.lam, 0, b0, b0 + nb)
+        dt = time.perf_counter() - t0
+        if step >= a.warmup:
+            times.append(dt)
+    sample = nb * M
+    ms = 1e3 * sum(times) / len(times)
+    value = sample / (ms * 1e-3)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "nnz/s", "n_gpus": a.gpus,
+        "steps": a.steps, "warmup": a.warmup, "ms_per_step": ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": w.name, "minibatch": M, "ranks": list(w.ranks), "r_core": w.r_core,
+                   "step": f"{nb} minibatches of epoch 0 (bounded sample of one epoch)"},
+        "cpu_baseline": {"value": value, "unit": "nnz/s", "cores": 1, "kind": "oracle",
+                         "sample": f"{nb} minibatches x {M} nonzeros per step, single thread"},
+        "e2e": {"value": value, "unit": "nnz/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_gpu(a):
+    import numpy as np
+    import torch
+
+    world, rank, local = _dist()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    import __graft_entry__ as ge
+    ge.build()
+    from paper_2012_03550_gb300 import binding as B
+    from paper_2012_03550_gb300 import synth
+
+    w, gen_s = _workload(a.scale)
+    t = w.tensor
+    c, v = t.split("train")
+    tc, tv = t.split("test")
+    N, J, R, M = t.order, w.ranks[0], w.r_core, w.minibatch
+    A0, B0 = synth.init_params(t.shape, w.ranks, R, mode="rating", seed=1, mean_value=float(np.mean(v)))
+
+    stream = torch.cuda.Stream(device=dev)
+    # device-resident inputs: the COO and the test split live in HBM
+    dc = torch.from_numpy(c).to(dev)
+    dv = torch.from_numpy(v).to(dev)
+    dtc = torch.from_numpy(tc).to(dev)
+    dtv = torch.from_numpy(tv).to(dev)
+    torch.cuda.synchronize()
+    opt = B.std_default_options()
+    opt.r_core = R
+    opt.ptr_kind = 1
+    opt.stream = stream.cuda_stream
+    ctx = B.std_create(N, t.shape, w.ranks, c.shape[0], dc, dv, opt)
+    B.std_set_params(ctx, [np.ascontiguousarray(x) for x in A0], [np.ascontiguousarray(x) for x in B0], 0)
+    del dc, dv
+
+    def step():
+        st = B.std_sgd_epoch(ctx, w.lr, w.lr, w.lam, w.lam, M)
+        r = B.std_rmse(ctx, tc.shape[0], dtc, dtv)
+        return st, r
+
+    for _ in range(a.warmup):
+        step()
+    sampler = ClockSampler(local)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    sampler.start()
+    time.sleep(0.3)
+    with torch.cuda.stream(stream):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        upd, sched, rm = [], [], None
+        for _ in range(a.steps):
+            st, rm = step()
+            upd.append(st["update_seconds"])
+            sched.append(st["sched_seconds"])
+        e1.record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    clocks = sampler.stop()
+    elapsed = e0.elapsed_time(e1) * 1e-3
+    if world > 1:
+        tt = torch.tensor([elapsed], device=dev, dtype=torch.float64)
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        elapsed = float(tt.item())
+    n_train = c.shape[0]
+    value = world * n_train * a.steps / elapsed
+    ms_per_step = 1e3 * elapsed / a.steps
+
+    # roofline of the dominant kernel (the persistent update kernel)
+    bpn = _bytes_per_nnz(N, J)
+    upd_s = sum(upd) / len(upd)
+    achieved = n_train * bpn / upd_s / 1e9
+    peak, peak_kind = _peaks()
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": None, "kernel": "k_epoch", "peak_kind": peak_kind,
+                "bytes_per_nnz": bpn, "kernel_ms": upd_s * 1e3, "sched_kernel_ms": 1e3 * sum(sched) / len(sched)}
+
+    # end to end through the C ABI with host buffers (pinned), copies timed
+    e2e = None
+    if not a.no_e2e and a.e2e_steps > 0:
+        pc = torch.from_numpy(c).pin_memory()
+        pv = torch.from_numpy(v).pin_memory()
+        ptc = torch.from_numpy(tc).pin_memory()
+        ptv = torch.from_numpy(tv).pin_memory()
+        hA = [torch.from_numpy(np.ascontiguousarray(x)).pin_memory() for x in A0]
+        hB = [torch.from_numpy(np.ascontiguousarray(x)).pin_memory() for x in B0]
+        nA = [x.numpy() for x in hA]
+        nB = [x.numpy() for x in hB]
+        o2 = B.std_default_options()
+        o2.r_core = R
+        o2.ptr_kind = 0
+        o2.stream = stream.cuda_stream
+        h2d = c.nbytes + v.nbytes + sum(x.nbytes for x in nA) + sum(x.nbytes for x in nB) + tc.nbytes + tv.nbytes
+        d2h = 16
+        times = []
+        for i in range(a.e2e_steps + 1):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            cx = B.std_create(N, t.shape, w.ranks, c.shape[0], pc.numpy(), pv.numpy(), o2)
+            B.std_set_params(cx, nA, nB, 0)
+            B.std_sgd_epoch(cx, w.lr, w.lr, w.lam, w.lam, M)
+            B.std_rmse(cx, tc.shape[0], ptc.numpy(), ptv.numpy())
+            B.std_destroy(cx)
+            torch.cuda.synchronize()
+            if i > 0:
+                times.append(time.perf_counter() - t0)
+        e2e = {"value": n_train / (sum(times) / len(times)), "unit": "nnz/s", "h2d_bytes_per_step": int(h2d),
+               "d2h_bytes_per_step": d2h, "steps": len(times),
+               "path": "std_create(host COO) + std_set_params + std_sgd_epoch + std_rmse(host test) + std_destroy"}
+
+    # CPU baseline: the oracle as it stands on a bounded sample (rank 0, N = 1)
+    cpu = None
+    if not a.no_cpu_baseline and world == 1 and rank == 0:
+        from oracle import oracle as O
+        md = O.Model(t.shape, w.ranks, R, A0, B0)
+        nb = a.cpu_batches
+        t0 = time.perf_counter()
+        md.epoch(c, v, M, 2, 0, w.lr, w.lr, w.lam, w.lam, 0, 0, nb)
+        dt = time.perf_counter() - t0
+        cpu = {"value": nb * M / dt, "unit": "nnz/s", "cores": 1, "kind": "oracle",
+               "sample": f"first {nb} minibatches ({nb * M} nonzeros) of epoch 0, FP64, single thread"}
+
+    B.std_destroy(ctx)
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "nnz/s", "n_gpus": world, "steps": a.steps,
+            "warmup": a.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": w.name, "nnz_train": int(n_train), "nnz_test": int(tc.shape[0]),
+                       "minibatch": M, "ranks": list(w.ranks), "r_core": R, "precision": "fp32",
+                       "parallelism": "replicas" if world > 1 else "single GPU",
+                       "l2": "inputs larger than L2 (COO and per-epoch schedule are GBs); no flush",
+                       "step": "one epoch (sampler, tiler, core and factor phases) + test RMSE/MAE",
+                       "datagen_s": round(gen_s, 1)},
+            "roofline": roofline,
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "gpu_launches": 4 * a.steps,
+            "clocks": clocks,
+            "test_rmse": rm[0] if rm else None,
+            "test_mae": rm[1] if rm else None,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def main():
+    a = _args()
+    if a.impl == "reference":
+        return run_reference(a)
+    return run_gpu(a)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -104,8 +104,10 @@ int std_destroy(std_ctx* ctx);
 
 /* Per-epoch statistics (nullable output of std_sgd_epoch). */
 typedef struct {
-    double  seconds;     /* device time of the epoch (sampler, tiler and update kernels) */
-    double  nnz_per_s;   /* nnz / seconds */
+    double  seconds;        /* device time of the epoch (sampler, tiler and update kernels) */
+    double  sched_seconds;  /* device time of the sampler/tiler kernel alone */
+    double  update_seconds; /* device time of the persistent update kernel alone */
+    double  nnz_per_s;      /* nnz / seconds */
     int64_t nnz;         /* training nonzeros visited */
     int64_t batches;     /* minibatches in the epoch (the last one may be short) */
     int64_t epoch;       /* index of the epoch just run */

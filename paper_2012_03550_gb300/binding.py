@@ -59,6 +59,8 @@ class std_options(ctypes.Structure):
 class std_epoch_stats(ctypes.Structure):
     _fields_ = [
         ("seconds", ctypes.c_double),
+        ("sched_seconds", ctypes.c_double),
+        ("update_seconds", ctypes.c_double),
         ("nnz_per_s", ctypes.c_double),
         ("nnz", ctypes.c_int64),
         ("batches", ctypes.c_int64),
@@ -169,7 +171,8 @@ def std_destroy(ctx) -> None:
 def std_sgd_epoch(ctx, lr_a: float, lr_b: float, lambda_a: float, lambda_b: float, minibatch: int) -> dict:
     st = std_epoch_stats()
     _check(lib().std_sgd_epoch(ctx, lr_a, lr_b, lambda_a, lambda_b, int(minibatch), ctypes.byref(st)))
-    return dict(seconds=st.seconds, nnz_per_s=st.nnz_per_s, nnz=st.nnz, batches=st.batches, epoch=st.epoch)
+    return dict(seconds=st.seconds, sched_seconds=st.sched_seconds, update_seconds=st.update_seconds,
+                nnz_per_s=st.nnz_per_s, nnz=st.nnz, batches=st.batches, epoch=st.epoch)
 
 
 def std_sgd_batches(ctx, lr_a, lr_b, lambda_a, lambda_b, minibatch, batch_begin, batch_end, probe=None):

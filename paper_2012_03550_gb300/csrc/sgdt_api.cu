@@ -73,7 +73,7 @@ struct std_ctx {
   double* result = nullptr;
   int64_t epoch = 0;
   size_t allocated = 0;
-  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr, evm = nullptr;
 };
 
 namespace {
@@ -296,6 +296,7 @@ int run_batches(std_ctx* c, float lr_a, float lr_b, float lam_a, float lam_b, in
   a.probeF = pF;
   STD_CUDA(cudaMemsetAsync(c->bcnt, 0, (size_t)G * 4, c->stream), "run counters clear");
   STD_CUDA(cudaMemsetAsync(c->bar, 0, sizeof(unsigned long long), c->stream), "barrier clear");
+  if (record_end) STD_CUDA(cudaEventRecord(c->evm, c->stream), "event");
   if (b1 > b0) STD_CUDA(launch_epoch(a, G, smem, c->stream), "epoch kernel launch");
   if (record_end) STD_CUDA(cudaEventRecord(c->ev1, c->stream), "event");
   return read_err(c, "epoch kernel");
@@ -359,6 +360,7 @@ int std_destroy(std_ctx* c) {
     if (p) cudaFree(p);
   if (c->ev0) cudaEventDestroy(c->ev0);
   if (c->ev1) cudaEventDestroy(c->ev1);
+  if (c->evm) cudaEventDestroy(c->evm);
   delete c;
   return STD_OK;
 }
@@ -432,6 +434,7 @@ int std_create(std_ctx** out, int32_t order, const int64_t* mode_sizes, const in
   } while (0)
   TRY(cudaEventCreate(&c->ev0) == cudaSuccess ? STD_OK : cuda_error(cudaGetLastError(), "event create"));
   TRY(cudaEventCreate(&c->ev1) == cudaSuccess ? STD_OK : cuda_error(cudaGetLastError(), "event create"));
+  TRY(cudaEventCreate(&c->evm) == cudaSuccess ? STD_OK : cuda_error(cudaGetLastError(), "event create"));
   TRY(dev_alloc(c, (void**)&c->err, 16, "error word"));
   TRY(dev_alloc(c, (void**)&c->bar, 16, "barrier word"));
   TRY(dev_alloc(c, (void**)&c->result, 16, "result"));
@@ -481,10 +484,14 @@ int std_sgd_epoch(std_ctx* c, float lr_a, float lr_b, float lambda_a, float lamb
   rc = ensure_schedule(c, minibatch);
   if (!rc) rc = run_batches(c, lr_a, lr_b, lambda_a, lambda_b, minibatch, 0, nb, false, true);
   if (rc) return rc;
-  float ms = 0.f;
+  float ms = 0.f, ms_sched = 0.f, ms_upd = 0.f;
   STD_CUDA(cudaEventElapsedTime(&ms, c->ev0, c->ev1), "event time");
+  STD_CUDA(cudaEventElapsedTime(&ms_sched, c->ev0, c->evm), "event time");
+  STD_CUDA(cudaEventElapsedTime(&ms_upd, c->evm, c->ev1), "event time");
   if (out) {
     out->seconds = ms * 1e-3;
+    out->sched_seconds = ms_sched * 1e-3;
+    out->update_seconds = ms_upd * 1e-3;
     out->nnz = c->nnz;
     out->batches = nb;
     out->nnz_per_s = ms > 0.f ? (double)c->nnz / (ms * 1e-3) : 0.0;

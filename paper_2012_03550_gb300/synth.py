@@ -24,8 +24,12 @@ machine from (seed, purpose).
 """
 from __future__ import annotations
 
+import concurrent.futures
+import ctypes
 import dataclasses
 import math
+import os
+import subprocess
 from typing import List, Optional, Sequence
 
 import numpy as np
@@ -85,9 +89,47 @@ def draw_mode_indices(rng: np.random.Generator, count: int, size: int,
         if table is None:
             table = zipf_table(size, s)
         u = rng.random(count)
-        r = np.searchsorted(table, u, side="right")
+        step = 1 << 22
+        parts = _parallel(lambda lo: np.searchsorted(table, u[lo:lo + step], side="right"),
+                          list(range(0, count, step)))
+        r = np.concatenate(parts) if parts else np.empty(0, dtype=np.int64)
         return np.minimum(r, size - 1).astype(np.int64)
     raise ValueError(f"unknown distribution {dist!r}")
+
+
+_DEDUP_SRC = os.path.join(os.path.dirname(os.path.abspath(__file__)), "synth_dedup.c")
+_DEDUP_LIB = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libsynth_dedup.so")
+_dedup = None
+
+
+def build_native(force: bool = False) -> str:
+    """Compile the generator's C helper (first-occurrence hash set)."""
+    if (not force and os.path.exists(_DEDUP_LIB)
+            and os.path.getmtime(_DEDUP_LIB) >= os.path.getmtime(_DEDUP_SRC)):
+        return _DEDUP_LIB
+    tmp = _DEDUP_LIB + f".tmp{os.getpid()}"
+    subprocess.run(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-o", tmp, _DEDUP_SRC], check=True)
+    os.replace(tmp, _DEDUP_LIB)
+    return _DEDUP_LIB
+
+
+def _dedup_lib():
+    global _dedup
+    if _dedup is None:
+        L = ctypes.CDLL(build_native())
+        L.synth_first_unique.restype = ctypes.c_int64
+        L.synth_first_unique.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64, ctypes.c_void_p,
+                                         ctypes.c_void_p, ctypes.c_int64]
+        _dedup = L
+    return _dedup
+
+
+def _parallel(fn, items, workers=None):
+    workers = workers or min(16, os.cpu_count() or 4)
+    if len(items) <= 1 or workers <= 1:
+        return [fn(x) for x in items]
+    with concurrent.futures.ThreadPoolExecutor(max_workers=workers) as ex:
+        return list(ex.map(fn, items))
 
 
 def distinct_coords(rng: np.random.Generator, shape: Sequence[int], nnz: int,
@@ -95,6 +137,10 @@ def distinct_coords(rng: np.random.Generator, shape: Sequence[int], nnz: int,
     """Draw `nnz` distinct coordinates; duplicates are rejected in draw order.
 
     dists[n] is ("uniform",) or ("zipf", s).  Returns int32 [nnz, N].
+    Coordinates are drawn in rounds appended to one stream; a hash set keeps
+    the first occurrence of each cell in draw order (the result of drawing one
+    coordinate at a time and rejecting repeats).  Round sizes adapt to the
+    observed acceptance rate.
     """
     N = len(shape)
     cells = 1
@@ -107,38 +153,36 @@ def distinct_coords(rng: np.random.Generator, shape: Sequence[int], nnz: int,
     strides = np.ones(N, dtype=np.int64)
     for n in range(1, N):
         strides[n] = strides[n - 1] * int(shape[n - 1])
-    accepted_keys = np.empty(0, dtype=np.int64)      # sorted, for membership
-    out_chunks: List[np.ndarray] = []
+    cap = 1
+    while cap < 2 * nnz + 16:
+        cap <<= 1
+    table = np.zeros(cap, dtype=np.uint64)
+    out = np.empty((nnz, N), dtype=np.int32)
+    idx = np.empty(nnz, dtype=np.int64)
+    L = _dedup_lib()
+    accept_rate = 0.9
     have = 0
-    rounds = 0
-    while have < nnz:
+    for _ in range(1000):
         need = nnz - have
-        draw = int(need * 1.2) + 1024
+        if need <= 0:
+            break
+        draw = int(need / max(accept_rate, 0.02) * 1.05) + 1024
         cols = [draw_mode_indices(rng, draw, int(shape[n]), dists[n][0],
                                   dists[n][1] if len(dists[n]) > 1 else 0.0, tables[n])
                 for n in range(N)]
         keys = np.zeros(draw, dtype=np.int64)
         for n in range(N):
             keys += cols[n] * strides[n]
-        _, first = np.unique(keys, return_index=True)
-        first.sort()                                  # keep draw order
-        k = keys[first]
-        if accepted_keys.size:
-            pos = np.searchsorted(accepted_keys, k)
-            pos = np.minimum(pos, accepted_keys.size - 1)
-            fresh = accepted_keys[pos] != k
-            first = first[fresh]
-            k = k[fresh]
-        first = first[:need]
-        k = k[:need]
-        chunk = np.stack([cols[n][first] for n in range(N)], axis=1).astype(np.int32)
-        out_chunks.append(chunk)
-        accepted_keys = np.union1d(accepted_keys, k)
-        have += chunk.shape[0]
-        rounds += 1
-        if rounds > 200:
-            raise RuntimeError("coordinate rejection did not converge")
-    return np.concatenate(out_chunks, axis=0)
+        got = int(L.synth_first_unique(keys.ctypes.data, draw, need, idx.ctypes.data + 8 * have,
+                                       table.ctypes.data, cap))
+        sel = idx[have:have + got]
+        for n in range(N):
+            out[have:have + got, n] = cols[n][sel]
+        have += got
+        accept_rate = max(got / float(draw), 1e-3)
+    else:
+        raise RuntimeError("coordinate rejection did not converge")
+    return out
 
 
 def planted_tucker(rng: np.random.Generator, shape: Sequence[int], ranks: Sequence[int]):
@@ -153,22 +197,26 @@ def planted_tucker(rng: np.random.Generator, shape: Sequence[int], ranks: Sequen
 
 
 def planted_values(core: np.ndarray, factors: Sequence[np.ndarray], coords: np.ndarray,
-                   chunk: int = 1 << 20) -> np.ndarray:
+                   chunk: int = 1 << 18) -> np.ndarray:
     """Evaluate the planted dense Tucker model at `coords` in FP64 (numpy
-    contractions, chunked): sum over j of core[j] * prod_n factors[n][i_n, j_n]."""
+    contractions, chunked): sum over j of core[j] * prod_n factors[n][i_n, j_n].
+    The core is contracted with mode 1 by a GEMM, then with the remaining
+    modes from the last one inwards."""
     N = coords.shape[1]
     out = np.empty(coords.shape[0], dtype=np.float64)
     J0 = core.shape[0]
     core0 = core.reshape(J0, -1)
-    for lo in range(0, coords.shape[0], chunk):
+
+    def one(lo):
         hi = min(lo + chunk, coords.shape[0])
         c = coords[lo:hi]
-        t = factors[0][c[:, 0]] @ core0                 # [m, J2*...*JN]
-        t = t.reshape((hi - lo,) + core.shape[1:])
-        for n in range(1, N):
+        t = (factors[0][c[:, 0]] @ core0).reshape((hi - lo,) + core.shape[1:])
+        for n in range(N - 1, 0, -1):
             a = factors[n][c[:, n]]                     # [m, Jn]
-            t = np.einsum("sj...,sj->s...", t, a)
+            t = (t * a.reshape((hi - lo,) + (1,) * (n - 1) + (a.shape[1],))).sum(axis=-1)
         out[lo:hi] = t
+
+    _parallel(one, list(range(0, coords.shape[0], chunk)))
     return out
 
 
