@@ -190,6 +190,36 @@ int std_set_params(std_ctx* ctx, const float* const* A, const float* const* B, i
 /* Thread-local description of the last error ("" if none). */
 const char* std_last_error(void);
 
+/*
+ * RMSE and MAE without any device allocation.  The paper has no counterpart:
+ * this is for callers that cannot let a library allocate device memory, such
+ * as a serving process whose device memory is all reserved by its own pool
+ * allocator, or a latency-critical loop that cannot pay for cudaMalloc and
+ * cudaFree (cudaFree synchronises the whole device).
+ *
+ * Same quantity as std_rmse (Eq. 19) for the model given by the caller:
+ *   order, mode_sizes[N], ranks[N], r_core   host values (limits as std_create)
+ *   A[N]     host array of device pointers; A[n] is I_n x J_n, row-major
+ *   B[N]     host array of device pointers; B[n] is J_n x r_core, row-major
+ *   coords   device, k x N int32 (0-based); values: device, k floats
+ *   out      device, 2 doubles: {rmse, mae}; {0, 0} when k = 0
+ *   stream   cudaStream_t (NULL = legacy stream)
+ * The call only enqueues two kernels on `stream` and returns; read `out`
+ * after synchronising the stream.  A coordinate outside [0, I_n) makes the
+ * result NaN.  Sizes beyond the limits return STD_EUNSUPPORTED.
+ * Scratch: a fixed __device__ array of STD_STATIC_RMSE_BLOCKS x 2 doubles
+ * (16 KiB) inside the library, held by every GPU that loads the library until
+ * the process exits.  It is not zeroed: each call writes every slot it reads.
+ * Every call shares it, so calls that overlap on the GPU (concurrent streams,
+ * other threads) race and must be serialised by the caller.  The first call
+ * on each device looks up the array's device address with that device
+ * current; make that first call before any stream capture.
+ */
+#define STD_STATIC_RMSE_BLOCKS 1024
+int std_rmse_static(int32_t order, const int64_t* mode_sizes, const int32_t* ranks, int32_t r_core,
+                    const float* const* A, const float* const* B, int64_t k, const int32_t* coords,
+                    const float* values, double* out, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

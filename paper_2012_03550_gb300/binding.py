@@ -94,6 +94,8 @@ SIGNATURES = {
     "std_get_params": (ctypes.c_int, [_P, _P, _P, _P, _P]),
     "std_set_params": (ctypes.c_int, [_P, _P, _P, ctypes.c_int64]),
     "std_last_error": (ctypes.c_char_p, []),
+    "std_rmse_static": (ctypes.c_int, [ctypes.c_int32, _P, _P, ctypes.c_int32, _P, _P, ctypes.c_int64, _P, _P,
+                                       _P, _P]),
 }
 
 
@@ -214,6 +216,16 @@ def std_set_params(ctx, A=None, B=None, epoch: int = -1) -> None:
     Ap = _ptr_array(A) if A is not None else None
     Bp = _ptr_array(B) if B is not None else None
     _check(lib().std_set_params(ctx, Ap, Bp, int(epoch)))
+
+
+def std_rmse_static(order, mode_sizes, ranks, r_core, A, B, k, coords, values, out, stream=None) -> None:
+    """Allocation-free RMSE/MAE: A, B lists of device tensors, coords/values/out
+    device tensors (out: 2 float64); enqueued on `stream` (a cudaStream_t
+    handle or None).  Read `out` after synchronising the stream."""
+    ms = np.ascontiguousarray(mode_sizes, dtype=np.int64)
+    rk = np.ascontiguousarray(ranks, dtype=np.int32)
+    _check(lib().std_rmse_static(int(order), ms.ctypes.data, rk.ctypes.data, int(r_core), _ptr_array(A),
+                                 _ptr_array(B), int(k), _addr(coords), _addr(values), _addr(out), stream))
 
 
 class Tucker:

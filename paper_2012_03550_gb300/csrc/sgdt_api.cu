@@ -35,6 +35,8 @@ int cuda_error(cudaError_t e, const char* what) {
 
 }  // namespace
 
+int sgdt::record_error(int code, const std::string& msg) { return set_error(code, msg); }
+
 struct std_ctx {
   Geometry g{};
   std_options opt{};

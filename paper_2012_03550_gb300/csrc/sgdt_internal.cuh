@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cstdint>
+#include <string>
 #include <cuda_runtime.h>
 
 #include "sgd_tucker.h"
@@ -153,5 +154,8 @@ cudaError_t launch_predict(const Geometry& g, const AParams& A, const float* B, 
                            const float* values, int64_t k, float* out, double* partials, int blocks,
                            int* err, cudaStream_t st);
 cudaError_t launch_rmse_finish(const double* partials, int blocks, double* result, cudaStream_t st);
+
+// Sets the thread-local message returned by std_last_error(); returns code.
+int record_error(int code, const std::string& msg);
 
 }  // namespace sgdt
