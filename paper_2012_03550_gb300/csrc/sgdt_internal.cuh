@@ -11,7 +11,7 @@ namespace sgdt {
 
 constexpr int kMaxN = STD_MAX_ORDER;
 constexpr int kMaxJ = STD_MAX_RANK;
-constexpr int kEpochThreads = 256;
+constexpr int kEpochThreads = 512;
 constexpr int kScheduleThreads = 512;
 constexpr int kMaxChunk = 128;          // samples per CTA per phase in the epoch kernel
 constexpr int kMaxCorePayload = 8192;   // floats of the per-mode core reduction
