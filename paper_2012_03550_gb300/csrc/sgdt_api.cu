@@ -126,15 +126,7 @@ int ensure_stage(std_ctx* c, size_t bytes) {
   return STD_OK;
 }
 
-int payload_floats(const Geometry& g) {
-  int mx = 0;
-  for (int n = 0; n < g.N; ++n) {
-    const int Jn = g.J[n];
-    const int P = g.R * Jn + (g.R * (g.R - 1) / 2) * (Jn * (Jn + 1) / 2);
-    if (P > mx) mx = P;
-  }
-  return mx;
-}
+int payload_floats(const Geometry& g) { return epoch_payload_floats(g); }
 
 int ensure_schedule(std_ctx* c, int M) {
   if (c->sched_mem && c->sched_M == M && c->sched_epoch == c->epoch) return STD_OK;
@@ -172,27 +164,28 @@ int ensure_schedule(std_ctx* c, int M) {
 int choose_ctas(std_ctx* c, int M, int* ctas, int* chunk_max, size_t* smem) {
   const int payload = payload_floats(c->g);
   if (payload > kMaxCorePayload)
-    return set_error(STD_EUNSUPPORTED, "core reduction payload R*J + R(R-1)/2*J(J+1)/2 exceeds 8192 floats");
+    return set_error(STD_EUNSUPPORTED, "core reduction payload R*J + R(R-1)/2*J*J exceeds 8192 floats");
+  const int cap = epoch_chunk_cap(c->g);
   int G = c->opt.ctas;
   if (G <= 0) {
     G = (M + 15) / 16;
     if (G > c->sms) G = c->sms;
-    const int need = (M + kMaxChunk - 1) / kMaxChunk;
+    const int need = (M + cap - 1) / cap;
     if (G < need) G = need;
   }
   if (G < 1) G = 1;
   int ch = (M + G - 1) / G;
-  if (ch > kMaxChunk) return set_error(STD_EUNSUPPORTED, "minibatch too large for the chosen CTA count");
+  if (ch > cap) return set_error(STD_EUNSUPPORTED, "minibatch too large for the CTA count at these ranks");
   size_t sm = epoch_smem_bytes(c->g, ch, payload);
   if (sm > 227 * 1024) return set_error(STD_EUNSUPPORTED, "shape needs more shared memory than a CTA has");
-  STD_CUDA(epoch_kernel_setup(sm), "epoch kernel attributes");
-  const int maxG = epoch_max_ctas(sm);
+  STD_CUDA(epoch_kernel_setup(c->g.N, sm), "epoch kernel attributes");
+  const int maxG = epoch_max_ctas(c->g.N, sm);
   if (maxG < 1) return set_error(STD_EUNSUPPORTED, "epoch kernel cannot be resident");
   if (G > maxG) {
     if (c->opt.ctas > 0) return set_error(STD_EINVAL, "requested CTA count exceeds co-resident capacity");
     G = maxG;
     ch = (M + G - 1) / G;
-    if (ch > kMaxChunk) return set_error(STD_EUNSUPPORTED, "minibatch too large for the co-resident CTAs");
+    if (ch > cap) return set_error(STD_EUNSUPPORTED, "minibatch too large for the co-resident CTAs at these ranks");
     sm = epoch_smem_bytes(c->g, ch, payload);
   }
   *ctas = G;

@@ -138,9 +138,11 @@ struct AParams {
 // Launchers (host side, defined in the .cu files).
 cudaError_t launch_schedule(const Geometry& g, const uint32_t* coo, int cs, const Feistel& f,
                             const Schedule& s, int64_t b0, int64_t b1, cudaStream_t st);
+int epoch_payload_floats(const Geometry& g);
+int epoch_chunk_cap(const Geometry& g);   // largest samples per CTA per phase the kernel takes
 size_t epoch_smem_bytes(const Geometry& g, int chunk_max, int payload_max);
-cudaError_t epoch_kernel_setup(size_t smem);
-int epoch_max_ctas(size_t smem);
+cudaError_t epoch_kernel_setup(int N, size_t smem);
+int epoch_max_ctas(int N, size_t smem);
 cudaError_t launch_epoch(const EpochArgs& a, int ctas, size_t smem, cudaStream_t st);
 cudaError_t launch_init_params(const Geometry& g, float* const* A, float* B, int mode, double mu,
                                double sigma, uint64_t seed, cudaStream_t st);
