@@ -51,6 +51,7 @@ def _args():
     p.add_argument("--e2e-steps", type=int, default=2)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-bf16", action="store_true")
     return p.parse_args()
 
 
@@ -214,7 +215,6 @@ def run_gpu(a):
     opt.stream = stream.cuda_stream
     ctx = B.std_create(N, t.shape, w.ranks, c.shape[0], dc, dv, opt)
     B.std_set_params(ctx, [np.ascontiguousarray(x) for x in A0], [np.ascontiguousarray(x) for x in B0], 0)
-    del dc, dv
 
     def step():
         st = B.std_sgd_epoch(ctx, w.lr, w.lr, w.lam, w.lam, M)
@@ -245,6 +245,43 @@ def run_gpu(a):
     # every rank runs its own replica: all ranks' nonzeros over the slowest rank's time
     value, elapsed = D.weak_scaling_rate(float(n_train * a.steps), e0.elapsed_time(e1) * 1e-3, device=dev)
     ms_per_step = 1e3 * elapsed / a.steps
+
+    # the BF16 form on the same data and schedule (BF16 factor mirrors and core,
+    # tensor-core contraction, FP32 masters): throughput and RMSE gap
+    bf16 = None
+    if not a.no_bf16:
+        o16 = B.std_default_options()
+        o16.r_core = R
+        o16.ptr_kind = 1
+        o16.precision = 1
+        o16.stream = stream.cuda_stream
+        cx16 = B.std_create(N, t.shape, w.ranks, c.shape[0], dc, dv, o16)
+        B.std_set_params(cx16, [np.ascontiguousarray(x) for x in A0], [np.ascontiguousarray(x) for x in B0], 0)
+        rm16 = None
+        for _ in range(a.warmup):
+            B.std_sgd_epoch(cx16, w.lr, w.lr, w.lam, w.lam, M)
+            B.std_rmse(cx16, tc.shape[0], dtc, dtv)
+        torch.cuda.synchronize()
+        f0 = torch.cuda.Event(enable_timing=True)
+        f1 = torch.cuda.Event(enable_timing=True)
+        f0.record(stream)
+        upd16 = []
+        for _ in range(a.steps):
+            st16 = B.std_sgd_epoch(cx16, w.lr, w.lr, w.lam, w.lam, M)
+            rm16 = B.std_rmse(cx16, tc.shape[0], dtc, dtv)
+            upd16.append(st16["update_seconds"])
+        f1.record(stream)
+        torch.cuda.synchronize()
+        v16, e16 = D.weak_scaling_rate(float(n_train * a.steps), f0.elapsed_time(f1) * 1e-3, device=dev)
+        bf16 = {"value": v16, "unit": "nnz/s", "ms_per_step": 1e3 * e16 / a.steps,
+                "kernel_ms": 1e3 * sum(upd16) / len(upd16),
+                "speedup_vs_fp32": v16 / value,
+                "test_rmse": rm16[0], "test_mae": rm16[1],
+                "test_rmse_gap_vs_fp32": abs(rm16[0] - rm[0]),
+                "bytes_per_nnz": _bytes_per_nnz(N, J, 2),
+                "note": "same schedule and initial state as the FP32 run; RMSE after the same epochs"}
+        B.std_destroy(cx16)
+    del dc, dv
 
     # roofline of the dominant kernel (the persistent update kernel)
     bpn = _bytes_per_nnz(N, J)
@@ -315,6 +352,7 @@ def run_gpu(a):
             "roofline": roofline,
             "cpu_baseline": cpu,
             "e2e": e2e,
+            "bf16": bf16,
             "gpu_launches": 4 * a.steps,
             "clocks": clocks,
             "test_rmse": rm[0] if rm else None,

@@ -46,6 +46,7 @@ struct std_ctx {
   int cs = 0;                       // 32-bit words per packed COO record
   uint32_t* coo = nullptr;
   float* A[kMaxN] = {};
+  uint16_t* Ab[kMaxN] = {};   // BF16 mirrors (precision 1)
   float* B = nullptr;
   float* core = nullptr;
   int* err = nullptr;
@@ -176,7 +177,7 @@ int choose_ctas(std_ctx* c, int M, int* ctas, int* chunk_max, size_t* smem) {
   if (G < 1) G = 1;
   int ch = (M + G - 1) / G;
   if (ch > cap) return set_error(STD_EUNSUPPORTED, "minibatch too large for the CTA count at these ranks");
-  size_t sm = epoch_smem_bytes(c->g, ch, payload);
+  size_t sm = epoch_smem_bytes(c->g, ch, payload, c->opt.precision);
   if (sm > 227 * 1024) return set_error(STD_EUNSUPPORTED, "shape needs more shared memory than a CTA has");
   STD_CUDA(epoch_kernel_setup(c->g.N, sm), "epoch kernel attributes");
   const int maxG = epoch_max_ctas(c->g.N, sm);
@@ -186,7 +187,7 @@ int choose_ctas(std_ctx* c, int M, int* ctas, int* chunk_max, size_t* smem) {
     G = maxG;
     ch = (M + G - 1) / G;
     if (ch > cap) return set_error(STD_EUNSUPPORTED, "minibatch too large for the co-resident CTAs at these ranks");
-    sm = epoch_smem_bytes(c->g, ch, payload);
+    sm = epoch_smem_bytes(c->g, ch, payload, c->opt.precision);
   }
   *ctas = G;
   *chunk_max = ch;
@@ -266,7 +267,11 @@ int run_batches(std_ctx* c, float lr_a, float lr_b, float lam_a, float lam_b, in
   }
   EpochArgs a{};
   a.g = c->g;
-  for (int n = 0; n < c->g.N; ++n) a.A[n] = c->A[n];
+  for (int n = 0; n < c->g.N; ++n) {
+    a.A[n] = c->A[n];
+    a.Ab[n] = c->Ab[n];
+  }
+  a.precision = c->opt.precision;
   a.B = c->B;
   a.core = c->core;
   a.s = c->sched;
@@ -347,8 +352,10 @@ const char* std_last_error(void) { return g_last_error.c_str(); }
 int std_destroy(std_ctx* c) {
   if (!c) return STD_OK;
   cudaStreamSynchronize(c->stream);
-  for (int n = 0; n < kMaxN; ++n)
+  for (int n = 0; n < kMaxN; ++n) {
     if (c->A[n]) cudaFree(c->A[n]);
+    if (c->Ab[n]) cudaFree(c->Ab[n]);
+  }
   void* ptrs[] = {c->coo, c->B, c->core, c->err, c->bar, c->sched_mem, c->part, c->red,
                   c->bpart, c->bcnt, c->probe_mem, c->stage, c->rpart, c->result};
   for (void* p : ptrs)
@@ -374,7 +381,6 @@ int std_create(std_ctx** out, int32_t order, const int64_t* mode_sizes, const in
   if (opt.r_core < 1) return set_error(STD_EINVAL, "r_core must be >= 1");
   if (opt.r_core > STD_MAX_RANK) return set_error(STD_EUNSUPPORTED, "r_core exceeds STD_MAX_RANK");
   if (opt.precision != 0 && opt.precision != 1) return set_error(STD_EINVAL, "precision must be 0 or 1");
-  if (opt.precision == 1) return set_error(STD_EUNSUPPORTED, "BF16 storage is not built into this library");
   if (opt.norm_mode != 0 && opt.norm_mode != 1) return set_error(STD_EINVAL, "norm_mode must be 0 or 1");
   if (opt.init_mode != 0 && opt.init_mode != 1) return set_error(STD_EINVAL, "init_mode must be 0 or 1");
   if (opt.ptr_kind != 0 && opt.ptr_kind != 1) return set_error(STD_EINVAL, "ptr_kind must be 0 or 1");
@@ -391,6 +397,7 @@ int std_create(std_ctx** out, int32_t order, const int64_t* mode_sizes, const in
     g.I[n] = mode_sizes[n];
     g.J[n] = ranks[n];
     g.Jp[n] = (ranks[n] + 3) & ~3;
+    g.Jb[n] = (ranks[n] + 7) & ~7;
     g.boff[n] = boff;
     boff += ranks[n] * g.R;
     g.joff[n] = sumJ;
@@ -435,6 +442,9 @@ int std_create(std_ctx** out, int32_t order, const int64_t* mode_sizes, const in
   TRY(dev_alloc(c, (void**)&c->result, 16, "result"));
   TRY(dev_alloc(c, (void**)&c->coo, (size_t)nnz * c->cs * 4, "COO"));
   for (int n = 0; n < order; ++n) TRY(dev_alloc(c, (void**)&c->A[n], (size_t)g.I[n] * g.Jp[n] * 4, "factor matrix"));
+  if (opt.precision == 1)
+    for (int n = 0; n < order; ++n)
+      TRY(dev_alloc(c, (void**)&c->Ab[n], (size_t)g.I[n] * g.Jb[n] * 2, "BF16 factor mirror"));
   TRY(dev_alloc(c, (void**)&c->B, (size_t)boff * 4, "Kruskal matrices"));
   TRY(dev_alloc(c, (void**)&c->core, (size_t)g.prodJ * 4, "core"));
   TRY(cudaMemsetAsync(c->err, 0, 16, c->stream) == cudaSuccess ? STD_OK : cuda_error(cudaGetLastError(), "memset"));
@@ -456,6 +466,10 @@ int std_create(std_ctx** out, int32_t order, const int64_t* mode_sizes, const in
   TRY(e == cudaSuccess ? STD_OK : cuda_error(e, "parameter init"));
   e = launch_build_core(g, c->B, c->core, c->stream);
   TRY(e == cudaSuccess ? STD_OK : cuda_error(e, "core build"));
+  if (opt.precision == 1) {
+    e = launch_mirror_bf16(g, c->A, c->Ab, c->stream);
+    TRY(e == cudaSuccess ? STD_OK : cuda_error(e, "BF16 mirror"));
+  }
   TRY(read_err(c, "std_create"));
   if (opt.ptr_kind == 0) {
     // the staging buffer held the whole COO; give it back
@@ -663,6 +677,7 @@ int std_set_params(std_ctx* c, const float* const* A, const float* const* B, int
                "set B");
   }
   STD_CUDA(launch_build_core(g, c->B, c->core, c->stream), "core build");
+  if (c->opt.precision == 1) STD_CUDA(launch_mirror_bf16(g, c->A, c->Ab, c->stream), "BF16 mirror");
   STD_CUDA(cudaStreamSynchronize(c->stream), "set params sync");
   if (epoch >= 0) c->epoch = epoch;
   return STD_OK;

@@ -42,6 +42,8 @@
 // chunk and the last contributor (an acquire-release arrival count per run)
 // adds the pieces in chunk order and applies the update, so the result does
 // not depend on arrival order and no floating-point atomics are used.
+#include <cuda_bf16.h>
+
 #include "sgdt_internal.cuh"
 
 namespace sgdt {
@@ -74,16 +76,31 @@ __host__ __device__ inline int sum_pn(const Geometry& g) {
   return s;
 }
 
+__host__ __device__ inline int round_up(int x, int m) { return (x + m - 1) / m * m; }
+
+// Row stride (in BF16 elements) of the Kronecker-row and unfolded-core tiles
+// of the tensor-core contraction: at least the K extent rounded up to 16, and
+// congruent to 8 modulo 64 so that the eight rows a fragment load touches fall
+// on distinct shared-memory banks.
+__host__ __device__ inline int bf16_row_stride(int Pn) {
+  const int p16 = round_up(Pn, 16);
+  int q = (p16 - 8 + 63) / 64;
+  if (q < 0) q = 0;
+  int kp = 64 * q + 8;
+  if (kp < p16) kp += 64;
+  return kp;
+}
+
 // Row stride of Y' = [Y | e] in shared memory: R*Jmax + 1 columns plus one
 // spare (2-wide tiles may read one column past the residual), even.
 __host__ __device__ inline int ystride(const Geometry& g) { return (g.R * g.Jmax + 3) & ~1; }
 
 struct SmemLayout {
-  int B, G, GT[2], ldig, coff, cdig, rowtab, rows, p, w, Y, S, E, F, red, V, D;
+  int B, G, GT[2], GTh[2], Sh, ldig, coff, cdig, rowtab, rows, p, w, Y, S, E, F, red, V, D;
   int crd[2], xs[2], seg[2], head, total_words;
 };
 
-__host__ __device__ inline SmemLayout smem_layout(const Geometry& g, int chunk, int payload) {
+__host__ __device__ inline SmemLayout smem_layout(const Geometry& g, int chunk, int payload, int precision) {
   SmemLayout L;
   int off = 0;
   auto take = [&](int words) {
@@ -98,8 +115,14 @@ __host__ __device__ inline SmemLayout smem_layout(const Geometry& g, int chunk, 
   const int gt = g.Jmax * pad4(Pmax);
   L.B = take(sumJR);
   L.G = take(g.prodJ);
-  L.GT[0] = take(gt);
-  L.GT[1] = take(gt);
+  const bool bf = precision == 1;
+  const int kpmax = bf16_row_stride(Pmax);
+  const int jn16 = round_up(g.Jmax, 16);
+  L.GT[0] = take(bf ? 0 : gt);
+  L.GT[1] = take(bf ? 0 : gt);
+  L.GTh[0] = take(bf ? jn16 * kpmax / 2 : 0);
+  L.GTh[1] = take(bf ? jn16 * kpmax / 2 : 0);
+  L.Sh = take(bf ? round_up(chunk, 16) * kpmax / 2 : 0);
   L.ldig = take(g.prodJ);
   L.coff = take(sum_pn(g));
   L.cdig = take(2 * sum_pn(g));
@@ -108,7 +131,7 @@ __host__ __device__ inline SmemLayout smem_layout(const Geometry& g, int chunk, 
   L.p = take(chunk * g.N * g.R);
   L.w = take(chunk * g.R);
   L.Y = take(chunk * ystride(g));
-  L.S = take(chunk * tile);
+  L.S = take(bf ? 0 : chunk * tile);
   L.E = take(chunk * g.Jmax);
   L.F = take(chunk * g.Jmax);
   L.red = take(payload);
@@ -229,13 +252,40 @@ __device__ __forceinline__ void load_rows(const EpochArgs& a, const int* crd, in
       if (i < total) {
         const int s = i / sumJ, jj = i - s * sumJ;
         const int k = rowtab[jj] & 0xff, j = rowtab[jj] >> 8;
-        v[u] = __ldcg(a.A[k] + (size_t)crd[s * N + k] * g.Jp[k] + j);
+        if (a.precision == 1) {
+          const unsigned short h = __ldcg(reinterpret_cast<const unsigned short*>(a.Ab[k]) +
+                                          (size_t)crd[s * N + k] * g.Jb[k] + j);
+          v[u] = __uint_as_float((uint32_t)h << 16);
+        } else {
+          v[u] = __ldcg(a.A[k] + (size_t)crd[s * N + k] * g.Jp[k] + j);
+        }
       }
     }
 #pragma unroll
     for (int u = 0; u < 4; ++u)
       if (i0 + u * T < total) rows[i0 + u * T] = v[u];
   }
+}
+
+// G_(n) as BF16 [j][c] with row stride bf16_row_stride(P_n); rows j >= J_n
+// (up to a multiple of 16) and columns c >= P_n are zero.
+__device__ __forceinline__ void build_gt_bf16(__nv_bfloat16* dst, const float* Gsm, const int* cof, int Jn, int Pn,
+                                              int gsn, int t0, int nt) {
+  const int KP = bf16_row_stride(Pn), J16 = round_up(Jn, 16);
+  for (int i = t0; i < J16 * KP; i += nt) {
+    const int j = i / KP, cc = i - j * KP;
+    const float v = (j < Jn && cc < Pn) ? Gsm[cof[cc] + j * gsn] : 0.f;
+    dst[i] = __float2bfloat16_rn(v);
+  }
+}
+
+__device__ __forceinline__ void mma_bf16_16816(float* d, uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3,
+                                               uint32_t b0, uint32_t b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+      "{%0,%1,%2,%3};"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
 }
 
 }  // namespace
@@ -246,10 +296,14 @@ k_epoch(EpochArgs a) {
   extern __shared__ __align__(16) float sm[];
   const Geometry& g = a.g;
   const int R = g.R;
-  const SmemLayout L = smem_layout(g, a.chunk_max, a.payload_max);
+  const SmemLayout L = smem_layout(g, a.chunk_max, a.payload_max, a.precision);
   float* Bsm = sm + L.B;
   float* Gsm = sm + L.G;
   float* GTb[2] = {sm + L.GT[0], sm + L.GT[1]};
+  __nv_bfloat16* GThb[2] = {reinterpret_cast<__nv_bfloat16*>(sm + L.GTh[0]),
+                            reinterpret_cast<__nv_bfloat16*>(sm + L.GTh[1])};
+  __nv_bfloat16* Sh = reinterpret_cast<__nv_bfloat16*>(sm + L.Sh);
+  const bool bf = a.precision == 1;
   uint32_t* ldig = reinterpret_cast<uint32_t*>(sm + L.ldig);
   int* coff = reinterpret_cast<int*>(sm + L.coff);
   unsigned long long* cdig = reinterpret_cast<unsigned long long*>(sm + L.cdig);
@@ -583,7 +637,9 @@ k_epoch(EpochArgs a) {
       Gsm[lin] = acc;
     }
     __syncthreads();
-    {
+    if (bf) {
+      build_gt_bf16(GThb[0], Gsm, coff, Jr[0], g.prodJ / Jr[0], g.gstride[0], tid, T);
+    } else {
       const int Pn = g.prodJ / Jr[0], Pp = pad4(Pn);
       float* GT = GTb[0];
       for (int i = tid; i < Jr[0] * Pp; i += T) {
@@ -623,100 +679,180 @@ k_epoch(EpochArgs a) {
       load_rows<N>(a, fcrd, cnt, rowtab, rows);
       __syncthreads();
       const int nheads = head[cnt];
-      // Gather-contract E_s = G_(n) S_s^T over Kronecker-row tiles.  Thread
-      // tile (sample, column pair, half of the Kronecker columns); the two
-      // halves are adjacent lanes; 2*Tj lanes per sample.
-      const int ntj = (Jn + 1) >> 1;
-      const int Tj = pow2_at_least(ntj);
-      const int lg = 31 - __clz(2 * Tj);          // log2(2 * Tj)
-      const int nout = cnt << lg;
-      float acc[kOutPerThread][2];
-#pragma unroll
-      for (int q = 0; q < kOutPerThread; ++q) acc[q][0] = acc[q][1] = 0.f;
-      for (int c0 = 0; c0 < Pp; c0 += ctile_cap) {
-        const int ct = min(ctile_cap, Pp - c0);
-        if (c0 > 0) __syncthreads();
-        // column-major build: thread per (Kronecker column, sample group)
+      if (bf) {
+        // Tensor-core contraction: E (samples x J_n) = S (samples x P_n) .
+        // G_(n)^T with BF16 operands and FP32 accumulation, mma.sync
+        // m16n8k16 tiles (one warp per 16 x 8 output tile, full K).
+        const int KP = bf16_row_stride(Pn);
+        const int C16 = round_up(cnt, 16);
+        const __nv_bfloat16* GTh = GThb[n & 1];
         {
-          const int ngroups = max(1, T / ct);
-          const int sg = tid / ct, cl = tid - sg * ct;
+          // thread per (Kronecker column, sample group); columns looped when
+          // the row is wider than the block
+          const int ngroups = max(1, T / KP);
+          const int sg = tid / KP;
           if (sg < ngroups) {
-            const int cc = c0 + cl;
-            if (cc < Pn) {
-              const unsigned long long packed = cdn[cc];
+            for (int cl = tid - sg * KP; cl < KP; cl += (KP > T ? T : KP)) {
               int off[N - 1];
+              const bool colv = cl < Pn;
+              if (colv) {
+                const unsigned long long packed = cdn[cl];
 #pragma unroll
-              for (int k = 0; k < N - 1; ++k) off[k] = (int)((packed >> (8 * k)) & 0xffu);
-              for (int s = sg; s < cnt; s += ngroups) {
-                const float* rs = rows + s * sumJ;
-                float S1 = rs[off[0]];
-#pragma unroll
-                for (int k = 1; k < N - 1; ++k) S1 *= rs[off[k]];
-                Sbuf[s * ctile_cap + cl] = S1;
+                for (int k = 0; k < N - 1; ++k) off[k] = (int)((packed >> (8 * k)) & 0xffu);
               }
-            } else {
-              for (int s = sg; s < cnt; s += ngroups) Sbuf[s * ctile_cap + cl] = 0.f;
+              for (int s = sg; s < C16; s += ngroups) {
+                float S1 = 0.f;
+                if (colv && s < cnt) {
+                  const float* rs = rows + s * sumJ;
+                  S1 = rs[off[0]];
+#pragma unroll
+                  for (int k = 1; k < N - 1; ++k) S1 *= rs[off[k]];
+                }
+                Sh[s * KP + cl] = __float2bfloat16_rn(S1);
+              }
             }
           }
         }
         __syncthreads();
+        {
+          const int mt = C16 >> 4, ntile = (Jn + 7) >> 3, ksteps = round_up(Pn, 16) >> 4;
+          const int gq = lane >> 2, tq = lane & 3;
+          for (int w = warp; w < mt * ntile; w += nwarps) {
+            const int mi = w / ntile, ni = w - mi * ntile;
+            const uint32_t* A0 = reinterpret_cast<const uint32_t*>(Sh + (mi * 16 + gq) * KP);
+            const uint32_t* A1 = reinterpret_cast<const uint32_t*>(Sh + (mi * 16 + gq + 8) * KP);
+            const uint32_t* Bq = reinterpret_cast<const uint32_t*>(GTh + (ni * 8 + gq) * KP);
+            float d[4] = {0.f, 0.f, 0.f, 0.f};
+            for (int ks = 0; ks < ksteps; ++ks) {
+              const int kw = ks * 8 + tq;
+              mma_bf16_16816(d, A0[kw], A1[kw], A0[kw + 4], A1[kw + 4], Bq[kw], Bq[kw + 4]);
+            }
+            const int s0 = mi * 16 + gq, j0 = ni * 8 + 2 * tq;
+            if (s0 < cnt) {
+              if (j0 < Jn) Ebuf[s0 * Jmax + j0] = d[0];
+              if (j0 + 1 < Jn) Ebuf[s0 * Jmax + j0 + 1] = d[1];
+            }
+            if (s0 + 8 < cnt) {
+              if (j0 < Jn) Ebuf[(s0 + 8) * Jmax + j0] = d[2];
+              if (j0 + 1 < Jn) Ebuf[(s0 + 8) * Jmax + j0 + 1] = d[3];
+            }
+          }
+        }
+        __syncthreads();
+        // residual e_s = a_n . E_s - x_s (8 lanes per sample), contributions in place
+        for (int base = 0; base < cnt * 8; base += T) {
+          const int t8 = base + tid, s = t8 >> 3, l = t8 & 7;
+          const bool live = s < cnt;
+          float part = 0.f;
+          if (live) {
+            const float* an = rows + s * sumJ + joff[n];
+            for (int j = l; j < Jn; j += 8) part = fmaf(an[j], Ebuf[s * Jmax + j], part);
+          }
+          part += __shfl_xor_sync(0xffffffffu, part, 4);
+          part += __shfl_xor_sync(0xffffffffu, part, 2);
+          part += __shfl_xor_sync(0xffffffffu, part, 1);
+          if (live) {
+            const float e = part - fx[s];
+            for (int j = l; j < Jn; j += 8) Ebuf[s * Jmax + j] *= e;
+          }
+        }
+        __syncthreads();
+      } else {
+      // Gather-contract E_s = G_(n) S_s^T over Kronecker-row tiles.  Thread
+        // tile (sample, column pair, half of the Kronecker columns); the two
+        // halves are adjacent lanes; 2*Tj lanes per sample.
+        const int ntj = (Jn + 1) >> 1;
+        const int Tj = pow2_at_least(ntj);
+        const int lg = 31 - __clz(2 * Tj);          // log2(2 * Tj)
+        const int nout = cnt << lg;
+        float acc[kOutPerThread][2];
+#pragma unroll
+        for (int q = 0; q < kOutPerThread; ++q) acc[q][0] = acc[q][1] = 0.f;
+        for (int c0 = 0; c0 < Pp; c0 += ctile_cap) {
+          const int ct = min(ctile_cap, Pp - c0);
+          if (c0 > 0) __syncthreads();
+          // column-major build: thread per (Kronecker column, sample group)
+          {
+            const int ngroups = max(1, T / ct);
+            const int sg = tid / ct, cl = tid - sg * ct;
+            if (sg < ngroups) {
+              const int cc = c0 + cl;
+              if (cc < Pn) {
+                const unsigned long long packed = cdn[cc];
+                int off[N - 1];
+#pragma unroll
+                for (int k = 0; k < N - 1; ++k) off[k] = (int)((packed >> (8 * k)) & 0xffu);
+                for (int s = sg; s < cnt; s += ngroups) {
+                  const float* rs = rows + s * sumJ;
+                  float S1 = rs[off[0]];
+#pragma unroll
+                  for (int k = 1; k < N - 1; ++k) S1 *= rs[off[k]];
+                  Sbuf[s * ctile_cap + cl] = S1;
+                }
+              } else {
+                for (int s = sg; s < cnt; s += ngroups) Sbuf[s * ctile_cap + cl] = 0.f;
+              }
+            }
+          }
+          __syncthreads();
+#pragma unroll
+          for (int q = 0; q < kOutPerThread; ++q) {
+            const int o = tid + q * T;
+            const int s = o >> lg, rem = o & ((1 << lg) - 1), jt = rem >> 1, h = rem & 1;
+            if (o < nout && jt < ntj) {
+              const int j0 = 2 * jt;
+              const float4* sv = reinterpret_cast<const float4*>(Sbuf + s * ctile_cap);
+              const float4* g0 = reinterpret_cast<const float4*>(GT + j0 * Pp + c0);
+              const float4* g1 = reinterpret_cast<const float4*>(GT + min(j0 + 1, Jn - 1) * Pp + c0);
+              float a0 = acc[q][0], a1 = acc[q][1], b0 = 0.f, b1 = 0.f;
+              const int nv = ct >> 2;
+              int v = h;
+              for (; v + 2 < nv; v += 4) {
+                const float4 x = sv[v], y = g0[v], z = g1[v];
+                const float4 x2 = sv[v + 2], y2 = g0[v + 2], z2 = g1[v + 2];
+                a0 = fmaf(x.x, y.x, a0); a0 = fmaf(x.y, y.y, a0); a0 = fmaf(x.z, y.z, a0); a0 = fmaf(x.w, y.w, a0);
+                a1 = fmaf(x.x, z.x, a1); a1 = fmaf(x.y, z.y, a1); a1 = fmaf(x.z, z.z, a1); a1 = fmaf(x.w, z.w, a1);
+                b0 = fmaf(x2.x, y2.x, b0); b0 = fmaf(x2.y, y2.y, b0); b0 = fmaf(x2.z, y2.z, b0); b0 = fmaf(x2.w, y2.w, b0);
+                b1 = fmaf(x2.x, z2.x, b1); b1 = fmaf(x2.y, z2.y, b1); b1 = fmaf(x2.z, z2.z, b1); b1 = fmaf(x2.w, z2.w, b1);
+              }
+              if (v < nv) {
+                const float4 x = sv[v], y = g0[v], z = g1[v];
+                a0 = fmaf(x.x, y.x, a0); a0 = fmaf(x.y, y.y, a0); a0 = fmaf(x.z, y.z, a0); a0 = fmaf(x.w, y.w, a0);
+                a1 = fmaf(x.x, z.x, a1); a1 = fmaf(x.y, z.y, a1); a1 = fmaf(x.z, z.z, a1); a1 = fmaf(x.w, z.w, a1);
+              }
+              acc[q][0] = a0 + b0;
+              acc[q][1] = a1 + b1;
+            }
+          }
+        }
+        // combine the two halves, residual e_s = a_n . E_s - x_s (shuffle sum
+        // over the sample's lanes), then the contributions e_s E_s
 #pragma unroll
         for (int q = 0; q < kOutPerThread; ++q) {
-          const int o = tid + q * T;
-          const int s = o >> lg, rem = o & ((1 << lg) - 1), jt = rem >> 1, h = rem & 1;
-          if (o < nout && jt < ntj) {
+          const int o0 = q * T;
+          if (o0 < nout) {   // uniform across the block
+            const int o = tid + o0;
+            const int s = o >> lg, rem = o & ((1 << lg) - 1), jt = rem >> 1, h = rem & 1;
+            const bool live = (o < nout) && (jt < ntj);
             const int j0 = 2 * jt;
-            const float4* sv = reinterpret_cast<const float4*>(Sbuf + s * ctile_cap);
-            const float4* g0 = reinterpret_cast<const float4*>(GT + j0 * Pp + c0);
-            const float4* g1 = reinterpret_cast<const float4*>(GT + min(j0 + 1, Jn - 1) * Pp + c0);
-            float a0 = acc[q][0], a1 = acc[q][1], b0 = 0.f, b1 = 0.f;
-            const int nv = ct >> 2;
-            int v = h;
-            for (; v + 2 < nv; v += 4) {
-              const float4 x = sv[v], y = g0[v], z = g1[v];
-              const float4 x2 = sv[v + 2], y2 = g0[v + 2], z2 = g1[v + 2];
-              a0 = fmaf(x.x, y.x, a0); a0 = fmaf(x.y, y.y, a0); a0 = fmaf(x.z, y.z, a0); a0 = fmaf(x.w, y.w, a0);
-              a1 = fmaf(x.x, z.x, a1); a1 = fmaf(x.y, z.y, a1); a1 = fmaf(x.z, z.z, a1); a1 = fmaf(x.w, z.w, a1);
-              b0 = fmaf(x2.x, y2.x, b0); b0 = fmaf(x2.y, y2.y, b0); b0 = fmaf(x2.z, y2.z, b0); b0 = fmaf(x2.w, y2.w, b0);
-              b1 = fmaf(x2.x, z2.x, b1); b1 = fmaf(x2.y, z2.y, b1); b1 = fmaf(x2.z, z2.z, b1); b1 = fmaf(x2.w, z2.w, b1);
+            float e0 = acc[q][0] + __shfl_xor_sync(0xffffffffu, acc[q][0], 1);
+            float e1 = acc[q][1] + __shfl_xor_sync(0xffffffffu, acc[q][1], 1);
+            float part = 0.f;
+            if (live && h == 0) {
+              const float* an = rows + s * sumJ + joff[n];
+              part = an[j0] * e0;
+              if (j0 + 1 < Jn) part = fmaf(an[j0 + 1], e1, part);
             }
-            if (v < nv) {
-              const float4 x = sv[v], y = g0[v], z = g1[v];
-              a0 = fmaf(x.x, y.x, a0); a0 = fmaf(x.y, y.y, a0); a0 = fmaf(x.z, y.z, a0); a0 = fmaf(x.w, y.w, a0);
-              a1 = fmaf(x.x, z.x, a1); a1 = fmaf(x.y, z.y, a1); a1 = fmaf(x.z, z.z, a1); a1 = fmaf(x.w, z.w, a1);
+            for (int off = 1 << (lg - 1); off > 0; off >>= 1) part += __shfl_xor_sync(0xffffffffu, part, off);
+            if (live && h == 0) {
+              const float e = part - fx[s];
+              Ebuf[s * Jmax + j0] = e * e0;
+              if (j0 + 1 < Jn) Ebuf[s * Jmax + j0 + 1] = e * e1;
             }
-            acc[q][0] = a0 + b0;
-            acc[q][1] = a1 + b1;
           }
         }
+        __syncthreads();
       }
-      // combine the two halves, residual e_s = a_n . E_s - x_s (shuffle sum
-      // over the sample's lanes), then the contributions e_s E_s
-#pragma unroll
-      for (int q = 0; q < kOutPerThread; ++q) {
-        const int o0 = q * T;
-        if (o0 < nout) {   // uniform across the block
-          const int o = tid + o0;
-          const int s = o >> lg, rem = o & ((1 << lg) - 1), jt = rem >> 1, h = rem & 1;
-          const bool live = (o < nout) && (jt < ntj);
-          const int j0 = 2 * jt;
-          float e0 = acc[q][0] + __shfl_xor_sync(0xffffffffu, acc[q][0], 1);
-          float e1 = acc[q][1] + __shfl_xor_sync(0xffffffffu, acc[q][1], 1);
-          float part = 0.f;
-          if (live && h == 0) {
-            const float* an = rows + s * sumJ + joff[n];
-            part = an[j0] * e0;
-            if (j0 + 1 < Jn) part = fmaf(an[j0 + 1], e1, part);
-          }
-          for (int off = 1 << (lg - 1); off > 0; off >>= 1) part += __shfl_xor_sync(0xffffffffu, part, off);
-          if (live && h == 0) {
-            const float e = part - fx[s];
-            Ebuf[s * Jmax + j0] = e * e0;
-            if (j0 + 1 < Jn) Ebuf[s * Jmax + j0 + 1] = e * e1;
-          }
-        }
-      }
-      __syncthreads();
       // run sums: segmented inclusive scan of the contributions over the
       // sorted samples, one warp per column j, 32 samples at a time
       for (int j = warp; j < Jn; j += nwarps) {
@@ -764,9 +900,13 @@ k_epoch(EpochArgs a) {
         if (st >= lo && en < hi) {
           const float F = Fbuf[h * Jmax + j];
           const float denom = a.norm_mode == 1 ? (float)(en - st + 1) : fm;
-          float* ap = a.A[n] + (size_t)fcrd[s0 * N + n] * g.Jp[n] + j;
-          const float av = rows[s0 * sumJ + joff[n] + j];
-          __stcg(ap, av - a.lr_a * (F / denom + a.lam_a * av));
+          const int row = fcrd[s0 * N + n];
+          float* ap = a.A[n] + (size_t)row * g.Jp[n] + j;
+          const float av = bf ? __ldcg(ap) : rows[s0 * sumJ + joff[n] + j];
+          const float nv = av - a.lr_a * (F / denom + a.lam_a * av);
+          __stcg(ap, nv);
+          if (bf) __stcg(reinterpret_cast<unsigned short*>(a.Ab[n]) + (size_t)row * g.Jb[n] + j,
+                         __bfloat16_as_ushort(__float2bfloat16_rn(nv)));
           if (probe && a.probeF) a.probeF[((size_t)n * M + st) * kMaxJ + j] = F;
         }
       }
@@ -796,9 +936,13 @@ k_epoch(EpochArgs a) {
               float F = __ldcg(a.bpart + ((size_t)c0 * 2 + 1) * kMaxJ + lane);
               for (int cc = c0 + 1; cc <= c1; ++cc) F += __ldcg(a.bpart + ((size_t)cc * 2 + 0) * kMaxJ + lane);
               const float denom = a.norm_mode == 1 ? (float)(en - st + 1) : fm;
-              float* ap = a.A[n] + (size_t)fcrd[s0 * N + n] * g.Jp[n] + lane;
-              const float av = rows[s0 * sumJ + joff[n] + lane];
-              __stcg(ap, av - a.lr_a * (F / denom + a.lam_a * av));
+              const int row = fcrd[s0 * N + n];
+              float* ap = a.A[n] + (size_t)row * g.Jp[n] + lane;
+              const float av = bf ? __ldcg(ap) : rows[s0 * sumJ + joff[n] + lane];
+              const float nv = av - a.lr_a * (F / denom + a.lam_a * av);
+              __stcg(ap, nv);
+              if (bf) __stcg(reinterpret_cast<unsigned short*>(a.Ab[n]) + (size_t)row * g.Jb[n] + lane,
+                             __bfloat16_as_ushort(__float2bfloat16_rn(nv)));
               if (probe && a.probeF) a.probeF[((size_t)n * M + st) * kMaxJ + lane] = F;
             }
             if (lane == 0) a.bcnt[c1] = 0u;
@@ -810,10 +954,14 @@ k_epoch(EpochArgs a) {
         const int nt = T - 64, t2 = tid - 64;
         const int n1 = n + 1, Pn1 = g.prodJ / Jr[n1], Pp1 = pad4(Pn1);
         const int* cof1 = coff + toff + Pn;
-        float* GT1 = GTb[n1 & 1];
-        for (int i = t2; i < Jr[n1] * Pp1; i += nt) {
-          const int j = i / Pp1, cc = i - j * Pp1;
-          GT1[i] = cc < Pn1 ? Gsm[cof1[cc] + j * g.gstride[n1]] : 0.f;
+        if (bf) {
+          build_gt_bf16(GThb[n1 & 1], Gsm, cof1, Jr[n1], Pn1, g.gstride[n1], t2, nt);
+        } else {
+          float* GT1 = GTb[n1 & 1];
+          for (int i = t2; i < Jr[n1] * Pp1; i += nt) {
+            const int j = i / Pp1, cc = i - j * Pp1;
+            GT1[i] = cc < Pn1 ? Gsm[cof1[cc] + j * g.gstride[n1]] : 0.f;
+          }
         }
       }
       {
@@ -879,8 +1027,8 @@ int epoch_payload_floats(const Geometry& g) {
   return mx;
 }
 
-size_t epoch_smem_bytes(const Geometry& g, int chunk_max, int payload_max) {
-  return (size_t)smem_layout(g, chunk_max, payload_max).total_words * sizeof(float);
+size_t epoch_smem_bytes(const Geometry& g, int chunk_max, int payload_max, int precision) {
+  return (size_t)smem_layout(g, chunk_max, payload_max, precision).total_words * sizeof(float);
 }
 
 cudaError_t epoch_kernel_setup(int N, size_t smem) {

@@ -78,6 +78,7 @@ struct Geometry {
   int R;
   int J[kMaxN];
   int Jp[kMaxN];        // row stride of the FP32 factor matrices (J_n rounded up to 4)
+  int Jb[kMaxN];        // row stride of the BF16 factor mirrors (J_n rounded up to 8)
   int boff[kMaxN];      // offset of B(n) (J_n x R, row-major) in the concatenated B
   int joff[kMaxN];      // offset of mode n's row inside a sample's concatenated rows
   int gstride[kMaxN];   // stride of j_n in G-hat (mode 1 fastest)
@@ -108,6 +109,8 @@ struct Schedule {
 struct EpochArgs {
   Geometry g;
   float* A[kMaxN];       // FP32 factor masters, I_n x Jp_n
+  uint16_t* Ab[kMaxN];   // BF16 mirrors of A (precision 1), I_n x Jb_n
+  int precision;         // 0 FP32; 1 BF16 gathers and tensor-core contraction
   float* B;              // concatenated Kruskal matrices (read at start, written at end)
   float* core;           // G-hat output (prod J), written at end
   Schedule s;
@@ -139,8 +142,9 @@ struct AParams {
 cudaError_t launch_schedule(const Geometry& g, const uint32_t* coo, int cs, const Feistel& f,
                             const Schedule& s, int64_t b0, int64_t b1, cudaStream_t st);
 int epoch_payload_floats(const Geometry& g);
+cudaError_t launch_mirror_bf16(const Geometry& g, float* const* A, uint16_t* const* Ab, cudaStream_t st);
 int epoch_chunk_cap(const Geometry& g);   // largest samples per CTA per phase the kernel takes
-size_t epoch_smem_bytes(const Geometry& g, int chunk_max, int payload_max);
+size_t epoch_smem_bytes(const Geometry& g, int chunk_max, int payload_max, int precision);
 cudaError_t epoch_kernel_setup(int N, size_t smem);
 int epoch_max_ctas(int N, size_t smem);
 cudaError_t launch_epoch(const EpochArgs& a, int ctas, size_t smem, cudaStream_t st);

@@ -3,6 +3,8 @@
 // RMSE-MAE reduction of Eq. 19.
 #include <cmath>
 
+#include <cuda_bf16.h>
+
 #include "sgdt_internal.cuh"
 
 namespace sgdt {
@@ -163,6 +165,16 @@ __global__ void k_rmse_finish(const double* __restrict__ partials, int blocks, d
   if (threadIdx.x == 0) { result[0] = s1[0]; result[1] = s2[0]; }
 }
 
+// BF16 mirror of an FP32 factor matrix (round to nearest even; padding 0).
+__global__ void k_mirror_bf16(const float* __restrict__ A, uint16_t* __restrict__ Ab, int64_t I, int J, int Jp,
+                              int Jb) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < I * Jb; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t row = i / Jb;
+    const int j = (int)(i - row * Jb);
+    Ab[i] = j < J ? __bfloat16_as_ushort(__float2bfloat16_rn(A[row * Jp + j])) : (uint16_t)0;
+  }
+}
+
 static int grid_for(int64_t work, int threads) {
   int64_t b = (work + threads - 1) / threads;
   if (b < 1) b = 1;
@@ -193,6 +205,16 @@ cudaError_t launch_init_params(const Geometry& g, float* const* A, float* B, int
   }
   k_init_kruskal<<<1, 256, 0, st>>>(B, g, mode, mu, sigma, seed);
   return cudaGetLastError();
+}
+
+cudaError_t launch_mirror_bf16(const Geometry& g, float* const* A, uint16_t* const* Ab, cudaStream_t st) {
+  for (int n = 0; n < g.N; ++n) {
+    if (!Ab[n]) continue;
+    k_mirror_bf16<<<grid_for(g.I[n] * g.Jb[n], 256), 256, 0, st>>>(A[n], Ab[n], g.I[n], g.J[n], g.Jp[n], g.Jb[n]);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
 }
 
 cudaError_t launch_build_core(const Geometry& g, const float* B, float* core, cudaStream_t st) {

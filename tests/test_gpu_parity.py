@@ -269,3 +269,62 @@ def test_checkpoint_resume_is_bit_identical(B, synth, cfg1):
     for x, y in zip(full[0] + full[1], resumed[0] + resumed[1]):
         assert np.array_equal(x, y)
     assert resumed[3] == 3
+
+
+# ---------------------------------------------------------------------------
+# BF16 form: BF16 factor mirrors for the gathers, BF16 unfolded core and
+# Kronecker rows on tensor cores, FP32 accumulation and FP32 masters.  Bar:
+# its train/test RMSE tracks the FP32 form within 1e-3 absolute per epoch.
+# ---------------------------------------------------------------------------
+
+def _rmse_track(B, synth, tensor, ranks, R, M, lr, lam, epochs, init="normal"):
+    c, v = tensor.split("train")
+    tc, tv = tensor.split("test")
+    A0, B0 = synth.init_params(tensor.shape, ranks, R, mode=init, seed=1, mean_value=float(np.mean(v)))
+    worst = 0.0
+    with _gpu(B, tensor.shape, ranks, R, c, v, A0, B0) as g32, \
+            _gpu(B, tensor.shape, ranks, R, c, v, A0, B0, precision=1) as g16:
+        for ep in range(epochs):
+            g32.epoch(lr, lr, lam, lam, M)
+            g16.epoch(lr, lr, lam, lam, M)
+            for cc, vv in ((c, v), (tc, tv)):
+                if cc.shape[0] == 0:
+                    continue
+                r32, m32 = g32.rmse(cc, vv)
+                r16, m16 = g16.rmse(cc, vv)
+                worst = max(worst, abs(r32 - r16), abs(m32 - m16))
+    return worst
+
+
+def test_bf16_rmse_tracks_fp32_config1(B, synth, cfg1):
+    worst = _rmse_track(B, synth, cfg1.tensor, cfg1.ranks, 5, 256, 0.5, 1e-3, 10)
+    assert worst <= 1e-3, worst
+
+
+def test_bf16_rmse_tracks_fp32_rating(B, synth):
+    w = synth.config2(scale=0.004)
+    worst = _rmse_track(B, synth, w.tensor, w.ranks, 5, 4096, 0.05, 1e-3, 5, init="rating")
+    assert worst <= 1e-3, worst
+
+
+def test_bf16_rmse_tracks_fp32_4order(B, synth):
+    w = synth.config3(scale=0.004)
+    worst = _rmse_track(B, synth, w.tensor, w.ranks, 5, 8192, 0.5, 1e-3, 5)
+    assert worst <= 1e-3, worst
+
+
+def test_bf16_step_gradients_close_to_oracle(B, synth, cfg1):
+    """One step in the BF16 form: gradients within the BF16 rounding bound
+    (2^-8 relative per operand; 2e-2 norm-wise) of the FP64 oracle."""
+    c, v = cfg1.tensor.split("train")
+    A0, B0 = synth.init_params(cfg1.tensor.shape, cfg1.ranks, 5, mode="normal", seed=1)
+    ref = O.Model(cfg1.tensor.shape, cfg1.ranks, 5, A0, B0)
+    with _gpu(B, cfg1.tensor.shape, cfg1.ranks, 5, c, v, A0, B0, precision=1) as g:
+        pr = g.batches(0.3, 0.2, 0.01, 0.02, 256, 0, 1, probe=True)
+    sched = O.perm_range(c.shape[0], 2, 0, 0, 256)
+    V, F, nseg = ref.step(c[sched], v[sched], 0.3, 0.2, 0.01, 0.02, probe=True)
+    for n in range(3):
+        assert _rel(pr["core_V"][n, :5, :5], V[n, :5, :5]) <= 2e-2
+        U = int(nseg[n])
+        assert pr["nseg"][n] == U
+        assert _rel(pr["factor_F"][n, :U, :5], F[n, :U, :5]) <= 2e-2
