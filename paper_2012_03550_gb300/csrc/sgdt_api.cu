@@ -57,14 +57,16 @@ struct std_ctx {
   size_t sched_bytes = 0;
   int64_t sched_epoch = -1;
   int sched_M = 0;
-  // epoch scratch
-  float* part = nullptr;
-  size_t part_floats = 0;
-  float* red = nullptr;
-  size_t red_floats = 0;
-  float* bpart = nullptr;
-  unsigned* bcnt = nullptr;
-  int scratch_ctas = 0;
+  // epoch exchange words (tagged; see k_epoch)
+  unsigned long long* part = nullptr;
+  size_t part_words = 0;
+  unsigned long long* inbox = nullptr;
+  size_t inbox_words = 0;
+  unsigned long long* piece = nullptr;
+  size_t piece_words = 0;
+  unsigned long long* mail = nullptr;
+  size_t mail_words = 0;
+  uint32_t tag_base = 1;
   // probe
   float* probe_mem = nullptr;
   size_t probe_floats = 0;
@@ -134,7 +136,7 @@ int ensure_schedule(std_ctx* c, int M) {
   const int N = c->g.N;
   const int64_t nb = (c->nnz + M - 1) / M;
   const int64_t npad = nb * M;
-  const size_t words = (size_t)npad * ((size_t)N * (N + 3) + 1);
+  const size_t words = (size_t)npad * schedule_words_per_position(N);
   const size_t bytes = words * 4;
   if (bytes > c->sched_bytes) {
     dev_free(c, c->sched_mem, c->sched_bytes);
@@ -151,6 +153,8 @@ int ensure_schedule(std_ctx* c, int M) {
   s.pos = base + (size_t)npad * (N * N + N);
   s.seg = reinterpret_cast<uint32_t*>(base + (size_t)npad * (N * N + 2 * N));
   s.sid = base + (size_t)npad * (N * N + 3 * N);
+  s.link = s.sid + (size_t)npad;
+  s.rsp = s.link + (size_t)npad * (N * (N - 1) / 2);
   s.npad = npad;
   s.n = c->nnz;
   s.M = M;
@@ -165,7 +169,9 @@ int ensure_schedule(std_ctx* c, int M) {
 int choose_ctas(std_ctx* c, int M, int* ctas, int* chunk_max, size_t* smem) {
   const int payload = payload_floats(c->g);
   if (payload > kMaxCorePayload)
-    return set_error(STD_EUNSUPPORTED, "core reduction payload R*J + R(R-1)/2*J*J exceeds 8192 floats");
+    return set_error(STD_EUNSUPPORTED, "core reduction payload R*J + R(R-1)/2*J(J+1)/2 exceeds 8192 floats");
+  if (!epoch_gram_fits(c->g))
+    return set_error(STD_EUNSUPPORTED, "core reduction tiles exceed the epoch kernel's per-thread limit");
   const int cap = epoch_chunk_cap(c->g);
   int G = c->opt.ctas;
   if (G <= 0) {
@@ -175,19 +181,25 @@ int choose_ctas(std_ctx* c, int M, int* ctas, int* chunk_max, size_t* smem) {
     if (G < need) G = need;
   }
   if (G < 1) G = 1;
+  if (G > kMaxEpochCtas) {
+    if (c->opt.ctas > 0) return set_error(STD_EINVAL, "requested CTA count exceeds the epoch kernel's limit (256)");
+    G = kMaxEpochCtas;
+  }
   int ch = (M + G - 1) / G;
   if (ch > cap) return set_error(STD_EUNSUPPORTED, "minibatch too large for the CTA count at these ranks");
-  size_t sm = epoch_smem_bytes(c->g, ch, payload, c->opt.precision);
+  size_t sm = epoch_smem_bytes(c->g, ch, G, c->opt.precision);
   if (sm > 227 * 1024) return set_error(STD_EUNSUPPORTED, "shape needs more shared memory than a CTA has");
-  STD_CUDA(epoch_kernel_setup(c->g.N, sm), "epoch kernel attributes");
-  const int maxG = epoch_max_ctas(c->g.N, sm);
+  STD_CUDA(epoch_kernel_setup(c->opt.precision, sm), "epoch kernel attributes");
+  const int maxG = epoch_max_ctas(c->opt.precision, sm);
   if (maxG < 1) return set_error(STD_EUNSUPPORTED, "epoch kernel cannot be resident");
   if (G > maxG) {
     if (c->opt.ctas > 0) return set_error(STD_EINVAL, "requested CTA count exceeds co-resident capacity");
     G = maxG;
     ch = (M + G - 1) / G;
     if (ch > cap) return set_error(STD_EUNSUPPORTED, "minibatch too large for the co-resident CTAs at these ranks");
-    sm = epoch_smem_bytes(c->g, ch, payload, c->opt.precision);
+    sm = epoch_smem_bytes(c->g, ch, G, c->opt.precision);
+    if (sm > 227 * 1024) return set_error(STD_EUNSUPPORTED, "shape needs more shared memory than a CTA has");
+    STD_CUDA(epoch_kernel_setup(c->opt.precision, sm), "epoch kernel attributes");
   }
   *ctas = G;
   *chunk_max = ch;
@@ -195,36 +207,47 @@ int choose_ctas(std_ctx* c, int M, int* ctas, int* chunk_max, size_t* smem) {
   return STD_OK;
 }
 
-int ensure_scratch(std_ctx* c, int G, int payload) {
-  const size_t pf = (size_t)G * payload;
-  if (pf > c->part_floats) {
-    dev_free(c, c->part, c->part_floats * 4);
-    c->part = nullptr;
-    c->part_floats = 0;
-    int rc = dev_alloc(c, (void**)&c->part, pf * 4, "core partials");
-    if (rc) return rc;
-    c->part_floats = pf;
+// Grows one exchange buffer to at least `words` tagged words; a new buffer
+// starts zeroed (tag 0, which no exchange uses).
+int ensure_words(std_ctx* c, unsigned long long** p, size_t* have, size_t words, const char* what) {
+  if (words <= *have) return STD_OK;
+  dev_free(c, *p, *have * 8);
+  *p = nullptr;
+  *have = 0;
+  int rc = dev_alloc(c, (void**)p, words * 8, what);
+  if (rc) return rc;
+  *have = words;
+  STD_CUDA(cudaMemsetAsync(*p, 0, words * 8, c->stream), what);
+  return STD_OK;
+}
+
+int exchange_pstride(int payload) { return (payload + 7) & ~7; }
+
+int ensure_scratch(std_ctx* c, int G, int payload, int M) {
+  const size_t ps = (size_t)exchange_pstride(payload);
+  const size_t NJ = (size_t)c->g.N * c->g.Jmax;
+  int rc = ensure_words(c, &c->part, &c->part_words, (size_t)G * ps, "core partials");
+  if (!rc) rc = ensure_words(c, &c->inbox, &c->inbox_words, (size_t)G * ps, "core reduction copies");
+  if (!rc) rc = ensure_words(c, &c->piece, &c->piece_words, (size_t)G * NJ, "run pieces");
+  if (!rc) rc = ensure_words(c, &c->mail, &c->mail_words, (size_t)M * NJ, "row slots");
+  return rc;
+}
+
+// Tags of one launch over `batches` minibatches: tag_base + 8 (b - b0) + n.
+// Before the 32-bit sequence would wrap, every exchange word is cleared and
+// the sequence restarts at 1, so a stale word never carries a live tag.
+int reserve_tags(std_ctx* c, int64_t batches, uint32_t* base) {
+  const uint64_t span = (uint64_t)batches * 8ULL + 8ULL;
+  if (span >= 0x80000000ULL) return set_error(STD_EUNSUPPORTED, "too many minibatches in one launch");
+  if ((uint64_t)c->tag_base + span >= 0xFFFFFFF0ULL) {
+    STD_CUDA(cudaMemsetAsync(c->part, 0, c->part_words * 8, c->stream), "exchange reset");
+    STD_CUDA(cudaMemsetAsync(c->inbox, 0, c->inbox_words * 8, c->stream), "exchange reset");
+    STD_CUDA(cudaMemsetAsync(c->piece, 0, c->piece_words * 8, c->stream), "exchange reset");
+    STD_CUDA(cudaMemsetAsync(c->mail, 0, c->mail_words * 8, c->stream), "exchange reset");
+    c->tag_base = 1;
   }
-  if ((size_t)payload > c->red_floats) {
-    dev_free(c, c->red, c->red_floats * 4);
-    c->red = nullptr;
-    c->red_floats = 0;
-    int rc = dev_alloc(c, (void**)&c->red, (size_t)payload * 4, "core reduction");
-    if (rc) return rc;
-    c->red_floats = payload;
-  }
-  if (G > c->scratch_ctas) {
-    dev_free(c, c->bpart, (size_t)c->scratch_ctas * 2 * kMaxJ * 4);
-    dev_free(c, c->bcnt, (size_t)c->scratch_ctas * 4);
-    c->bpart = nullptr;
-    c->bcnt = nullptr;
-    c->scratch_ctas = 0;
-    int rc = dev_alloc(c, (void**)&c->bpart, (size_t)G * 2 * kMaxJ * 4, "run pieces");
-    if (rc) return rc;
-    rc = dev_alloc(c, (void**)&c->bcnt, (size_t)G * 4, "run counters");
-    if (rc) return rc;
-    c->scratch_ctas = G;
-  }
+  *base = c->tag_base;
+  c->tag_base += (uint32_t)span;
   return STD_OK;
 }
 
@@ -247,7 +270,10 @@ int run_batches(std_ctx* c, float lr_a, float lr_b, float lam_a, float lam_b, in
   rc = choose_ctas(c, M, &G, &chunk, &smem);
   if (rc) return rc;
   const int payload = payload_floats(c->g);
-  rc = ensure_scratch(c, G, payload);
+  rc = ensure_scratch(c, G, payload, M);
+  if (rc) return rc;
+  uint32_t tag_base = 0;
+  rc = reserve_tags(c, b1 - b0, &tag_base);
   if (rc) return rc;
   float* pV = nullptr;
   float* pF = nullptr;
@@ -283,18 +309,18 @@ int run_batches(std_ctx* c, float lr_a, float lr_b, float lam_a, float lam_b, in
   a.lam_b = lam_b;
   a.norm_mode = c->opt.norm_mode;
   a.chunk_max = chunk;
-  a.payload_max = payload;
+  a.tag_base = tag_base;
   a.part = c->part;
-  a.red = c->red;
-  a.bpart = c->bpart;
-  a.bcnt = c->bcnt;
+  a.inbox = c->inbox;
+  a.piece = c->piece;
+  a.mail = c->mail;
+  a.pstride = exchange_pstride(payload);
   a.bar = c->bar;
   a.err = c->err;
   a.watchdog_ns = c->opt.watchdog_ns ? c->opt.watchdog_ns : 2000000000ULL;
   a.probe_batch = probe ? b0 : -1;
   a.probeV = pV;
   a.probeF = pF;
-  STD_CUDA(cudaMemsetAsync(c->bcnt, 0, (size_t)G * 4, c->stream), "run counters clear");
   STD_CUDA(cudaMemsetAsync(c->bar, 0, sizeof(unsigned long long), c->stream), "barrier clear");
   if (record_end) STD_CUDA(cudaEventRecord(c->evm, c->stream), "event");
   if (b1 > b0) STD_CUDA(launch_epoch(a, G, smem, c->stream), "epoch kernel launch");
@@ -356,8 +382,8 @@ int std_destroy(std_ctx* c) {
     if (c->A[n]) cudaFree(c->A[n]);
     if (c->Ab[n]) cudaFree(c->Ab[n]);
   }
-  void* ptrs[] = {c->coo, c->B, c->core, c->err, c->bar, c->sched_mem, c->part, c->red,
-                  c->bpart, c->bcnt, c->probe_mem, c->stage, c->rpart, c->result};
+  void* ptrs[] = {c->coo, c->B, c->core, c->err, c->bar, c->sched_mem, c->part, c->inbox,
+                  c->piece, c->mail, c->probe_mem, c->stage, c->rpart, c->result};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (c->ev0) cudaEventDestroy(c->ev0);

@@ -2,46 +2,58 @@
 //
 // One cooperative launch holds G co-resident CTAs (one per SM) for the whole
 // range.  Each minibatch (m samples) is split into G contiguous chunks of
-// ceil(m/G) samples per phase; phases are separated by grid barriers with a
-// watchdog.  The kernel is instantiated per order N so that every loop over
-// modes unrolls; the work inside a phase is a handful of block-wide steps
-// (small register-tiled products over the chunk's samples, warp-shuffle
-// reductions per sample), and the next phase's schedule is prefetched into a
-// second shared-memory buffer while the current phase runs.
+// ceil(m/G) samples.  The chain of dependent phases per minibatch (N core
+// modes, the core rebuild, N factor modes) makes the kernel latency-bound, so
+// it is built to shorten that chain:
+//  - per minibatch there is one grid barrier, so that the next minibatch
+//    gathers every row this one updated;
+//  - everything exchanged between CTAs inside a minibatch travels as 64-bit
+//    words (sequence tag << 32 | float bits), written with relaxed stores and
+//    polled with relaxed loads until the tag of the current (minibatch, mode)
+//    shows up.  A 64-bit access is single-copy atomic, so a reader that sees
+//    the tag sees the value written with it: no fence and no barrier, and a
+//    consumer waits only for the words it needs.  Every wait is bounded by a
+//    watchdog (error word + early return);
+//  - each CTA step is written for a short per-warp instruction stream:
+//    compact code (mode loops are not unrolled, per-mode constants live in
+//    shared memory), divisions by launch constants through multiply-high,
+//    operand rows built once per minibatch, and register-tiled products.
 //
 // Core phase (Algorithm 1 lines 1-15; Eq. 7, Eq. 15).  A is fixed during the
 // phase: each CTA gathers its samples' N factor rows once and keeps
 //   p[s][k][r] = <a_k(s), b(k)_r>.
 // For mode n the line-5 product W_r = H O_r has the closed form
-// W_r[s] = a_n(s) * w[s][r], w[s][r] = prod_{k != n} p[s][k][r] (mixed-product
-// property of the Kronecker product, Eq. 7), i.e. the rows of all W_r together
-// are Y_s = w_s (x) a_n(s) (length R*J_n).  The line-13 vector of column r
+// W_r[s] = w[s][r] a_n(s), w[s][r] = prod_{k != n} p[s][k][r] (mixed-product
+// property of the Kronecker product, Eq. 7).  The line-13 vector of column r
 // after columns r' < r moved by Delta_{r'} is
 //   V_r = g_r + sum_{r' < r} C_{r r'} Delta_{r'},
-//   g_r = sum_s W_r[s] e_s,  C_{r r'} = sum_s W_r[s] W_{r'}[s]^T,
-//   e_s = sum_r W_r[s].b_r - x_s at the start of the mode,
-// the exact algebra of lines 8-13 (the line 8-11 residual is e_s plus the moves
-// already made).  So g and the blocks C_{r r'} (r' < r) are parts of the Gram
-// matrix of [Y | e] over the samples: one register-tiled product per CTA, one
-// grid-wide reduction per mode (every CTA writes its partial, CTA c sums a
-// slice over all CTAs in a fixed order), and after a second barrier every CTA
-// replays the R cyclic SGD steps (line 14) as a block forward substitution on
-// the same numbers, so all CTAs hold bit-identical B without a broadcast.
+//   g_r = sum_s e_s w[s][r] a_n(s),  C_{r r'} = sum_s w[s][r] w[s][r'] a_n(s) a_n(s)^T,
+//   e_s = sum_r w[s][r] p[s][n][r] - x_s at the start of the mode,
+// the exact algebra of lines 8-13 (the line 8-11 residual is e_s plus the
+// moves already made).  Each C_{r r'} is symmetric, so the payload is g plus
+// the upper triangles of the blocks r' < r.  Reduction over the CTAs in two
+// tagged hops: every CTA publishes its partial payload; CTA c sums a slice of
+// it over all CTAs in a fixed order and pushes the sums into every CTA's own
+// copy of the payload (so each CTA then polls lines nobody else reads); every
+// CTA replays the R cyclic SGD steps (line 14) on identical numbers, so all
+// CTAs hold bit-identical B without a broadcast.
 //
 // Core rebuild (line 16, Eq. 4) is done redundantly by every CTA.
 //
 // Factor phase (lines 17-25; Eqs. 10, 11, 18), mode after mode, samples
 // sorted by i_n (tiler) so that each row's samples form one run.  Per chunk:
-// the Kronecker rows S_s (Eq. 10, Def. 1 column order) are built tile by
-// tile in shared memory and contracted with the unfolded core,
-// E_s = G_(n) S_s^T, by (sample, column-pair) register tiles; the residual
-// e_s = a_n . E_s - x_s is reduced across each sample's lanes with shuffles,
-// and the row sums F = sum_s e_s E_s (the row's -X E^T + a E E^T of line 22)
-// come from segmented scans over the sorted samples.  Runs inside the chunk
-// are applied by the owning CTA; a run that crosses chunks is summed per
-// chunk and the last contributor (an acquire-release arrival count per run)
-// adds the pieces in chunk order and applies the update, so the result does
-// not depend on arrival order and no floating-point atomics are used.
+// the Kronecker rows S_s (Eq. 10, Def. 1 column order) are built in shared
+// memory and contracted with the unfolded core, E_s = G_(n) S_s^T; the
+// residual e_s = a_n . E_s - x_s is reduced across each sample's lanes with
+// shuffles, and the row sums F = sum_s e_s E_s (the row's -X E^T + a E E^T of
+// line 22) are summed per run in sorted order.  A run inside the chunk is
+// applied by this CTA.  A run that continues from an earlier chunk is
+// published as a tagged piece; the CTA where the run starts polls the pieces,
+// adds them in chunk order and applies the update, so no floating-point
+// atomics are used and the result does not depend on timing.  Each updated
+// row is also published, tagged, under its run start; later modes of the
+// same minibatch (which need the rows of modes k < n as updated, Gauss-Seidel
+// order) poll those slots, found through the tiler's links.
 #include <cuda_bf16.h>
 
 #include "sgdt_internal.cuh"
@@ -50,8 +62,9 @@ namespace sgdt {
 
 namespace {
 
-constexpr int kCTile = 256;        // Kronecker-row columns per shared-memory tile
-constexpr int kOutPerThread = 2;   // (sample, column pair, half) tiles per thread
+constexpr int kRightBudget = 16384;  // floats of precomputed right Gram operands (all modes)
+constexpr int kSBudget = 32768;      // floats of Kronecker rows materialised at once (FP32 form)
+constexpr int kMaxSmemBytes = 227 * 1024;
 
 __host__ __device__ inline int pad4(int x) { return (x + 3) & ~3; }
 
@@ -60,6 +73,10 @@ __host__ __device__ inline int pow2_at_least(int x) {
   while (p < x) p <<= 1;
   return p;
 }
+
+__host__ __device__ inline int round_up(int x, int m) { return (x + m - 1) / m * m; }
+
+__host__ __device__ inline int tri(int J) { return J * (J + 1) / 2; }
 
 __host__ __device__ inline int max_pn(const Geometry& g) {
   int mx = 1;
@@ -76,7 +93,26 @@ __host__ __device__ inline int sum_pn(const Geometry& g) {
   return s;
 }
 
-__host__ __device__ inline int round_up(int x, int m) { return (x + m - 1) / m * m; }
+// Core-phase payload of mode n: g (R x J_n) and the upper triangles of the
+// R(R-1)/2 blocks C_{r r'}, r' < r.
+__host__ __device__ inline int core_payload(int Jn, int R) { return R * Jn + (R * (R - 1) / 2) * tri(Jn); }
+
+__host__ __device__ inline int payload_max(const Geometry& g) {
+  int mx = 0;
+  for (int n = 0; n < g.N; ++n) mx = core_payload(g.J[n], g.R) > mx ? core_payload(g.J[n], g.R) : mx;
+  return mx;
+}
+
+// The reduced payload in shared memory: g (R x J_n, padded to 4), then every
+// block C_{r r'} unpacked to full J_n x pad4(J_n) rows.
+__host__ __device__ inline int unpacked_payload(int Jn, int R) {
+  return pad4(R * Jn) + (R * (R - 1) / 2) * Jn * pad4(Jn);
+}
+
+// Width of a sample's Gram operand rows: left = [w_r w_r' (pairs) | e w_r],
+// right = [a_j a_j' (upper triangle, padded to 4) | a_j (padded to 4)].
+__host__ __device__ inline int left_width(const Geometry& g) { return g.R * (g.R - 1) / 2 + g.R; }
+__host__ __device__ inline int right_width(int Jn) { return pad4(tri(Jn)) + pad4(Jn); }
 
 // Row stride (in BF16 elements) of the Kronecker-row and unfolded-core tiles
 // of the tensor-core contraction: at least the K extent rounded up to 16, and
@@ -91,16 +127,20 @@ __host__ __device__ inline int bf16_row_stride(int Pn) {
   return kp;
 }
 
-// Row stride of Y' = [Y | e] in shared memory: R*Jmax + 1 columns plus one
-// spare (2-wide tiles may read one column past the residual), even.
-__host__ __device__ inline int ystride(const Geometry& g) { return (g.R * g.Jmax + 3) & ~1; }
-
 struct SmemLayout {
-  int B, G, GT[2], GTh[2], Sh, ldig, coff, cdig, rowtab, rows, p, w, Y, S, E, F, red, V, D;
-  int crd[2], xs[2], seg[2], head, total_words;
+  int B, G, GT, GTh, Sh, S, ldig, cdig, rowtab, trij, sc[2], rows, master, p, left, right, red, D, q, head, fown,
+      pbuf, total_words;
+  int lw, rw, sfloats, rpre;
 };
 
-__host__ __device__ inline SmemLayout smem_layout(const Geometry& g, int chunk, int payload, int precision) {
+// Words of one phase's schedule chunk: coordinates [s][N], value, run
+// bounds, links [s][N].
+__host__ __device__ inline int sched_chunk_words(int N, int chunk) { return (2 * N + 2) * chunk; }
+
+// Layout variant v: 0 = right Gram operands of all modes precomputed once per
+// minibatch and all Kronecker rows materialised; 1 = right operands rebuilt
+// per mode; 2 = also Kronecker entries formed on the fly in the contraction.
+__host__ __device__ inline SmemLayout smem_layout_v(const Geometry& g, int chunk, int ctas, int precision, int v) {
   SmemLayout L;
   int off = 0;
   auto take = [&](int words) {
@@ -108,46 +148,78 @@ __host__ __device__ inline SmemLayout smem_layout(const Geometry& g, int chunk, 
     off += pad4(words);
     return at;
   };
-  int sumJR = 0;
-  for (int n = 0; n < g.N; ++n) sumJR += g.J[n] * g.R;
+  int sumJR = 0, rwmax = 0, rwall = 0, redmax = 0;
+  for (int n = 0; n < g.N; ++n) {
+    sumJR += g.J[n] * g.R;
+    rwmax = right_width(g.J[n]) > rwmax ? right_width(g.J[n]) : rwmax;
+    rwall += right_width(g.J[n]);
+    redmax = unpacked_payload(g.J[n], g.R) > redmax ? unpacked_payload(g.J[n], g.R) : redmax;
+  }
   const int Pmax = max_pn(g);
-  const int tile = Pmax < kCTile ? pad4(Pmax) : kCTile;
-  const int gt = g.Jmax * pad4(Pmax);
+  const bool bf = precision == 1;
+  L.lw = left_width(g);
+  L.rpre = (v == 0 && chunk * rwall <= kRightBudget) ? 1 : 0;
+  L.rw = L.rpre ? rwall : rwmax;
+  L.sfloats = (bf || v == 2) ? 0 : (chunk * pad4(Pmax) < kSBudget ? chunk * pad4(Pmax) : kSBudget);
+  const int kpmax = bf16_row_stride(Pmax);
   L.B = take(sumJR);
   L.G = take(g.prodJ);
-  const bool bf = precision == 1;
-  const int kpmax = bf16_row_stride(Pmax);
-  const int jn16 = round_up(g.Jmax, 16);
-  L.GT[0] = take(bf ? 0 : gt);
-  L.GT[1] = take(bf ? 0 : gt);
-  L.GTh[0] = take(bf ? jn16 * kpmax / 2 : 0);
-  L.GTh[1] = take(bf ? jn16 * kpmax / 2 : 0);
+  L.GT = take(bf ? 0 : g.Jmax * pad4(Pmax));
+  L.GTh = take(bf ? round_up(g.Jmax, 16) * kpmax / 2 : 0);
   L.Sh = take(bf ? round_up(chunk, 16) * kpmax / 2 : 0);
+  L.S = take(L.sfloats);
   L.ldig = take(g.prodJ);
-  L.coff = take(sum_pn(g));
   L.cdig = take(2 * sum_pn(g));
   L.rowtab = take(g.sumJ);
+  L.trij = take(tri(g.Jmax));
+  L.sc[0] = take(sched_chunk_words(g.N, chunk));
+  L.sc[1] = take(sched_chunk_words(g.N, chunk));
   L.rows = take(chunk * g.sumJ);
+  L.master = take(bf ? chunk * g.Jmax : 0);
   L.p = take(chunk * g.N * g.R);
-  L.w = take(chunk * g.R);
-  L.Y = take(chunk * ystride(g));
-  L.S = take(bf ? 0 : chunk * tile);
-  L.E = take(chunk * g.Jmax);
-  L.F = take(chunk * g.Jmax);
-  L.red = take(payload);
-  L.V = take(g.R * kMaxJ);
-  L.D = take(g.R * kMaxJ);
-  L.crd[0] = take(chunk * g.N);
-  L.crd[1] = take(chunk * g.N);
-  L.xs[0] = take(chunk);
-  L.xs[1] = take(chunk);
-  L.seg[0] = take(chunk);
-  L.seg[1] = take(chunk);
-  L.head = take(chunk + 1);
+  L.left = take(chunk * L.lw);
+  L.right = take(chunk * L.rw);
+  L.red = take(redmax);
+  L.D = take(64);
+  L.q = take(chunk * g.Jmax);
+  L.head = take(chunk + 2);
+  L.fown = take(32);
+  L.pbuf = take(ctas * g.Jmax);
   L.total_words = off;
   return L;
 }
 
+// The first variant whose shared memory fits a CTA.
+__host__ __device__ inline SmemLayout smem_layout(const Geometry& g, int chunk, int ctas, int precision) {
+  SmemLayout L = smem_layout_v(g, chunk, ctas, precision, 0);
+  if (L.total_words * 4 > kMaxSmemBytes) L = smem_layout_v(g, chunk, ctas, precision, 1);
+  if (L.total_words * 4 > kMaxSmemBytes) L = smem_layout_v(g, chunk, ctas, precision, 2);
+  return L;
+}
+
+// Division of small non-negative integers (< 2^31) by a launch constant d
+// with one multiply-high (Granlund & Montgomery 1994): q = (umulhi(x, mul) +
+// x) >> shr with shr = ceil(log2 d), mul = 2^32 (2^shr - d) / d + 1.
+struct FastDiv {
+  uint32_t mul, shr;
+};
+
+__host__ __device__ inline FastDiv make_fastdiv(uint32_t d) {
+  uint32_t s = 0;
+  while ((1ULL << s) < d) ++s;
+  FastDiv f;
+  f.shr = s;
+  f.mul = (uint32_t)(((1ULL << 32) * ((1ULL << s) - d)) / d + 1);
+  return f;
+}
+
+__device__ __forceinline__ int fdiv(int x, FastDiv f) {
+  return (int)((__umulhi((uint32_t)x, f.mul) + (uint32_t)x) >> f.shr);
+}
+
+// ---------------------------------------------------------------------------
+// Memory-model primitives.
+// ---------------------------------------------------------------------------
 __device__ __forceinline__ unsigned long long globaltimer_ns() {
   unsigned long long t;
   asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
@@ -164,13 +236,88 @@ __device__ __forceinline__ void red_release_add_u64(unsigned long long* p, unsig
   asm volatile("red.release.gpu.global.add.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
 
-__device__ __forceinline__ unsigned atom_acq_rel_add_u32(unsigned* p, unsigned v) {
-  unsigned old;
-  asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
-  return old;
+__device__ __forceinline__ int ld_volatile_int(const int* p) { return *reinterpret_cast<const volatile int*>(p); }
+
+// Tagged exchange word: relaxed (strong, single-copy atomic) 64-bit accesses.
+__device__ __forceinline__ void put_word(unsigned long long* p, uint32_t tag, float v) {
+  const unsigned long long w = ((unsigned long long)tag << 32) | (unsigned long long)__float_as_uint(v);
+  asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(w) : "memory");
 }
 
-__device__ __forceinline__ int ld_volatile_int(const int* p) { return *reinterpret_cast<const volatile int*>(p); }
+__device__ __forceinline__ unsigned long long get_word(const unsigned long long* p) {
+  unsigned long long w;
+  asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(w) : "l"(p) : "memory");
+  return w;
+}
+
+__device__ __forceinline__ uint32_t tag_of(unsigned long long w) { return (uint32_t)(w >> 32); }
+__device__ __forceinline__ float val_of(unsigned long long w) { return __uint_as_float((uint32_t)w); }
+
+// Re-reads *p until it carries `tag` (short back-off after the first rounds,
+// to keep polling traffic off the L2) and returns that word.  On watchdog
+// expiry, or when another CTA raised an error, returns the last word read
+// (its tag is not `tag`).  Kept out of line: it is only entered when the
+// first read of a word came back early, and one shared copy keeps the
+// per-minibatch code small.
+__device__ __noinline__ unsigned long long spin_word(const unsigned long long* p, uint32_t tag, int* err,
+                                                     unsigned long long budget) {
+  const unsigned long long t0 = globaltimer_ns();
+  unsigned spins = 0;
+  unsigned long long w = get_word(p);
+  while (tag_of(w) != tag) {
+    if (++spins > 4) __nanosleep(32);
+    if ((spins & 15u) == 0u) {
+      if (ld_volatile_int(err) != 0) break;
+      if (globaltimer_ns() - t0 > budget) {
+        atomicCAS(err, 0, STD_ETIMEOUT);
+        break;
+      }
+    }
+    w = get_word(p);
+  }
+  return w;
+}
+
+// The word at p once it carries `tag`, given a first read w; `ok` turns false
+// when the wait gave up.
+__device__ __forceinline__ unsigned long long settle(const unsigned long long* p, unsigned long long w, uint32_t tag,
+                                                     bool& ok, const EpochArgs& a) {
+  if (tag_of(w) != tag) {
+    w = ok ? spin_word(p, tag, a.err, a.watchdog_ns) : w;
+    ok = ok && tag_of(w) == tag;
+  }
+  return w;
+}
+
+// Waits until every live word w[u] (p[u] != nullptr) carries tag tg[u]: each
+// round re-reads all the words still missing at once, so the waits overlap.
+// Returns false when the watchdog expires or another CTA raised an error.
+template <int K>
+__device__ __forceinline__ bool wait_all(const unsigned long long* const (&p)[K], unsigned long long (&w)[K],
+                                         const uint32_t (&tg)[K], const EpochArgs& a) {
+  unsigned long long t0 = 0;
+  unsigned spins = 0;
+#pragma unroll 1
+  while (true) {
+    bool done = true;
+#pragma unroll
+    for (int u = 0; u < K; ++u)
+      if (p[u] && tag_of(w[u]) != tg[u]) {
+        done = false;
+        w[u] = get_word(p[u]);
+      }
+    if (done) return true;
+    if (t0 == 0) t0 = globaltimer_ns();
+    if (++spins > 4) __nanosleep(32);
+    if ((spins & 15u) == 0u) {
+      if (ld_volatile_int(a.err) != 0) return false;
+      if (globaltimer_ns() - t0 > a.watchdog_ns) {
+        atomicCAS(a.err, 0, STD_ETIMEOUT);
+        return false;
+      }
+    }
+  }
+}
 
 // Grid barrier over all CTAs of the cooperative launch.  The counter only
 // grows; barrier k completes when it reaches k * G.  A wait longer than the
@@ -204,6 +351,19 @@ __device__ bool grid_barrier(const EpochArgs& a, unsigned long long& generation)
   return s_ok != 0;
 }
 
+// Named barrier over the first `threads` threads of the CTA (id 1; id 0 is
+// __syncthreads).
+__device__ __forceinline__ void named_sync(int threads) {
+  asm volatile("bar.sync 1, %0;" ::"r"(threads) : "memory");
+}
+
+__device__ __forceinline__ void cp_async4(void* smem, const void* gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
 struct Phase {
   int m, chunk, lo, hi, cnt;
 };
@@ -220,64 +380,33 @@ __device__ __forceinline__ Phase phase_of(const EpochArgs& a, int64_t b) {
   return ph;
 }
 
-// This CTA's chunk of the mode-`mode` sorted copy of minibatch b (coordinates
-// [s][k], values, runs) into shared buffers.
-template <int N>
-__device__ __forceinline__ void load_schedule(const EpochArgs& a, int64_t b, int mode, int* crd, float* xs,
-                                              uint32_t* seg) {
+// Asynchronous copy of this CTA's chunk of the mode-`mode` sorted copy of
+// minibatch b into a shared schedule buffer (coordinates [s][N], values, run
+// bounds, links [s][N]).
+__device__ __forceinline__ void prefetch_schedule(const EpochArgs& a, int N, int64_t b, int mode, int* buf,
+                                                  int chunk_max, FastDiv fper) {
   const Phase ph = phase_of(a, b);
   const size_t base = (size_t)(b * (int64_t)a.s.M + ph.lo);
-  for (int s = threadIdx.x; s < ph.cnt; s += blockDim.x) {
-#pragma unroll
-    for (int k = 0; k < N; ++k) crd[s * N + k] = __ldg(a.s.crd + ((size_t)mode * N + k) * a.s.npad + base + s);
-    xs[s] = __ldg(a.s.val + (size_t)mode * a.s.npad + base + s);
-    seg[s] = __ldg(a.s.seg + (size_t)mode * a.s.npad + base + s);
-  }
-}
-
-// The N factor rows of every sample of the chunk, with L2-coherent loads
-// (rows may have been written by other CTAs in earlier phases).
-template <int N>
-__device__ __forceinline__ void load_rows(const EpochArgs& a, const int* crd, int cnt, const int* rowtab,
-                                          float* rows) {
-  const Geometry& g = a.g;
-  const int sumJ = g.sumJ;
-  const int total = cnt * sumJ, T = blockDim.x;
-  for (int i0 = threadIdx.x; i0 < total; i0 += 4 * T) {
-    float v[4];
-#pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      const int i = i0 + u * T;
-      v[u] = 0.f;
-      if (i < total) {
-        const int s = i / sumJ, jj = i - s * sumJ;
-        const int k = rowtab[jj] & 0xff, j = rowtab[jj] >> 8;
-        if (a.precision == 1) {
-          const unsigned short h = __ldcg(reinterpret_cast<const unsigned short*>(a.Ab[k]) +
-                                          (size_t)crd[s * N + k] * g.Jb[k] + j);
-          v[u] = __uint_as_float((uint32_t)h << 16);
-        } else {
-          v[u] = __ldcg(a.A[k] + (size_t)crd[s * N + k] * g.Jp[k] + j);
-        }
-      }
+  int* crd = buf;
+  int* xs = buf + N * chunk_max;
+  int* seg = xs + chunk_max;
+  int* lnk = seg + chunk_max;
+  const int per = N + 2 + mode;
+#pragma unroll 1
+  for (int i = threadIdx.x; i < ph.cnt * per; i += blockDim.x) {
+    const int s = fdiv(i, fper), f = i - s * per;
+    const size_t t = base + s;
+    if (f < N) cp_async4(crd + s * N + f, a.s.crd + ((size_t)mode * N + f) * a.s.npad + t);
+    else if (f == N) cp_async4(xs + s, a.s.val + (size_t)mode * a.s.npad + t);
+    else if (f == N + 1) cp_async4(seg + s, a.s.seg + (size_t)mode * a.s.npad + t);
+    else {
+      const int k = f - N - 2;
+      cp_async4(lnk + s * N + k, a.s.link + (size_t)(mode * (mode - 1) / 2 + k) * a.s.npad + t);
     }
-#pragma unroll
-    for (int u = 0; u < 4; ++u)
-      if (i0 + u * T < total) rows[i0 + u * T] = v[u];
   }
 }
 
-// G_(n) as BF16 [j][c] with row stride bf16_row_stride(P_n); rows j >= J_n
-// (up to a multiple of 16) and columns c >= P_n are zero.
-__device__ __forceinline__ void build_gt_bf16(__nv_bfloat16* dst, const float* Gsm, const int* cof, int Jn, int Pn,
-                                              int gsn, int t0, int nt) {
-  const int KP = bf16_row_stride(Pn), J16 = round_up(Jn, 16);
-  for (int i = t0; i < J16 * KP; i += nt) {
-    const int j = i / KP, cc = i - j * KP;
-    const float v = (j < Jn && cc < Pn) ? Gsm[cof[cc] + j * gsn] : 0.f;
-    dst[i] = __float2bfloat16_rn(v);
-  }
-}
+__device__ __forceinline__ float bf16_round(float v) { return __bfloat162float(__float2bfloat16_rn(v)); }
 
 __device__ __forceinline__ void mma_bf16_16816(float* d, uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3,
                                                uint32_t b0, uint32_t b1) {
@@ -288,702 +417,794 @@ __device__ __forceinline__ void mma_bf16_16816(float* d, uint32_t a0, uint32_t a
       : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
 }
 
+// Product of a sample's N-1 row entries named by a packed Kronecker column
+// (8-bit element offsets into the sample's concatenated rows).
+__device__ __forceinline__ float kron_entry(const float* rs, unsigned long long packed, int nm1) {
+  float v = rs[(int)(packed & 0xffu)];
+#pragma unroll 1
+  for (int k = 1; k < nm1; ++k) v *= rs[(int)((packed >> (8 * k)) & 0xffu)];
+  return v;
+}
+
+// Right Gram operand row of one sample for mode n (a_j a_j' packed, then a_j),
+// written by the lanes of one warp.
+__device__ __forceinline__ void right_row(float* dst, const float* an, int Jn, int tJ, int tJp, int rwn,
+                                          const int* trij, int lane) {
+#pragma unroll 1
+  for (int qq = lane; qq < rwn; qq += 32) {
+    float v = 0.f;
+    if (qq < tJ) {
+      const int t = trij[qq];
+      v = an[t & 0xff] * an[t >> 8];
+    } else if (qq >= tJp && qq < tJp + Jn) {
+      v = an[qq - tJp];
+    }
+    dst[qq] = v;
+  }
+}
+
 }  // namespace
 
-template <int N>
+template <bool BF>
 __global__ void __launch_bounds__(kEpochThreads, 1)
 k_epoch(EpochArgs a) {
   extern __shared__ __align__(16) float sm[];
-  const Geometry& g = a.g;
-  const int R = g.R;
-  const SmemLayout L = smem_layout(g, a.chunk_max, a.payload_max, a.precision);
+  // per-mode constants, indexed by the (runtime) mode
+  __shared__ int mJ[kMaxN], mJoff[kMaxN], mBoff[kMaxN], mJp[kMaxN], mJb[kMaxN], mPn[kMaxN], mToff[kMaxN],
+      mGs[kMaxN], mRoff[kMaxN];
+  __shared__ FastDiv mFna4[kMaxN], mFnq4[kMaxN], mFtJ[kMaxN], mFJ[kMaxN], mFper[kMaxN];
+  __shared__ float* mA[kMaxN];
+  __shared__ unsigned short* mAb[kMaxN];
+  __shared__ int s_nheads;
+  const int N = a.g.N, R = a.g.R;
+  const int chunk_max = a.chunk_max;
+  const SmemLayout L = smem_layout(a.g, chunk_max, gridDim.x, BF ? 1 : 0);
   float* Bsm = sm + L.B;
   float* Gsm = sm + L.G;
-  float* GTb[2] = {sm + L.GT[0], sm + L.GT[1]};
-  __nv_bfloat16* GThb[2] = {reinterpret_cast<__nv_bfloat16*>(sm + L.GTh[0]),
-                            reinterpret_cast<__nv_bfloat16*>(sm + L.GTh[1])};
+  float* GT = sm + L.GT;
+  __nv_bfloat16* GTh = reinterpret_cast<__nv_bfloat16*>(sm + L.GTh);
   __nv_bfloat16* Sh = reinterpret_cast<__nv_bfloat16*>(sm + L.Sh);
-  const bool bf = a.precision == 1;
+  float* Sbuf = sm + L.S;
   uint32_t* ldig = reinterpret_cast<uint32_t*>(sm + L.ldig);
-  int* coff = reinterpret_cast<int*>(sm + L.coff);
   unsigned long long* cdig = reinterpret_cast<unsigned long long*>(sm + L.cdig);
   int* rowtab = reinterpret_cast<int*>(sm + L.rowtab);
+  int* trij = reinterpret_cast<int*>(sm + L.trij);
+  int* scb[2] = {reinterpret_cast<int*>(sm + L.sc[0]), reinterpret_cast<int*>(sm + L.sc[1])};
   float* rows = sm + L.rows;
+  float* master = sm + L.master;
   float* pbuf = sm + L.p;
-  float* Ybuf = sm + L.Y;
-  float* Sbuf = sm + L.S;
-  float* Ebuf = sm + L.E;
-  float* Fbuf = sm + L.F;
+  float* left = sm + L.left;
+  float* right = sm + L.right;
   float* redsm = sm + L.red;
-  float* Vsm = sm + L.V;
   float* Dsm = sm + L.D;
-  int* crdb[2] = {reinterpret_cast<int*>(sm + L.crd[0]), reinterpret_cast<int*>(sm + L.crd[1])};
-  float* xsb[2] = {sm + L.xs[0], sm + L.xs[1]};
-  uint32_t* segb[2] = {reinterpret_cast<uint32_t*>(sm + L.seg[0]), reinterpret_cast<uint32_t*>(sm + L.seg[1])};
+  float* qbuf = sm + L.q;
   int* head = reinterpret_cast<int*>(sm + L.head);
+  float* pieces_sm = sm + L.pbuf;
 
   const int G = gridDim.x, c = blockIdx.x, tid = threadIdx.x, T = blockDim.x;
   const int lane = tid & 31, warp = tid >> 5, nwarps = T >> 5;
   const int M = a.s.M;
-  const int sumJ = g.sumJ, Jmax = g.Jmax;
+  const int sumJ = a.g.sumJ, Jmax = a.g.Jmax, prodJ = a.g.prodJ;
   const int npairs = R * (R - 1) / 2;
-  const int Rp = pow2_at_least(R);            // lanes per sample in the W step (<= 32)
-  const int Pmax = max_pn(g);
-  const int ctile_cap = Pmax < kCTile ? pad4(Pmax) : kCTile;
-  const int ys = ystride(g);
-  int Jr[N], joff[N], boff[N];
-#pragma unroll
-  for (int k = 0; k < N; ++k) {
-    Jr[k] = g.J[k];
-    joff[k] = g.joff[k];
-    boff[k] = g.boff[k];
-  }
+  const int NR = N * R;
+  const int lw = L.lw, rw = L.rw;
   unsigned long long generation = 0;
 
   // ---- tables built once per launch ----
-  int sumJR = 0;
+  if (tid == 0) {
 #pragma unroll
-  for (int n = 0; n < N; ++n) sumJR += Jr[n] * R;
+    for (int k = 0; k < kMaxN; ++k) {
+      mJ[k] = a.g.J[k];
+      mJoff[k] = a.g.joff[k];
+      mBoff[k] = a.g.boff[k];
+      mJp[k] = a.g.Jp[k];
+      mJb[k] = a.g.Jb[k];
+      mGs[k] = a.g.gstride[k];
+      mA[k] = a.A[k];
+      mAb[k] = reinterpret_cast<unsigned short*>(a.Ab[k]);
+    }
+    int toff = 0, roff = 0;
+    for (int k = 0; k < N; ++k) {
+      const int Jk = mJ[k];
+      mPn[k] = prodJ / Jk;
+      mToff[k] = toff;
+      toff += mPn[k];
+      mRoff[k] = L.rpre ? roff : 0;
+      roff += right_width(Jk);
+      mFna4[k] = make_fastdiv((uint32_t)(pad4(Jk) >> 2));
+      mFnq4[k] = make_fastdiv((uint32_t)(pad4(tri(Jk)) >> 2));
+      mFtJ[k] = make_fastdiv((uint32_t)tri(Jk));
+      mFJ[k] = make_fastdiv((uint32_t)Jk);
+      mFper[k] = make_fastdiv((uint32_t)(N + 2 + k));
+    }
+  }
+  __syncthreads();
+  const FastDiv f_sumJ = make_fastdiv((uint32_t)sumJ);
+  const FastDiv f_R = make_fastdiv((uint32_t)R);
+  int sumJR = 0;
+  for (int n = 0; n < N; ++n) sumJR += mJ[n] * R;
+#pragma unroll 1
   for (int i = tid; i < sumJR; i += T) Bsm[i] = __ldcg(a.B + i);
-  for (int lin = tid; lin < g.prodJ; lin += T) {
+#pragma unroll 1
+  for (int lin = tid; lin < prodJ; lin += T) {
     int t = lin;
     uint32_t packed = 0;
-#pragma unroll
     for (int k = 0; k < N; ++k) {
-      packed |= (uint32_t)(t % Jr[k]) << (5 * k);
-      t /= Jr[k];
+      packed |= (uint32_t)(t % mJ[k]) << (5 * k);
+      t /= mJ[k];
     }
     ldig[lin] = packed;
   }
-  {
-    int base = 0;
-#pragma unroll
-    for (int n = 0; n < N; ++n) {
-      const int Pn = g.prodJ / Jr[n];
-      for (int cc = tid; cc < Pn; cc += T) {
-        int rem = cc, off = 0, sh = 0;
-        unsigned long long packed = 0;
-#pragma unroll
-        for (int k = 0; k < N; ++k) {
-          if (k == n) continue;
-          const int d = rem % Jr[k];
-          rem /= Jr[k];
-          off += d * g.gstride[k];
-          packed |= (unsigned long long)(joff[k] + d) << sh;   // element offset in a sample's rows
-          sh += 8;
-        }
-        coff[base + cc] = off;
-        cdig[base + cc] = packed;
+#pragma unroll 1
+  for (int n = 0; n < N; ++n) {
+#pragma unroll 1
+    for (int cc = tid; cc < mPn[n]; cc += T) {
+      int rem = cc, sh = 0;
+      unsigned long long packed = 0;
+      for (int k = 0; k < N; ++k) {
+        if (k == n) continue;
+        const int d = rem % mJ[k];
+        rem /= mJ[k];
+        packed |= (unsigned long long)(mJoff[k] + d) << sh;   // element offset in a sample's rows
+        sh += 8;
       }
-      base += Pn;
+      cdig[mToff[n] + cc] = packed;
     }
   }
+#pragma unroll 1
   for (int jj = tid; jj < sumJ; jj += T) {
     int k = 0, j = jj;
-    while (j >= g.J[k]) { j -= g.J[k]; ++k; }
+    while (j >= mJ[k]) { j -= mJ[k]; ++k; }
     rowtab[jj] = k | (j << 8);
   }
+#pragma unroll 1
+  for (int q = tid; q < tri(Jmax); q += T) {
+    int jb = 0;
+    while (tri(jb + 1) <= q) ++jb;
+    trij[q] = (q - tri(jb)) | (jb << 8);   // packed upper-triangle index q = jb (jb + 1) / 2 + ja
+  }
   int buf = 0;
-  if (a.b0 < a.b1) load_schedule<N>(a, a.b0, 0, crdb[0], xsb[0], segb[0]);
+  if (a.b0 < a.b1) prefetch_schedule(a, N, a.b0, 0, scb[0], chunk_max, mFper[0]);
+  cp_async_commit();
   __syncthreads();
 
+#pragma unroll 1
   for (int64_t b = a.b0; b < a.b1; ++b) {
     const Phase ph = phase_of(a, b);
     const int cnt = ph.cnt, lo = ph.lo, hi = ph.hi;
     const bool probe = (b == a.probe_batch);
     const float fm = (float)ph.m;
     const float invm = 1.0f / fm;
+    const uint32_t tag0 = a.tag_base + (uint32_t)((b - a.b0) * 8);
+
+    // every row update of the previous minibatch is visible after this
+    if (b > a.b0 && !grid_barrier(a, generation)) return;
+    cp_async_wait_all();
+    __syncthreads();
+    // factor mode 2's chunk arrives while the core phase runs
+    prefetch_schedule(a, N, b, 1, scb[buf ^ 1], chunk_max, mFper[1]);
+    cp_async_commit();
 
     // ------------------------------------------------------------------
-    // Core phase on this CTA's chunk of the mode-1-sorted copy.
+    // Core phase on this CTA's chunk of the mode-1-sorted copy; the rows
+    // stay in shared memory for factor mode 1, which uses the same chunk.
     // ------------------------------------------------------------------
-    const int* crd = crdb[buf];
-    const float* xs = xsb[buf];
-    load_rows<N>(a, crd, cnt, rowtab, rows);
-    // factor mode 1's schedule does not depend on the model: fetch it now
-    load_schedule<N>(a, b, 0, crdb[buf ^ 1], xsb[buf ^ 1], segb[buf ^ 1]);
-    __syncthreads();
-    // p[s][k][r]: thread per (s, r), all modes
-    for (int i = tid; i < cnt * R; i += T) {
-      const int s = i / R, r = i - s * R;
+    const int* crd = scb[buf];
+    const float* xs = reinterpret_cast<const float*>(scb[buf] + N * chunk_max);
+#pragma unroll 1
+    for (int i0 = tid; i0 < cnt * sumJ; i0 += 2 * T) {
+      float v[2];
 #pragma unroll
-      for (int k = 0; k < N; ++k) {
-        const float* ar = rows + s * sumJ + joff[k];
-        const float* br = Bsm + boff[k] + r;
+      for (int u = 0; u < 2; ++u) {
+        const int i = i0 + u * T;
+        v[u] = 0.f;
+        if (i < cnt * sumJ) {
+          const int s = fdiv(i, f_sumJ), jj = i - s * sumJ;
+          const int k = rowtab[jj] & 0xff, j = rowtab[jj] >> 8;
+          const unsigned row = (unsigned)crd[s * N + k];
+          if (BF) v[u] = __uint_as_float((uint32_t)__ldcg(mAb[k] + row * (unsigned)mJb[k] + j) << 16);
+          else v[u] = __ldcg(mA[k] + row * (unsigned)mJp[k] + j);
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < 2; ++u)
+        if (i0 + u * T < cnt * sumJ) rows[i0 + u * T] = v[u];
+    }
+    if (BF)
+#pragma unroll 1
+      for (int s = warp; s < cnt; s += nwarps)
+        if (lane < mJ[0]) master[s * Jmax + lane] = __ldcg(mA[0] + (unsigned)crd[s * N] * (unsigned)mJp[0] + lane);
+    __syncthreads();
+    // p[s][k][r] (warp per sample, lane per (k, r)) and, when they fit, the
+    // right Gram operand rows of every mode (they depend on A only)
+#pragma unroll 1
+    for (int s = warp; s < cnt; s += nwarps) {
+      const float* rs = rows + s * sumJ;
+#pragma unroll 1
+      for (int kr = lane; kr < NR; kr += 32) {
+        const int k = fdiv(kr, f_R), r = kr - k * R;
+        const float* ar = rs + mJoff[k];
+        const float* br = Bsm + mBoff[k] + r;
         float acc0 = 0.f, acc1 = 0.f;
         int j = 0;
-        for (; j + 1 < Jr[k]; j += 2) {
+#pragma unroll 1
+        for (; j + 1 < mJ[k]; j += 2) {
           acc0 = fmaf(ar[j], br[j * R], acc0);
           acc1 = fmaf(ar[j + 1], br[(j + 1) * R], acc1);
         }
-        if (j < Jr[k]) acc0 = fmaf(ar[j], br[j * R], acc0);
-        pbuf[(s * N + k) * R + r] = acc0 + acc1;
+        if (j < mJ[k]) acc0 = fmaf(ar[j], br[j * R], acc0);
+        pbuf[s * NR + kr] = acc0 + acc1;
       }
+      if (L.rpre)
+#pragma unroll 1
+        for (int n = 0; n < N; ++n) {
+          const int Jn = mJ[n];
+          right_row(right + s * rw + mRoff[n], rs + mJoff[n], Jn, tri(Jn), pad4(tri(Jn)), right_width(Jn), trij,
+                    lane);
+        }
     }
     __syncthreads();
 
-#pragma unroll
+#pragma unroll 1
     for (int n = 0; n < N; ++n) {
-      const int Jn = Jr[n];
+      const int Jn = mJ[n];
+      const int tJ = tri(Jn);
+      const int tJp = pad4(tJ);
+      const int Jq = pad4(Jn);
       const int K = R * Jn;
-      const int P = K + npairs * Jn * Jn;
-      // W step: Rp lanes per sample.  w[s][r], residual e_s (shuffle sum over r).
-      for (int i0 = 0; i0 < cnt * Rp; i0 += T) {
-        const int i = i0 + tid;
-        const int s = i / Rp, r = i - s * Rp;
-        const bool live = (s < cnt) && (r < R);
-        float w = 0.f, contrib = 0.f;
-        if (live) {
-          w = 1.f;
+      const int Kq = pad4(K);
+      const int P = K + npairs * tJ;
+      const uint32_t tag = tag0 + (uint32_t)n;
+      const int nq4 = tJp >> 2, na4 = Jq >> 2;
+      const int ntile = R * na4 + npairs * nq4;
+      const FastDiv f_na4 = mFna4[n], f_nq4 = mFnq4[n], f_tJ = mFtJ[n];
+      // left Gram operand rows, one sample per 16-lane group (R <= 16) or
+      // per warp: lane r forms w_r, the residual e_s (group sum), e_s w_r and
+      // w_r w_r' (r' < r); right operand rows of this mode unless built above
+      {
+        const int gl = R <= 16 ? 16 : 32;
+        const int gpw = 32 / gl;
+        const int sub = lane / gl, gla = lane - sub * gl;
+        const int gbase = sub * gl;
+#pragma unroll 1
+        for (int s0 = warp * gpw; s0 < cnt; s0 += nwarps * gpw) {
+          const int s = s0 + sub;
+          const bool live = (s < cnt) && (gla < R);
+          float w = 0.f, contrib = 0.f;
+          if (live) {
+            const float* ps = pbuf + s * NR + gla;
+            w = 1.f;
+#pragma unroll 1
+            for (int k = 0; k < N; ++k)
+              if (k != n) w *= ps[k * R];
+            contrib = w * ps[n * R];
+          }
 #pragma unroll
-          for (int k = 0; k < N; ++k)
-            if (k != n) w *= pbuf[(s * N + k) * R + r];
-          contrib = w * pbuf[(s * N + n) * R + r];
+          for (int off = 16; off > 0; off >>= 1)
+            if (off < gl) contrib += __shfl_xor_sync(0xffffffffu, contrib, off);
+          float* lrow = left + s * lw;
+#pragma unroll 1
+          for (int rp = 0; rp + 1 < R; ++rp) {
+            const float wp = __shfl_sync(0xffffffffu, w, gbase + rp);
+            if (live && rp < gla) lrow[gla * (gla - 1) / 2 + rp] = w * wp;
+          }
+          if (live) lrow[npairs + gla] = (contrib - xs[s]) * w;
         }
-        for (int off = Rp >> 1; off > 0; off >>= 1) contrib += __shfl_xor_sync(0xffffffffu, contrib, off);
-        if (live) {
-          // Y[s][r*Jn + j] = w[s][r] a_n(s)[j]; e_s in column K of Y'
-          float* yrow = Ybuf + s * ys;
-          const float* an = rows + s * sumJ + joff[n];
-          for (int j = 0; j < Jn; ++j) yrow[r * Jn + j] = w * an[j];
-          if (r == 0) yrow[K] = contrib - xs[s];
-        }
+        if (!L.rpre)
+#pragma unroll 1
+          for (int s = warp; s < cnt; s += nwarps)
+            right_row(right + s * rw, rows + s * sumJ + mJoff[n], Jn, tJ, tJp, right_width(Jn), trij, lane);
       }
       __syncthreads();
-      // Gram tiles of Y' (fixed sample order): g = Y'^T e (1 x 2 tiles) and
-      // C_{r r'} = Y_r^T Y_r' for r' < r (2 x 2 tiles)
+      // Gram partial, thread tile = one left column x 4 right columns over
+      // the chunk, published as soon as it is summed
       {
-        const int tj = (Jn + 1) >> 1;
-        const int gtiles = (K + 1) >> 1;
-        const int ntiles = gtiles + npairs * tj * tj;
-        for (int t = tid; t < ntiles; t += T) {
-          int ya, yb, rowsz, colsz, obase, ostride;
-          if (t < gtiles) {
-            ya = K;               // the residual column
-            yb = 2 * t;
-            rowsz = 1;
-            colsz = min(2, K - yb);
-            obase = yb;
-            ostride = 0;
+        const float* rbase = right + mRoff[n];
+        unsigned long long* dst = a.part + (unsigned)c * (unsigned)a.pstride;
+#pragma unroll 1
+        for (int t = tid; t < ntile; t += T) {
+          int li, rc, obase, width;
+          if (t < R * na4) {
+            const int r = fdiv(t, f_na4), jg = t - r * na4;
+            li = npairs + r;
+            rc = tJp + 4 * jg;
+            obase = r * Jn + 4 * jg;
+            width = Jn - 4 * jg;
           } else {
-            const int q = t - gtiles;
-            int pair = q / (tj * tj);
-            const int w2 = q - pair * tj * tj, ta = w2 / tj, tb = w2 - ta * tj;
-            int r = 1;
-            while (pair >= r) { pair -= r; ++r; }
-            const int rp = pair;
-            ya = r * Jn + 2 * ta;
-            yb = rp * Jn + 2 * tb;
-            rowsz = min(2, Jn - 2 * ta);
-            colsz = min(2, Jn - 2 * tb);
-            obase = K + ((r * (r - 1) / 2 + rp) * Jn + 2 * ta) * Jn + 2 * tb;
-            ostride = Jn;
+            const int t2 = t - R * na4;
+            const int qi = fdiv(t2, f_nq4), jg = t2 - qi * nq4;
+            li = qi;
+            rc = 4 * jg;
+            obase = K + qi * tJ + 4 * jg;
+            width = tJ - 4 * jg;
           }
-          float c00 = 0.f, c01 = 0.f, c10 = 0.f, c11 = 0.f;
-          float d00 = 0.f, d01 = 0.f, d10 = 0.f, d11 = 0.f;
-          const float* ysp = Ybuf;
+          float4 x0 = make_float4(0.f, 0.f, 0.f, 0.f), x1 = x0;
+          const float* lp = left + li;
+          const float* rp = rbase + rc;
           int s = 0;
-          for (; s + 1 < cnt; s += 2, ysp += 2 * ys) {
-            const float a0 = ysp[ya], a1 = ysp[ya + 1], b0 = ysp[yb], b1 = ysp[yb + 1];
-            const float e0 = ysp[ys + ya], e1 = ysp[ys + ya + 1], f0 = ysp[ys + yb], f1 = ysp[ys + yb + 1];
-            c00 = fmaf(a0, b0, c00);
-            c01 = fmaf(a0, b1, c01);
-            c10 = fmaf(a1, b0, c10);
-            c11 = fmaf(a1, b1, c11);
-            d00 = fmaf(e0, f0, d00);
-            d01 = fmaf(e0, f1, d01);
-            d10 = fmaf(e1, f0, d10);
-            d11 = fmaf(e1, f1, d11);
+#pragma unroll 1
+          for (; s + 1 < cnt; s += 2) {
+            const float l0 = lp[s * lw], l1 = lp[(s + 1) * lw];
+            const float4 r0 = *reinterpret_cast<const float4*>(rp + s * rw);
+            const float4 r1 = *reinterpret_cast<const float4*>(rp + (s + 1) * rw);
+            x0.x = fmaf(l0, r0.x, x0.x); x0.y = fmaf(l0, r0.y, x0.y);
+            x0.z = fmaf(l0, r0.z, x0.z); x0.w = fmaf(l0, r0.w, x0.w);
+            x1.x = fmaf(l1, r1.x, x1.x); x1.y = fmaf(l1, r1.y, x1.y);
+            x1.z = fmaf(l1, r1.z, x1.z); x1.w = fmaf(l1, r1.w, x1.w);
           }
           if (s < cnt) {
-            const float a0 = ysp[ya], a1 = ysp[ya + 1], b0 = ysp[yb], b1 = ysp[yb + 1];
-            c00 = fmaf(a0, b0, c00);
-            c01 = fmaf(a0, b1, c01);
-            c10 = fmaf(a1, b0, c10);
-            c11 = fmaf(a1, b1, c11);
+            const float l0 = lp[s * lw];
+            const float4 r0 = *reinterpret_cast<const float4*>(rp + s * rw);
+            x0.x = fmaf(l0, r0.x, x0.x); x0.y = fmaf(l0, r0.y, x0.y);
+            x0.z = fmaf(l0, r0.z, x0.z); x0.w = fmaf(l0, r0.w, x0.w);
           }
-          c00 += d00;
-          c01 += d01;
-          c10 += d10;
-          c11 += d11;
-          float* dst = a.part + (size_t)c * a.payload_max + obase;
-          __stcg(dst, c00);
-          if (colsz > 1) __stcg(dst + 1, c01);
-          if (rowsz > 1) {
-            __stcg(dst + ostride, c10);
-            if (colsz > 1) __stcg(dst + ostride + 1, c11);
-          }
+          put_word(dst + obase, tag, x0.x + x1.x);
+          if (width > 1) put_word(dst + obase + 1, tag, x0.y + x1.y);
+          if (width > 2) put_word(dst + obase + 2, tag, x0.z + x1.z);
+          if (width > 3) put_word(dst + obase + 3, tag, x0.w + x1.w);
         }
       }
-      if (!grid_barrier(a, generation)) return;
-      // CTA c sums its slice of the payload over all CTAs (fixed order)
+      // hop 1: CTA c sums its slice of the payload over all CTAs (in CTA
+      // order within each lane, then a fixed butterfly across lanes) and
+      // pushes each sum into every CTA's copy of the payload
+      bool ok = true;
       {
         const int per = (P + G - 1) / G;
         const int o_lo = c * per, o_hi = min(o_lo + per, P);
+#pragma unroll 1
         for (int o = o_lo + warp; o < o_hi; o += nwarps) {
-          float acc = 0.f;
-          for (int cc0 = lane; cc0 < G; cc0 += 8 * 32) {
-            float v[8];
+          unsigned long long w8[8];
+          const unsigned long long* p8[8];
+          uint32_t t8[8];
 #pragma unroll
-            for (int u = 0; u < 8; ++u) {
-              const int cc = cc0 + 32 * u;
-              v[u] = cc < G ? __ldcg(a.part + (size_t)cc * a.payload_max + o) : 0.f;
-            }
-#pragma unroll
-            for (int u = 0; u < 8; ++u) acc += v[u];
+          for (int u = 0; u < 8; ++u) {
+            const int cc = lane + 32 * u;
+            p8[u] = cc < G ? a.part + (unsigned)cc * (unsigned)a.pstride + o : nullptr;
+            w8[u] = p8[u] ? get_word(p8[u]) : 0ULL;
+            t8[u] = tag;
           }
+          if (ok) ok = wait_all<8>(p8, w8, t8, a);
+          float s = 0.f;
 #pragma unroll
-          for (int off = 16; off > 0; off >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, off);
-          if (lane == 0) __stcg(a.red + o, acc);
+          for (int u = 0; u < 8; ++u)
+            if (p8[u]) s += val_of(w8[u]);
+#pragma unroll
+          for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+          if (ok)
+#pragma unroll 1
+            for (int cc = lane; cc < G; cc += 32) put_word(a.inbox + (unsigned)cc * (unsigned)a.pstride + o, tag, s);
         }
       }
-      if (!grid_barrier(a, generation)) return;
-      for (int o0 = tid; o0 < P; o0 += 4 * T) {
-        float v[4];
-#pragma unroll
-        for (int u = 0; u < 4; ++u) v[u] = (o0 + u * T < P) ? __ldcg(a.red + o0 + u * T) : 0.f;
-#pragma unroll
-        for (int u = 0; u < 4; ++u)
-          if (o0 + u * T < P) redsm[o0 + u * T] = v[u];
-      }
-      __syncthreads();
-      // Cyclic SGD over the columns of B(n) (lines 7-14) as a block forward
-      // substitution: V_r starts at g_r; after column r moves by Delta_r,
-      // every later V_r'' gains C_{r'' r} Delta_r.
+      // hop 2: this CTA's copy of the reduced payload, into shared memory,
+      // each block C_{r r'} unpacked to full rows of stride pad4(J_n)
       {
-        // 8 lanes per (r'', j) share each dot product; the lane that
-        // completes V_{r+1} also moves column r+1
-        float* Bn = Bsm + boff[n];
-        const float* Cv = redsm + K;
-        for (int i = tid; i < K; i += T) {
-          const int r = i / Jn;
-          Vsm[r * kMaxJ + i - r * Jn] = redsm[i];
-        }
-        if (tid < Jn) {
-          const float V = redsm[tid];
-          const float bo = Bn[tid * R];
-          const float bn = bo - a.lr_b * (V * invm + a.lam_b * bo);
-          Dsm[tid] = bn - bo;
-          Bn[tid * R] = bn;
-          if (probe && c == 0 && a.probeV) a.probeV[((size_t)n * R) * kMaxJ + tid] = V;
-        }
-        __syncthreads();
-        for (int r = 0; r + 1 < R; ++r) {
-          const int Q = (R - 1 - r) * Jn;
-          for (int base = 0; base < Q * 8; base += T) {
-            const int t = base + tid, q = t >> 3, l = t & 7;
-            const bool live = q < Q;
-            int r2 = 0, j = 0;
-            float sum = 0.f;
-            if (live) {
-              const int qr = q / Jn;
-              r2 = r + 1 + qr;
-              j = q - qr * Jn;
-              const float* C = Cv + ((r2 * (r2 - 1) / 2 + r) * Jn + j) * Jn;
-              const float* D = Dsm + r * kMaxJ;
-              for (int jp = l; jp < Jn; jp += 8) sum = fmaf(C[jp], D[jp], sum);
-            }
-            sum += __shfl_xor_sync(0xffffffffu, sum, 4);
-            sum += __shfl_xor_sync(0xffffffffu, sum, 2);
-            sum += __shfl_xor_sync(0xffffffffu, sum, 1);
-            if (live && l == 0) {
-              const float V = Vsm[r2 * kMaxJ + j] + sum;
-              Vsm[r2 * kMaxJ + j] = V;
-              if (r2 == r + 1) {
-                const float bo = Bn[j * R + r2];
-                const float bn = bo - a.lr_b * (V * invm + a.lam_b * bo);
-                Dsm[r2 * kMaxJ + j] = bn - bo;
-                Bn[j * R + r2] = bn;
-                if (probe && c == 0 && a.probeV) a.probeV[((size_t)n * R + r2) * kMaxJ + j] = V;
+        const unsigned long long* mine = a.inbox + (unsigned)c * (unsigned)a.pstride;
+#pragma unroll 1
+        for (int o0 = tid; o0 < P; o0 += 2 * T) {
+          unsigned long long w2[2];
+          const unsigned long long* p2[2];
+          uint32_t t2[2];
+#pragma unroll
+          for (int u = 0; u < 2; ++u) {
+            p2[u] = (o0 + u * T < P) ? mine + o0 + u * T : nullptr;
+            w2[u] = p2[u] ? get_word(p2[u]) : 0ULL;
+            t2[u] = tag;
+          }
+          if (ok) ok = wait_all<2>(p2, w2, t2, a);
+#pragma unroll
+          for (int u = 0; u < 2; ++u) {
+            const int o = o0 + u * T;
+            if (o < P) {
+              const float v = val_of(w2[u]);
+              if (o < K) {
+                redsm[o] = v;
+              } else {
+                const int t = o - K;
+                const int q = fdiv(t, f_tJ), jj = t - q * tJ;
+                const int ja = trij[jj] & 0xff, jb = trij[jj] >> 8;
+                float* blk = redsm + Kq + q * Jn * Jq;
+                blk[ja * Jq + jb] = v;
+                blk[jb * Jq + ja] = v;
               }
             }
           }
-          __syncthreads();
         }
+        // zero padding columns of the unpacked blocks
+        if (Jq > Jn)
+#pragma unroll 1
+          for (int i = tid; i < npairs * Jn; i += T)
+#pragma unroll 1
+            for (int j = Jn; j < Jq; ++j) redsm[Kq + i * Jq + j] = 0.f;
       }
-      // p[s][n][r] with the new B(n)
-      for (int i = tid; i < cnt * R; i += T) {
-        const int s = i / R, r = i - s * R;
-        const float* ar = rows + s * sumJ + joff[n];
-        const float* br = Bsm + boff[n] + r;
-        float acc0 = 0.f, acc1 = 0.f;
-        int j = 0;
-        for (; j + 1 < Jn; j += 2) {
-          acc0 = fmaf(ar[j], br[j * R], acc0);
-          acc1 = fmaf(ar[j + 1], br[(j + 1) * R], acc1);
+      if (!__syncthreads_and(ok)) return;
+      // Cyclic SGD over the columns of B(n) (lines 7-14) as a block forward
+      // substitution: warp w keeps V_w (lane j) and V_{w+16}; at step r the
+      // owner of column r moves it, and every later V_r'' gains C_{r'' r}
+      // Delta_r (Delta double-buffered by step parity, one named barrier per
+      // step).
+      {
+        const int nrw = R < nwarps ? R : nwarps;
+        if (warp < nrw) {
+          float* Bn = Bsm + mBoff[n];
+          const float* Cv = redsm + Kq;
+          const bool lj = lane < Jn;
+          const int ra = warp, rb = warp + nwarps;
+          float Va = (lj && ra < R) ? redsm[ra * Jn + lane] : 0.f;
+          float Vb = (lj && rb < R) ? redsm[rb * Jn + lane] : 0.f;
+          const float boa = (lj && ra < R) ? Bn[lane * R + ra] : 0.f;
+          const float bob = (lj && rb < R) ? Bn[lane * R + rb] : 0.f;
+          const int nv4 = Jq >> 2;
+#pragma unroll 1
+          for (int r = 0; r < R; ++r) {
+            float* D = Dsm + (r & 1) * 32;
+            if ((ra == r || rb == r) && lane < Jq) {
+              float d = 0.f;
+              if (lj) {
+                const float V = ra == r ? Va : Vb;
+                const float bo = ra == r ? boa : bob;
+                const float bn = bo - a.lr_b * (V * invm + a.lam_b * bo);
+                d = bn - bo;
+                Bn[lane * R + r] = bn;
+                if (probe && c == 0 && a.probeV) a.probeV[((unsigned)n * R + r) * kMaxJ + lane] = V;
+              }
+              D[lane] = d;
+            }
+            named_sync(nrw * 32);
+            if (lj) {
+              const float4* D4 = reinterpret_cast<const float4*>(D);
+#pragma unroll 1
+              for (int h = 0; h < 2; ++h) {
+                const int r2 = h == 0 ? ra : rb;
+                if (r2 > r && r2 < R) {
+                  const float4* C4 = reinterpret_cast<const float4*>(Cv + ((r2 * (r2 - 1) / 2 + r) * Jn + lane) * Jq);
+                  float s0 = 0.f, s1 = 0.f;
+#pragma unroll 1
+                  for (int v = 0; v < nv4; ++v) {
+                    const float4 cv = C4[v], dv = D4[v];
+                    s0 = fmaf(cv.x, dv.x, s0);
+                    s1 = fmaf(cv.y, dv.y, s1);
+                    s0 = fmaf(cv.z, dv.z, s0);
+                    s1 = fmaf(cv.w, dv.w, s1);
+                  }
+                  if (h == 0) Va += s0 + s1;
+                  else Vb += s0 + s1;
+                }
+              }
+            }
+          }
         }
-        if (j < Jn) acc0 = fmaf(ar[j], br[j * R], acc0);
-        pbuf[(s * N + n) * R + r] = acc0 + acc1;
       }
       __syncthreads();
+      // p[s][n][r] with the new B(n): warp per sample, lane r
+#pragma unroll 1
+      for (int s = warp; s < cnt; s += nwarps)
+        if (lane < R) {
+          const float* ar = rows + s * sumJ + mJoff[n];
+          const float* br = Bsm + mBoff[n] + lane;
+          float acc0 = 0.f, acc1 = 0.f;
+          int j = 0;
+#pragma unroll 1
+          for (; j + 1 < Jn; j += 2) {
+            acc0 = fmaf(ar[j], br[j * R], acc0);
+            acc1 = fmaf(ar[j + 1], br[(j + 1) * R], acc1);
+          }
+          if (j < Jn) acc0 = fmaf(ar[j], br[j * R], acc0);
+          pbuf[s * NR + n * R + lane] = acc0 + acc1;
+        }
+      __syncthreads();
     }
-    buf ^= 1;
 
     // ------------------------------------------------------------------
-    // G-hat from B (Eq. 4), mode 1 fastest, then G_(1) as [j][c].
+    // G-hat from B (Eq. 4), mode 1 fastest.
     // ------------------------------------------------------------------
-    for (int lin = tid; lin < g.prodJ; lin += T) {
+#pragma unroll 1
+    for (int lin = tid; lin < prodJ; lin += T) {
       const uint32_t packed = ldig[lin];
-      const float* bp[N];
-#pragma unroll
-      for (int k = 0; k < N; ++k) bp[k] = Bsm + boff[k] + (int)((packed >> (5 * k)) & 31u) * R;
       float acc = 0.f;
+#pragma unroll 1
       for (int r = 0; r < R; ++r) {
-        float prod = bp[0][r];
-#pragma unroll
-        for (int k = 1; k < N; ++k) prod *= bp[k][r];
+        float prod = Bsm[mBoff[0] + (int)(packed & 31u) * R + r];
+#pragma unroll 1
+        for (int k = 1; k < N; ++k) prod *= Bsm[mBoff[k] + (int)((packed >> (5 * k)) & 31u) * R + r];
         acc += prod;
       }
       Gsm[lin] = acc;
-    }
-    __syncthreads();
-    if (bf) {
-      build_gt_bf16(GThb[0], Gsm, coff, Jr[0], g.prodJ / Jr[0], g.gstride[0], tid, T);
-    } else {
-      const int Pn = g.prodJ / Jr[0], Pp = pad4(Pn);
-      float* GT = GTb[0];
-      for (int i = tid; i < Jr[0] * Pp; i += T) {
-        const int j = i / Pp, cc = i - j * Pp;
-        GT[i] = cc < Pn ? Gsm[coff[cc] + j * g.gstride[0]] : 0.f;
-      }
     }
     __syncthreads();
 
     // ------------------------------------------------------------------
     // Factor phase, n = 1..N.
     // ------------------------------------------------------------------
-    int toff = 0;   // offset of mode n's column tables
-#pragma unroll
+#pragma unroll 1
     for (int n = 0; n < N; ++n) {
-      const int Jn = Jr[n];
-      const int Pn = g.prodJ / Jn;
+      const int Jn = mJ[n];
+      const int Pn = mPn[n];
       const int Pp = pad4(Pn);
-      const int* fcrd = crdb[buf];
-      const float* fx = xsb[buf];
-      const uint32_t* fseg = segb[buf];
-      const float* GT = GTb[n & 1];
-      const unsigned long long* cdn = cdig + toff;
-      // rows, and the run heads of this chunk compacted in order (warp 0)
-      if (warp == 0) {
-        int nh = 0;
-        for (int s0 = 0; s0 < cnt; s0 += 32) {
-          const int s = s0 + lane;
-          bool is_head = false;
-          if (s < cnt) is_head = (s == 0) || ((int)(fseg[s] & 0xffffu) == lo + s);
-          const unsigned mask = __ballot_sync(0xffffffffu, is_head);
-          if (is_head) head[nh + __popc(mask & ((1u << lane) - 1u))] = s;
-          nh += __popc(mask);
-        }
-        if (lane == 0) head[cnt] = nh;
+      const uint32_t tag = tag0 + (uint32_t)n;
+      const unsigned long long* cdn = cdig + mToff[n];
+      bool ok = true;
+      if (n > 0) {
+        cp_async_wait_all();
+        __syncthreads();
+        buf ^= 1;
+        // the next phase's chunk: mode n+1 of this minibatch, or mode 1 of the next
+        const int64_t nb = (n + 1 < N) ? b : b + 1;
+        const int nmode = (n + 1 < N) ? n + 1 : 0;
+        if (nb < a.b1) prefetch_schedule(a, N, nb, nmode, scb[buf ^ 1], chunk_max, mFper[nmode]);
+        cp_async_commit();
       }
-      load_rows<N>(a, fcrd, cnt, rowtab, rows);
+      const int* fcrd = scb[buf];
+      const float* fx = reinterpret_cast<const float*>(scb[buf] + N * chunk_max);
+      const uint32_t* fseg = reinterpret_cast<const uint32_t*>(scb[buf] + (N + 1) * chunk_max);
+      const int* fl = scb[buf] + (N + 2) * chunk_max;
+      // rows: modes k < n as updated earlier in this minibatch (tagged slots,
+      // through the links), modes k >= n from A; G_(n) and the run heads are
+      // built while the first loads are in flight
+      const int total = n > 0 ? cnt * sumJ : 0;
+      unsigned long long w2[2];
+      const unsigned long long* p2[2];
+      uint32_t t2[2];
+      float v2[2];
+      int i0 = tid;
+#pragma unroll 1
+      for (bool first = true; i0 < total || first; i0 += 2 * T, first = false) {
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+          const int i = i0 + u * T;
+          p2[u] = nullptr;
+          w2[u] = 0ULL;
+          t2[u] = 0u;
+          v2[u] = 0.f;
+          if (i < total) {
+            const int s = fdiv(i, f_sumJ), jj = i - s * sumJ;
+            const int k = rowtab[jj] & 0xff, j = rowtab[jj] >> 8;
+            if (k < n) {
+              p2[u] = a.mail + ((unsigned)k * (unsigned)M + (unsigned)fl[s * N + k]) * (unsigned)Jmax + j;
+              w2[u] = get_word(p2[u]);
+              t2[u] = tag0 + (uint32_t)k;
+            } else {
+              const unsigned row = (unsigned)fcrd[s * N + k];
+              if (BF) v2[u] = __uint_as_float((uint32_t)__ldcg(mAb[k] + row * (unsigned)mJb[k] + j) << 16);
+              else v2[u] = __ldcg(mA[k] + row * (unsigned)mJp[k] + j);
+            }
+          }
+        }
+        if (first) {
+          if (BF && n > 0)
+#pragma unroll 1
+            for (int s = warp; s < cnt; s += nwarps)
+              if (lane < Jn)
+                master[s * Jmax + lane] = __ldcg(mA[n] + (unsigned)fcrd[s * N + n] * (unsigned)mJp[n] + lane);
+          // G_(n) for the contraction, [j][c]: warp per j, lanes over c;
+          // column c sits at the offset of its other-mode digits in G-hat
+          const int KP = BF ? bf16_row_stride(Pn) : Pp;
+          const int Jrows = BF ? round_up(Jn, 16) : Jn;
+#pragma unroll 1
+          for (int j = warp; j < Jrows; j += nwarps)
+#pragma unroll 1
+            for (int cc = lane; cc < KP; cc += 32) {
+              float gv = 0.f;
+              if (j < Jn && cc < Pn) {
+                const unsigned long long packed = cdn[cc];
+                int off = j * mGs[n], sh = 0;
+#pragma unroll 1
+                for (int k = 0; k < N; ++k) {
+                  if (k == n) continue;
+                  off += ((int)((packed >> sh) & 0xffu) - mJoff[k]) * mGs[k];
+                  sh += 8;
+                }
+                gv = Gsm[off];
+              }
+              if (BF) GTh[j * KP + cc] = __float2bfloat16_rn(gv);
+              else GT[j * KP + cc] = gv;
+            }
+          // run heads of this chunk, compacted in order (last warp)
+          if (warp == nwarps - 1) {
+            int nh = 0;
+#pragma unroll 1
+            for (int s0 = 0; s0 < cnt; s0 += 32) {
+              const int s = s0 + lane;
+              bool is_head = false;
+              if (s < cnt) is_head = (s == 0) || ((int)(fseg[s] & 0xffffu) == lo + s);
+              const unsigned mask = __ballot_sync(0xffffffffu, is_head);
+              if (is_head) head[nh + __popc(mask & ((1u << lane) - 1u))] = s;
+              nh += __popc(mask);
+            }
+            if (lane == 0) {
+              head[nh] = cnt;
+              s_nheads = nh;
+            }
+          }
+        }
+        if (ok) ok = wait_all<2>(p2, w2, t2, a);
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+          const int i = i0 + u * T;
+          if (i < total) rows[i] = p2[u] ? (BF ? bf16_round(val_of(w2[u])) : val_of(w2[u])) : v2[u];
+        }
+      }
+      if (!__syncthreads_and(ok)) return;
+      // Kronecker rows S_s (Eq. 10), warp per sample, lanes over columns
+      const int nm1 = N - 1;
+      const bool full_s = BF || cnt * Pp <= L.sfloats;
+      if (BF) {
+        const int KP = bf16_row_stride(Pn);
+#pragma unroll 1
+        for (int s = warp; s < round_up(cnt, 16); s += nwarps) {
+          const float* rs = rows + s * sumJ;
+#pragma unroll 1
+          for (int cc = lane; cc < KP; cc += 32)
+            Sh[s * KP + cc] = __float2bfloat16_rn((s < cnt && cc < Pn) ? kron_entry(rs, cdn[cc], nm1) : 0.f);
+        }
+      } else if (full_s) {
+#pragma unroll 1
+        for (int s = warp; s < cnt; s += nwarps) {
+          const float* rs = rows + s * sumJ;
+#pragma unroll 1
+          for (int cc = lane; cc < Pp; cc += 32) Sbuf[s * Pp + cc] = cc < Pn ? kron_entry(rs, cdn[cc], nm1) : 0.f;
+        }
+      }
       __syncthreads();
-      const int nheads = head[cnt];
-      if (bf) {
+      const int nheads = s_nheads;
+      if (BF) {
         // Tensor-core contraction: E (samples x J_n) = S (samples x P_n) .
         // G_(n)^T with BF16 operands and FP32 accumulation, mma.sync
         // m16n8k16 tiles (one warp per 16 x 8 output tile, full K).
         const int KP = bf16_row_stride(Pn);
-        const int C16 = round_up(cnt, 16);
-        const __nv_bfloat16* GTh = GThb[n & 1];
-        {
-          // thread per (Kronecker column, sample group); columns looped when
-          // the row is wider than the block
-          const int ngroups = max(1, T / KP);
-          const int sg = tid / KP;
-          if (sg < ngroups) {
-            for (int cl = tid - sg * KP; cl < KP; cl += (KP > T ? T : KP)) {
-              int off[N - 1];
-              const bool colv = cl < Pn;
-              if (colv) {
-                const unsigned long long packed = cdn[cl];
-#pragma unroll
-                for (int k = 0; k < N - 1; ++k) off[k] = (int)((packed >> (8 * k)) & 0xffu);
-              }
-              for (int s = sg; s < C16; s += ngroups) {
-                float S1 = 0.f;
-                if (colv && s < cnt) {
-                  const float* rs = rows + s * sumJ;
-                  S1 = rs[off[0]];
-#pragma unroll
-                  for (int k = 1; k < N - 1; ++k) S1 *= rs[off[k]];
-                }
-                Sh[s * KP + cl] = __float2bfloat16_rn(S1);
-              }
-            }
+        const int mt = round_up(cnt, 16) >> 4, ntl = (Jn + 7) >> 3, ksteps = round_up(Pn, 16) >> 4;
+        const int gq = lane >> 2, tq = lane & 3;
+#pragma unroll 1
+        for (int w = warp; w < mt * ntl; w += nwarps) {
+          const int mi = w / ntl, ni = w - mi * ntl;
+          const uint32_t* A0 = reinterpret_cast<const uint32_t*>(Sh + (mi * 16 + gq) * KP);
+          const uint32_t* A1 = reinterpret_cast<const uint32_t*>(Sh + (mi * 16 + gq + 8) * KP);
+          const uint32_t* Bq = reinterpret_cast<const uint32_t*>(GTh + (ni * 8 + gq) * KP);
+          float d[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll 1
+          for (int ks = 0; ks < ksteps; ++ks) {
+            const int kw = ks * 8 + tq;
+            mma_bf16_16816(d, A0[kw], A1[kw], A0[kw + 4], A1[kw + 4], Bq[kw], Bq[kw + 4]);
           }
-        }
-        __syncthreads();
-        {
-          const int mt = C16 >> 4, ntile = (Jn + 7) >> 3, ksteps = round_up(Pn, 16) >> 4;
-          const int gq = lane >> 2, tq = lane & 3;
-          for (int w = warp; w < mt * ntile; w += nwarps) {
-            const int mi = w / ntile, ni = w - mi * ntile;
-            const uint32_t* A0 = reinterpret_cast<const uint32_t*>(Sh + (mi * 16 + gq) * KP);
-            const uint32_t* A1 = reinterpret_cast<const uint32_t*>(Sh + (mi * 16 + gq + 8) * KP);
-            const uint32_t* Bq = reinterpret_cast<const uint32_t*>(GTh + (ni * 8 + gq) * KP);
-            float d[4] = {0.f, 0.f, 0.f, 0.f};
-            for (int ks = 0; ks < ksteps; ++ks) {
-              const int kw = ks * 8 + tq;
-              mma_bf16_16816(d, A0[kw], A1[kw], A0[kw + 4], A1[kw + 4], Bq[kw], Bq[kw + 4]);
-            }
-            const int s0 = mi * 16 + gq, j0 = ni * 8 + 2 * tq;
-            if (s0 < cnt) {
-              if (j0 < Jn) Ebuf[s0 * Jmax + j0] = d[0];
-              if (j0 + 1 < Jn) Ebuf[s0 * Jmax + j0 + 1] = d[1];
-            }
-            if (s0 + 8 < cnt) {
-              if (j0 < Jn) Ebuf[(s0 + 8) * Jmax + j0] = d[2];
-              if (j0 + 1 < Jn) Ebuf[(s0 + 8) * Jmax + j0 + 1] = d[3];
-            }
+          const int s0 = mi * 16 + gq, j0 = ni * 8 + 2 * tq;
+          if (s0 < cnt) {
+            if (j0 < Jn) qbuf[s0 * Jmax + j0] = d[0];
+            if (j0 + 1 < Jn) qbuf[s0 * Jmax + j0 + 1] = d[1];
+          }
+          if (s0 + 8 < cnt) {
+            if (j0 < Jn) qbuf[(s0 + 8) * Jmax + j0] = d[2];
+            if (j0 + 1 < Jn) qbuf[(s0 + 8) * Jmax + j0 + 1] = d[3];
           }
         }
         __syncthreads();
         // residual e_s = a_n . E_s - x_s (8 lanes per sample), contributions in place
+#pragma unroll 1
         for (int base = 0; base < cnt * 8; base += T) {
           const int t8 = base + tid, s = t8 >> 3, l = t8 & 7;
           const bool live = s < cnt;
           float part = 0.f;
           if (live) {
-            const float* an = rows + s * sumJ + joff[n];
-            for (int j = l; j < Jn; j += 8) part = fmaf(an[j], Ebuf[s * Jmax + j], part);
+            const float* an = rows + s * sumJ + mJoff[n];
+#pragma unroll 1
+            for (int j = l; j < Jn; j += 8) part = fmaf(an[j], qbuf[s * Jmax + j], part);
           }
           part += __shfl_xor_sync(0xffffffffu, part, 4);
           part += __shfl_xor_sync(0xffffffffu, part, 2);
           part += __shfl_xor_sync(0xffffffffu, part, 1);
           if (live) {
             const float e = part - fx[s];
-            for (int j = l; j < Jn; j += 8) Ebuf[s * Jmax + j] *= e;
+#pragma unroll 1
+            for (int j = l; j < Jn; j += 8) qbuf[s * Jmax + j] *= e;
           }
         }
-        __syncthreads();
       } else {
-      // Gather-contract E_s = G_(n) S_s^T over Kronecker-row tiles.  Thread
-        // tile (sample, column pair, half of the Kronecker columns); the two
-        // halves are adjacent lanes; 2*Tj lanes per sample.
-        const int ntj = (Jn + 1) >> 1;
-        const int Tj = pow2_at_least(ntj);
-        const int lg = 31 - __clz(2 * Tj);          // log2(2 * Tj)
-        const int nout = cnt << lg;
-        float acc[kOutPerThread][2];
-#pragma unroll
-        for (int q = 0; q < kOutPerThread; ++q) acc[q][0] = acc[q][1] = 0.f;
-        for (int c0 = 0; c0 < Pp; c0 += ctile_cap) {
-          const int ct = min(ctile_cap, Pp - c0);
-          if (c0 > 0) __syncthreads();
-          // column-major build: thread per (Kronecker column, sample group)
-          {
-            const int ngroups = max(1, T / ct);
-            const int sg = tid / ct, cl = tid - sg * ct;
-            if (sg < ngroups) {
-              const int cc = c0 + cl;
-              if (cc < Pn) {
-                const unsigned long long packed = cdn[cc];
-                int off[N - 1];
-#pragma unroll
-                for (int k = 0; k < N - 1; ++k) off[k] = (int)((packed >> (8 * k)) & 0xffu);
-                for (int s = sg; s < cnt; s += ngroups) {
-                  const float* rs = rows + s * sumJ;
-                  float S1 = rs[off[0]];
-#pragma unroll
-                  for (int k = 1; k < N - 1; ++k) S1 *= rs[off[k]];
-                  Sbuf[s * ctile_cap + cl] = S1;
-                }
-              } else {
-                for (int s = sg; s < cnt; s += ngroups) Sbuf[s * ctile_cap + cl] = 0.f;
-              }
-            }
-          }
-          __syncthreads();
-#pragma unroll
-          for (int q = 0; q < kOutPerThread; ++q) {
-            const int o = tid + q * T;
-            const int s = o >> lg, rem = o & ((1 << lg) - 1), jt = rem >> 1, h = rem & 1;
-            if (o < nout && jt < ntj) {
-              const int j0 = 2 * jt;
-              const float4* sv = reinterpret_cast<const float4*>(Sbuf + s * ctile_cap);
-              const float4* g0 = reinterpret_cast<const float4*>(GT + j0 * Pp + c0);
-              const float4* g1 = reinterpret_cast<const float4*>(GT + min(j0 + 1, Jn - 1) * Pp + c0);
-              float a0 = acc[q][0], a1 = acc[q][1], b0 = 0.f, b1 = 0.f;
-              const int nv = ct >> 2;
-              int v = h;
-              for (; v + 2 < nv; v += 4) {
-                const float4 x = sv[v], y = g0[v], z = g1[v];
-                const float4 x2 = sv[v + 2], y2 = g0[v + 2], z2 = g1[v + 2];
+        // E_s = G_(n) S_s^T: thread per (sample, j), JL lanes per sample (J_n
+        // rounded up to a power of two); the residual e_s = a_n . E_s - x_s is
+        // a shuffle sum over the sample's lanes
+        const int JL = pow2_at_least(Jn);
+        const int lg = 31 - __clz(JL);
+        const int nitems = cnt << lg;
+#pragma unroll 1
+        for (int o0 = 0; o0 < nitems; o0 += T) {
+          const int o = o0 + tid;
+          const int s = o >> lg, j = o & (JL - 1);
+          const bool live = (o < nitems) && (j < Jn);
+          float e0 = 0.f;
+          if (live) {
+            const float* gv = GT + j * Pp;
+            float a0 = 0.f, a1 = 0.f;
+            if (full_s) {
+              const float4* sv = reinterpret_cast<const float4*>(Sbuf + s * Pp);
+              const float4* g4 = reinterpret_cast<const float4*>(gv);
+              const int nv = Pp >> 2;
+              int v = 0;
+#pragma unroll 1
+              for (; v + 1 < nv; v += 2) {
+                const float4 x = sv[v], y = g4[v];
+                const float4 x2 = sv[v + 1], y2 = g4[v + 1];
                 a0 = fmaf(x.x, y.x, a0); a0 = fmaf(x.y, y.y, a0); a0 = fmaf(x.z, y.z, a0); a0 = fmaf(x.w, y.w, a0);
-                a1 = fmaf(x.x, z.x, a1); a1 = fmaf(x.y, z.y, a1); a1 = fmaf(x.z, z.z, a1); a1 = fmaf(x.w, z.w, a1);
-                b0 = fmaf(x2.x, y2.x, b0); b0 = fmaf(x2.y, y2.y, b0); b0 = fmaf(x2.z, y2.z, b0); b0 = fmaf(x2.w, y2.w, b0);
-                b1 = fmaf(x2.x, z2.x, b1); b1 = fmaf(x2.y, z2.y, b1); b1 = fmaf(x2.z, z2.z, b1); b1 = fmaf(x2.w, z2.w, b1);
+                a1 = fmaf(x2.x, y2.x, a1); a1 = fmaf(x2.y, y2.y, a1); a1 = fmaf(x2.z, y2.z, a1); a1 = fmaf(x2.w, y2.w, a1);
               }
               if (v < nv) {
-                const float4 x = sv[v], y = g0[v], z = g1[v];
+                const float4 x = sv[v], y = g4[v];
                 a0 = fmaf(x.x, y.x, a0); a0 = fmaf(x.y, y.y, a0); a0 = fmaf(x.z, y.z, a0); a0 = fmaf(x.w, y.w, a0);
-                a1 = fmaf(x.x, z.x, a1); a1 = fmaf(x.y, z.y, a1); a1 = fmaf(x.z, z.z, a1); a1 = fmaf(x.w, z.w, a1);
               }
-              acc[q][0] = a0 + b0;
-              acc[q][1] = a1 + b1;
+            } else {
+              const float* rs = rows + s * sumJ;
+#pragma unroll 1
+              for (int cc = 0; cc < Pn; ++cc) a0 = fmaf(kron_entry(rs, cdn[cc], nm1), gv[cc], a0);
             }
+            e0 = a0 + a1;
           }
-        }
-        // combine the two halves, residual e_s = a_n . E_s - x_s (shuffle sum
-        // over the sample's lanes), then the contributions e_s E_s
-#pragma unroll
-        for (int q = 0; q < kOutPerThread; ++q) {
-          const int o0 = q * T;
-          if (o0 < nout) {   // uniform across the block
-            const int o = tid + o0;
-            const int s = o >> lg, rem = o & ((1 << lg) - 1), jt = rem >> 1, h = rem & 1;
-            const bool live = (o < nout) && (jt < ntj);
-            const int j0 = 2 * jt;
-            float e0 = acc[q][0] + __shfl_xor_sync(0xffffffffu, acc[q][0], 1);
-            float e1 = acc[q][1] + __shfl_xor_sync(0xffffffffu, acc[q][1], 1);
-            float part = 0.f;
-            if (live && h == 0) {
-              const float* an = rows + s * sumJ + joff[n];
-              part = an[j0] * e0;
-              if (j0 + 1 < Jn) part = fmaf(an[j0 + 1], e1, part);
-            }
-            for (int off = 1 << (lg - 1); off > 0; off >>= 1) part += __shfl_xor_sync(0xffffffffu, part, off);
-            if (live && h == 0) {
-              const float e = part - fx[s];
-              Ebuf[s * Jmax + j0] = e * e0;
-              if (j0 + 1 < Jn) Ebuf[s * Jmax + j0 + 1] = e * e1;
-            }
-          }
-        }
-        __syncthreads();
-      }
-      // run sums: segmented inclusive scan of the contributions over the
-      // sorted samples, one warp per column j, 32 samples at a time
-      for (int j = warp; j < Jn; j += nwarps) {
-        float carry = 0.f;
-        int pieces = 0;
-        for (int s0 = 0; s0 < cnt; s0 += 32) {
-          const int s = s0 + lane;
-          const bool valid = s < cnt;
-          bool is_head = false;
-          float x = 0.f;
-          if (valid) {
-            is_head = (s == 0) || ((int)(fseg[s] & 0xffffu) == lo + s);
-            x = Ebuf[s * Jmax + j];
-          }
-          const unsigned hmask = __ballot_sync(0xffffffffu, is_head);
-          const unsigned upto = hmask & (0xffffffffu >> (31 - lane));   // heads at lanes <= lane
-          const int first = upto ? 31 - __clz(upto) : -1;              // latest head at or before lane
-          if (lane == 0 && !is_head) x += carry;                       // run continued from the last block
-          const int start = first < 0 ? 0 : first;
-#pragma unroll
-          for (int off = 1; off < 32; off <<= 1) {
-            const float y = __shfl_up_sync(0xffffffffu, x, off);
-            if (lane - off >= start) x += y;
-          }
-          // a piece ends at s when the next sample starts a run or the chunk ends
-          bool ends = false;
-          if (valid) {
-            if (s + 1 >= cnt) ends = true;
-            else ends = ((int)(fseg[s + 1] & 0xffffu) == lo + s + 1);
-          }
-          const int piece = pieces + __popc(upto) - 1;
-          if (ends) Fbuf[piece * Jmax + j] = x;
-          carry = __shfl_sync(0xffffffffu, x, 31);
-          pieces += __popc(hmask);
+          float part = live ? rows[s * sumJ + mJoff[n] + j] * e0 : 0.f;
+#pragma unroll 1
+          for (int off = JL >> 1; off > 0; off >>= 1) part += __shfl_xor_sync(0xffffffffu, part, off);
+          if (live) qbuf[s * Jmax + j] = (part - fx[s]) * e0;
         }
       }
       __syncthreads();
-      // updates (line 23): runs inside the chunk directly; the first and last
-      // pieces, when their runs cross chunk edges, through the arrival count
-      for (int i = tid; i < nheads * Jn; i += T) {
-        const int h = i / Jn, j = i - h * Jn;
-        const int s0 = head[h];
-        const uint32_t sg = fseg[s0];
-        const int st = (int)(sg & 0xffffu), en = (int)(sg >> 16);
-        if (st >= lo && en < hi) {
-          const float F = Fbuf[h * Jmax + j];
-          const float denom = a.norm_mode == 1 ? (float)(en - st + 1) : fm;
-          const int row = fcrd[s0 * N + n];
-          float* ap = a.A[n] + (size_t)row * g.Jp[n] + j;
-          const float av = bf ? __ldcg(ap) : rows[s0 * sumJ + joff[n] + j];
-          const float nv = av - a.lr_a * (F / denom + a.lam_a * av);
-          __stcg(ap, nv);
-          if (bf) __stcg(reinterpret_cast<unsigned short*>(a.Ab[n]) + (size_t)row * g.Jb[n] + j,
-                         __bfloat16_as_ushort(__float2bfloat16_rn(nv)));
-          if (probe && a.probeF) a.probeF[((size_t)n * M + st) * kMaxJ + j] = F;
+      // run sums in sorted order (warp per run piece, lane j), kept in the
+      // run head's row of qbuf; the piece of a run begun in an earlier chunk
+      // is published
+#pragma unroll 1
+      for (int h = warp; h < nheads; h += nwarps)
+        if (lane < Jn) {
+          const int s0 = head[h], s1 = head[h + 1];
+          float F = 0.f;
+#pragma unroll 1
+          for (int s = s0; s < s1; ++s) F += qbuf[s * Jmax + lane];
+          qbuf[s0 * Jmax + lane] = F;
+          if ((int)(fseg[s0] & 0xffffu) < lo) put_word(a.piece + ((unsigned)n * G + c) * (unsigned)Jmax + lane, tag, F);
         }
+      // a run begun here that continues: the pieces of chunks c+1 .. c1,
+      // polled in parallel
+      const uint32_t seg_last = cnt > 0 ? fseg[head[nheads - 1]] : 0u;
+      const int st_last = (int)(seg_last & 0xffffu), en_last = (int)(seg_last >> 16);
+      const bool owner = cnt > 0 && st_last >= lo && en_last >= hi;
+      const int npc = owner ? (en_last / ph.chunk - c) * Jn : 0;
+#pragma unroll 1
+      for (int i = tid; i < npc; i += T) {
+        const int pc = fdiv(i, mFJ[n]), j = i - pc * Jn;
+        const unsigned long long* p = a.piece + ((unsigned)n * G + (unsigned)(c + 1 + pc)) * (unsigned)Jmax + j;
+        pieces_sm[i] = val_of(settle(p, get_word(p), tag, ok, a));
       }
-      if (warp < 2 && nheads > 0) {
-        const int h = (warp == 0) ? 0 : nheads - 1;
-        const int s0 = head[h];
-        const uint32_t sg = fseg[s0];
-        const int st = (int)(sg & 0xffffu), en = (int)(sg >> 16);
-        const bool crosses = (st < lo) || (en >= hi);
-        // warp 0 takes the first piece if its run began before the chunk;
-        // warp 1 takes the last piece if its run began inside and continues
-        const bool mine = crosses && ((warp == 0) ? (st < lo) : (st >= lo));
-        if (mine) {
-          const int slot = (st < lo) ? 0 : 1;
-          if (lane < Jn) __stcg(a.bpart + ((size_t)c * 2 + slot) * kMaxJ + lane, Fbuf[h * Jmax + lane]);
-          // the warp barrier orders the lanes' piece stores before lane 0's
-          // release; the acquire side is completed by a fence on the rare
-          // last-arriver path
-          __syncwarp();
-          const int c0 = st / ph.chunk, c1 = en / ph.chunk;
-          unsigned old = 0;
-          if (lane == 0) old = atom_acq_rel_add_u32(a.bcnt + c1, 1u);
-          old = __shfl_sync(0xffffffffu, old, 0);
-          if (old == (unsigned)(c1 - c0)) {
-            __threadfence();
-            if (lane < Jn) {
-              float F = __ldcg(a.bpart + ((size_t)c0 * 2 + 1) * kMaxJ + lane);
-              for (int cc = c0 + 1; cc <= c1; ++cc) F += __ldcg(a.bpart + ((size_t)cc * 2 + 0) * kMaxJ + lane);
-              const float denom = a.norm_mode == 1 ? (float)(en - st + 1) : fm;
-              const int row = fcrd[s0 * N + n];
-              float* ap = a.A[n] + (size_t)row * g.Jp[n] + lane;
-              const float av = bf ? __ldcg(ap) : rows[s0 * sumJ + joff[n] + lane];
-              const float nv = av - a.lr_a * (F / denom + a.lam_a * av);
-              __stcg(ap, nv);
-              if (bf) __stcg(reinterpret_cast<unsigned short*>(a.Ab[n]) + (size_t)row * g.Jb[n] + lane,
-                             __bfloat16_as_ushort(__float2bfloat16_rn(nv)));
-              if (probe && a.probeF) a.probeF[((size_t)n * M + st) * kMaxJ + lane] = F;
-            }
-            if (lane == 0) a.bcnt[c1] = 0u;
+      if (!__syncthreads_and(ok)) return;
+      // the line-23 update of every run that starts in this chunk (pieces of
+      // a continuing run added in chunk order), warp per run, lane j
+#pragma unroll 1
+      for (int h = warp; h < nheads; h += nwarps)
+        if (lane < Jn) {
+          const int s0 = head[h];
+          const uint32_t sg = fseg[s0];
+          const int st = (int)(sg & 0xffffu), en = (int)(sg >> 16);
+          if (st >= lo) {
+            float F = qbuf[s0 * Jmax + lane];
+            if (en >= hi)
+#pragma unroll 1
+              for (int i = lane; i < npc; i += Jn) F += pieces_sm[i];
+            const float denom = a.norm_mode == 1 ? (float)(en - st + 1) : fm;
+            const unsigned row = (unsigned)fcrd[s0 * N + n];
+            const float av = BF ? master[s0 * Jmax + lane] : rows[s0 * sumJ + mJoff[n] + lane];
+            const float nv = av - a.lr_a * (F / denom + a.lam_a * av);
+            __stcg(mA[n] + row * (unsigned)mJp[n] + lane, nv);
+            if (BF) __stcg(mAb[n] + row * (unsigned)mJb[n] + lane, __bfloat16_as_ushort(__float2bfloat16_rn(nv)));
+            if (n + 1 < N) put_word(a.mail + ((unsigned)n * (unsigned)M + st) * (unsigned)Jmax + lane, tag, nv);
+            if (probe && a.probeF) a.probeF[((unsigned)n * M + st) * kMaxJ + lane] = F;
           }
         }
-      }
-      // meanwhile: G_(n+1) as [j][c] and the next phase's schedule
-      if (warp >= 2 && n + 1 < N) {
-        const int nt = T - 64, t2 = tid - 64;
-        const int n1 = n + 1, Pn1 = g.prodJ / Jr[n1], Pp1 = pad4(Pn1);
-        const int* cof1 = coff + toff + Pn;
-        if (bf) {
-          build_gt_bf16(GThb[n1 & 1], Gsm, cof1, Jr[n1], Pn1, g.gstride[n1], t2, nt);
-        } else {
-          float* GT1 = GTb[n1 & 1];
-          for (int i = t2; i < Jr[n1] * Pp1; i += nt) {
-            const int j = i / Pp1, cc = i - j * Pp1;
-            GT1[i] = cc < Pn1 ? Gsm[cof1[cc] + j * g.gstride[n1]] : 0.f;
-          }
-        }
-      }
-      {
-        const int64_t nb = (n + 1 < N) ? b : b + 1;
-        const int nmode = (n + 1 < N) ? n + 1 : 0;
-        if (nb < a.b1) load_schedule<N>(a, nb, nmode, crdb[buf ^ 1], xsb[buf ^ 1], segb[buf ^ 1]);
-      }
-      buf ^= 1;
-      toff += Pn;
-      if (!grid_barrier(a, generation)) return;
     }
+    buf ^= 1;
   }
 
   if (c == 0) {
+#pragma unroll 1
     for (int i = tid; i < sumJR; i += T) a.B[i] = Bsm[i];
-    for (int lin = tid; lin < g.prodJ; lin += T) {
+#pragma unroll 1
+    for (int lin = tid; lin < prodJ; lin += T) {
       const uint32_t packed = ldig[lin];
       float acc = 0.f;
       for (int r = 0; r < R; ++r) {
         float prod = 1.f;
-#pragma unroll
-        for (int k = 0; k < N; ++k) prod *= Bsm[boff[k] + (int)((packed >> (5 * k)) & 31u) * R + r];
+        for (int k = 0; k < N; ++k) prod *= Bsm[mBoff[k] + (int)((packed >> (5 * k)) & 31u) * R + r];
         acc += prod;
       }
       a.core[lin] = acc;
@@ -993,54 +1214,34 @@ k_epoch(EpochArgs a) {
 
 namespace {
 
-template <int N>
-const void* epoch_fn() {
-  return (const void*)k_epoch<N>;
-}
-
-const void* kernel_for(int N) {
-  switch (N) {
-    case 2: return epoch_fn<2>();
-    case 3: return epoch_fn<3>();
-    case 4: return epoch_fn<4>();
-    case 5: return epoch_fn<5>();
-    case 6: return epoch_fn<6>();
-    default: return nullptr;
-  }
+const void* kernel_for(int precision) {
+  return precision == 1 ? (const void*)k_epoch<true> : (const void*)k_epoch<false>;
 }
 
 }  // namespace
 
 int epoch_chunk_cap(const Geometry& g) {
-  const int lanes = 2 * pow2_at_least((g.Jmax + 1) >> 1);   // lanes per sample in the contraction
-  int cap = kOutPerThread * kEpochThreads / lanes;
-  return cap < kMaxChunk ? cap : kMaxChunk;
+  (void)g;
+  return kMaxChunk;
 }
 
-int epoch_payload_floats(const Geometry& g) {
-  int mx = 0;
-  for (int n = 0; n < g.N; ++n) {
-    const int Jn = g.J[n];
-    const int P = g.R * Jn + (g.R * (g.R - 1) / 2) * Jn * Jn;
-    if (P > mx) mx = P;
-  }
-  return mx;
+int epoch_payload_floats(const Geometry& g) { return payload_max(g); }
+
+bool epoch_gram_fits(const Geometry& g) {
+  return g.sumJ < 256;   // Kronecker columns address a sample's rows with 8-bit offsets
 }
 
-size_t epoch_smem_bytes(const Geometry& g, int chunk_max, int payload_max, int precision) {
-  return (size_t)smem_layout(g, chunk_max, payload_max, precision).total_words * sizeof(float);
+size_t epoch_smem_bytes(const Geometry& g, int chunk_max, int ctas, int precision) {
+  return (size_t)smem_layout(g, chunk_max, ctas, precision).total_words * sizeof(float);
 }
 
-cudaError_t epoch_kernel_setup(int N, size_t smem) {
-  const void* fn = kernel_for(N);
-  if (!fn) return cudaErrorInvalidValue;
-  return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+cudaError_t epoch_kernel_setup(int precision, size_t smem) {
+  return cudaFuncSetAttribute(kernel_for(precision), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
 }
 
-int epoch_max_ctas(int N, size_t smem) {
-  const void* fn = kernel_for(N);
+int epoch_max_ctas(int precision, size_t smem) {
+  const void* fn = kernel_for(precision);
   int dev = 0, sms = 0, per = 0;
-  if (!fn) return 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return 0;
   if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fn, kEpochThreads, smem) != cudaSuccess) return 0;
@@ -1048,11 +1249,9 @@ int epoch_max_ctas(int N, size_t smem) {
 }
 
 cudaError_t launch_epoch(const EpochArgs& a, int ctas, size_t smem, cudaStream_t st) {
-  const void* fn = kernel_for(a.g.N);
-  if (!fn) return cudaErrorInvalidValue;
   EpochArgs copy = a;
   void* args[] = {&copy};
-  return cudaLaunchCooperativeKernel(fn, dim3(ctas), dim3(kEpochThreads), args, smem, st);
+  return cudaLaunchCooperativeKernel(kernel_for(a.precision), dim3(ctas), dim3(kEpochThreads), args, smem, st);
 }
 
 }  // namespace sgdt

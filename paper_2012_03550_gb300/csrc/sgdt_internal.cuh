@@ -15,6 +15,7 @@ constexpr int kEpochThreads = 512;
 constexpr int kScheduleThreads = 512;
 constexpr int kMaxChunk = 128;          // samples per CTA per phase in the epoch kernel
 constexpr int kMaxCorePayload = 8192;   // floats of the per-mode core reduction
+constexpr int kMaxEpochCtas = 256;     // CTAs of the epoch kernel (reductions poll 8 words per lane)
 
 // ---------------------------------------------------------------------------
 // Minibatch sampler: keyed permutation pi_e of [0, n) used to visit the
@@ -94,17 +95,28 @@ struct Geometry {
 //   val(n, t)      = val[(size_t)n * npad + t]
 //   pos(n, t)      = pos[(size_t)n * npad + t]        (batch position before sorting)
 //   seg(n, t)      = seg[(size_t)n * npad + t]        (run start | run end << 16, within the minibatch)
-// and sid[t] the training-entry index pi_e(t).
+//   link(n, k, t)  = link[(size_t)(n * (n - 1) / 2 + k) * npad + t],  k < n:
+//                    the start of the mode-k run that holds the same sample
+//                    (sorted position in the mode-k copy of the minibatch)
+// and sid[t] the training-entry index pi_e(t).  rsp[k][t] (k < N - 1) is the
+// tiler's scratch: the mode-k run start of batch position t - bM.
 struct Schedule {
   int32_t* crd;
   float* val;
   int32_t* pos;
   uint32_t* seg;
   int32_t* sid;
+  int32_t* link;
+  int32_t* rsp;
   int64_t npad;
   int64_t n;
   int M;
 };
+
+// Words per epoch position of a Schedule of order N.
+inline size_t schedule_words_per_position(int N) {
+  return (size_t)N * N + 3 * (size_t)N + 1 + (size_t)N * (N - 1) / 2 + (size_t)(N - 1);
+}
 
 struct EpochArgs {
   Geometry g;
@@ -118,12 +130,13 @@ struct EpochArgs {
   float lr_a, lr_b, lam_a, lam_b;
   int norm_mode;
   int chunk_max;
-  int payload_max;       // floats per CTA partial
-  // scratch
-  float* part;           // [G][payload_max]
-  float* red;            // [payload_max]
-  float* bpart;          // [G][2][kMaxJ]
-  unsigned* bcnt;        // [G]
+  // cross-CTA exchange words: (sequence tag << 32) | float bits
+  uint32_t tag_base;           // tag of (minibatch b, mode n) = tag_base + 8 (b - b0) + n
+  unsigned long long* part;    // [G][pstride]   per-CTA core-phase Gram partials
+  unsigned long long* inbox;   // [G][pstride]   reduced Gram payload, one copy per CTA
+  unsigned long long* piece;   // [N][G][Jmax]   run pieces that continue a run begun in an earlier chunk
+  unsigned long long* mail;    // [N][M][Jmax]   rows updated this minibatch, by mode-n run start
+  int pstride;
   unsigned long long* bar;
   int* err;
   unsigned long long watchdog_ns;
@@ -141,12 +154,13 @@ struct AParams {
 // Launchers (host side, defined in the .cu files).
 cudaError_t launch_schedule(const Geometry& g, const uint32_t* coo, int cs, const Feistel& f,
                             const Schedule& s, int64_t b0, int64_t b1, cudaStream_t st);
-int epoch_payload_floats(const Geometry& g);
+int epoch_payload_floats(const Geometry& g);   // largest core-phase Gram payload over the modes
+bool epoch_gram_fits(const Geometry& g);       // core-phase Gram tiles within the per-thread limit
 cudaError_t launch_mirror_bf16(const Geometry& g, float* const* A, uint16_t* const* Ab, cudaStream_t st);
 int epoch_chunk_cap(const Geometry& g);   // largest samples per CTA per phase the kernel takes
-size_t epoch_smem_bytes(const Geometry& g, int chunk_max, int payload_max, int precision);
-cudaError_t epoch_kernel_setup(int N, size_t smem);
-int epoch_max_ctas(int N, size_t smem);
+size_t epoch_smem_bytes(const Geometry& g, int chunk_max, int ctas, int precision);
+cudaError_t epoch_kernel_setup(int precision, size_t smem);
+int epoch_max_ctas(int precision, size_t smem);
 cudaError_t launch_epoch(const EpochArgs& a, int ctas, size_t smem, cudaStream_t st);
 cudaError_t launch_init_params(const Geometry& g, float* const* A, float* B, int mode, double mu,
                                double sigma, uint64_t seed, cudaStream_t st);

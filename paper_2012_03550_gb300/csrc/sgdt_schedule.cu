@@ -10,7 +10,11 @@
 //   3. tiler: for each mode n, a stable sort of the minibatch by i_n (keys
 //      (i_n, batch position), unique, sorted by an in-shared-memory bitonic
 //      network) and, for every sorted position, the first and last sorted
-//      position of its run of equal i_n.
+//      position of its run of equal i_n;
+//   4. links: for every sorted position of the mode-n copy and every k < n,
+//      the start of the mode-k run holding the same sample, i.e. the slot
+//      under which the epoch kernel publishes that sample's updated mode-k
+//      row during the minibatch.
 // The sorted copies let each phase of the epoch kernel stream its samples
 // contiguously and find the rows it owns without atomics.
 #include "sgdt_internal.cuh"
@@ -87,6 +91,12 @@ k_schedule(Geometry g, const uint32_t* __restrict__ coo, int cs, Feistel f, Sche
       s.val[(size_t)n * s.npad + t] = __uint_as_float(e[g.N]);
       s.pos[(size_t)n * s.npad + t] = pos;
       s.seg[(size_t)n * s.npad + t] = (uint32_t)start | ((uint32_t)end << 16);
+      if (n + 1 < g.N) s.rsp[(size_t)n * s.npad + (size_t)(t0 + pos)] = start;
+      // modes k < n were sorted in earlier passes of this CTA, which wrote
+      // rsp[k]; the pass-ending __syncthreads orders those writes before
+      // these reads
+      for (int k = 0; k < n; ++k)
+        s.link[(size_t)(n * (n - 1) / 2 + k) * s.npad + t] = s.rsp[(size_t)k * s.npad + (size_t)(t0 + pos)];
     }
     __syncthreads();
   }
