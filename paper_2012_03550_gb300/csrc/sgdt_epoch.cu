@@ -93,9 +93,13 @@ __host__ __device__ inline int sum_pn(const Geometry& g) {
   return s;
 }
 
-// Core-phase payload of mode n: g (R x J_n) and the upper triangles of the
-// R(R-1)/2 blocks C_{r r'}, r' < r.
-__host__ __device__ inline int core_payload(int Jn, int R) { return R * Jn + (R * (R - 1) / 2) * tri(Jn); }
+// Core-phase payload of mode n as exchanged (64-bit tagged words, moved two
+// per 16-byte access): g (R rows of J_n, each padded to a multiple of 4) and
+// the upper triangles of the R(R-1)/2 blocks C_{r r'}, r' < r (each padded to
+// a multiple of 4); padding words carry zeros.
+__host__ __device__ inline int core_payload(int Jn, int R) {
+  return R * pad4(Jn) + (R * (R - 1) / 2) * pad4(tri(Jn));
+}
 
 __host__ __device__ inline int payload_max(const Geometry& g) {
   int mx = 0;
@@ -250,6 +254,20 @@ __device__ __forceinline__ unsigned long long get_word(const unsigned long long*
   return w;
 }
 
+__device__ __forceinline__ void put_pair(unsigned long long* p, uint32_t tag, float v0, float v1) {
+  const unsigned long long w0 = ((unsigned long long)tag << 32) | (unsigned long long)__float_as_uint(v0);
+  const unsigned long long w1 = ((unsigned long long)tag << 32) | (unsigned long long)__float_as_uint(v1);
+  asm volatile("st.relaxed.gpu.global.v2.u64 [%0], {%1, %2};" ::"l"(p), "l"(w0), "l"(w1) : "memory");
+}
+
+// Two adjacent tagged words (16-byte aligned) in one access; each word is
+// single-copy atomic and carries its own tag.
+__device__ __forceinline__ ulonglong2 get_pair(const unsigned long long* p) {
+  ulonglong2 w;
+  asm volatile("ld.relaxed.gpu.global.v2.u64 {%0, %1}, [%2];" : "=l"(w.x), "=l"(w.y) : "l"(p) : "memory");
+  return w;
+}
+
 __device__ __forceinline__ uint32_t tag_of(unsigned long long w) { return (uint32_t)(w >> 32); }
 __device__ __forceinline__ float val_of(unsigned long long w) { return __uint_as_float((uint32_t)w); }
 
@@ -305,6 +323,35 @@ __device__ __forceinline__ bool wait_all(const unsigned long long* const (&p)[K]
       if (p[u] && tag_of(w[u]) != tg[u]) {
         done = false;
         w[u] = get_word(p[u]);
+      }
+    if (done) return true;
+    if (t0 == 0) t0 = globaltimer_ns();
+    if (++spins > 4) __nanosleep(32);
+    if ((spins & 15u) == 0u) {
+      if (ld_volatile_int(a.err) != 0) return false;
+      if (globaltimer_ns() - t0 > a.watchdog_ns) {
+        atomicCAS(a.err, 0, STD_ETIMEOUT);
+        return false;
+      }
+    }
+  }
+}
+
+// wait_all for word pairs: p[u] (16-byte aligned, nullptr = absent) must
+// hold `tag` in both words.
+template <int K>
+__device__ __forceinline__ bool wait_pairs(const unsigned long long* const (&p)[K], ulonglong2 (&w)[K], uint32_t tag,
+                                           const EpochArgs& a) {
+  unsigned long long t0 = 0;
+  unsigned spins = 0;
+#pragma unroll 1
+  while (true) {
+    bool done = true;
+#pragma unroll
+    for (int u = 0; u < K; ++u)
+      if (p[u] && (tag_of(w[u].x) != tag || tag_of(w[u].y) != tag)) {
+        done = false;
+        w[u] = get_pair(p[u]);
       }
     if (done) return true;
     if (t0 == 0) t0 = globaltimer_ns();
@@ -653,11 +700,12 @@ k_epoch(EpochArgs a) {
       const int Jq = pad4(Jn);
       const int K = R * Jn;
       const int Kq = pad4(K);
-      const int P = K + npairs * tJ;
+      const int Kx = R * Jq;                  // exchanged g rows, padded
+      const int P = Kx + npairs * tJp;        // exchanged payload (multiple of 4 words)
       const uint32_t tag = tag0 + (uint32_t)n;
       const int nq4 = tJp >> 2, na4 = Jq >> 2;
       const int ntile = R * na4 + npairs * nq4;
-      const FastDiv f_na4 = mFna4[n], f_nq4 = mFnq4[n], f_tJ = mFtJ[n];
+      const FastDiv f_na4 = mFna4[n], f_nq4 = mFnq4[n];
       // left Gram operand rows, one sample per 16-lane group (R <= 16) or
       // per warp: lane r forms w_r, the residual e_s (group sum), e_s w_r and
       // w_r w_r' (r' < r); right operand rows of this mode unless built above
@@ -703,21 +751,18 @@ k_epoch(EpochArgs a) {
         unsigned long long* dst = a.part + (unsigned)c * (unsigned)a.pstride;
 #pragma unroll 1
         for (int t = tid; t < ntile; t += T) {
-          int li, rc, obase, width;
+          int li, rc;
           if (t < R * na4) {
             const int r = fdiv(t, f_na4), jg = t - r * na4;
             li = npairs + r;
             rc = tJp + 4 * jg;
-            obase = r * Jn + 4 * jg;
-            width = Jn - 4 * jg;
           } else {
             const int t2 = t - R * na4;
             const int qi = fdiv(t2, f_nq4), jg = t2 - qi * nq4;
             li = qi;
             rc = 4 * jg;
-            obase = K + qi * tJ + 4 * jg;
-            width = tJ - 4 * jg;
           }
+          const int obase = 4 * t;   // tiles are the payload's 4-word groups in order
           float4 x0 = make_float4(0.f, 0.f, 0.f, 0.f), x1 = x0;
           const float* lp = left + li;
           const float* rp = rbase + rc;
@@ -738,69 +783,68 @@ k_epoch(EpochArgs a) {
             x0.x = fmaf(l0, r0.x, x0.x); x0.y = fmaf(l0, r0.y, x0.y);
             x0.z = fmaf(l0, r0.z, x0.z); x0.w = fmaf(l0, r0.w, x0.w);
           }
-          put_word(dst + obase, tag, x0.x + x1.x);
-          if (width > 1) put_word(dst + obase + 1, tag, x0.y + x1.y);
-          if (width > 2) put_word(dst + obase + 2, tag, x0.z + x1.z);
-          if (width > 3) put_word(dst + obase + 3, tag, x0.w + x1.w);
+          put_pair(dst + obase, tag, x0.x + x1.x, x0.y + x1.y);
+          put_pair(dst + obase + 2, tag, x0.z + x1.z, x0.w + x1.w);
         }
       }
-      // hop 1: CTA c sums its slice of the payload over all CTAs (in CTA
-      // order within each lane, then a fixed butterfly across lanes) and
-      // pushes each sum into every CTA's copy of the payload
+      // hop 1: CTA c sums its slice of the payload (word pairs) over all CTAs
+      // (in CTA order within each lane, then a fixed butterfly across lanes)
+      // and pushes each sum into every CTA's copy of the payload
       bool ok = true;
       {
-        const int per = (P + G - 1) / G;
-        const int o_lo = c * per, o_hi = min(o_lo + per, P);
+        const int P2 = P >> 1;
+        const int per = (P2 + G - 1) / G;
+        const int o_lo = c * per, o_hi = min(o_lo + per, P2);
 #pragma unroll 1
         for (int o = o_lo + warp; o < o_hi; o += nwarps) {
-          unsigned long long w8[8];
+          ulonglong2 w8[8];
           const unsigned long long* p8[8];
-          uint32_t t8[8];
 #pragma unroll
           for (int u = 0; u < 8; ++u) {
             const int cc = lane + 32 * u;
-            p8[u] = cc < G ? a.part + (unsigned)cc * (unsigned)a.pstride + o : nullptr;
-            w8[u] = p8[u] ? get_word(p8[u]) : 0ULL;
-            t8[u] = tag;
+            p8[u] = cc < G ? a.part + (unsigned)cc * (unsigned)a.pstride + 2 * o : nullptr;
+            w8[u] = p8[u] ? get_pair(p8[u]) : make_ulonglong2(0ULL, 0ULL);
           }
-          if (ok) ok = wait_all<8>(p8, w8, t8, a);
-          float s = 0.f;
+          if (ok) ok = wait_pairs<8>(p8, w8, tag, a);
+          float s0 = 0.f, s1 = 0.f;
 #pragma unroll
           for (int u = 0; u < 8; ++u)
-            if (p8[u]) s += val_of(w8[u]);
+            if (p8[u]) {
+              s0 += val_of(w8[u].x);
+              s1 += val_of(w8[u].y);
+            }
 #pragma unroll
-          for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+          for (int off = 16; off > 0; off >>= 1) {
+            s0 += __shfl_xor_sync(0xffffffffu, s0, off);
+            s1 += __shfl_xor_sync(0xffffffffu, s1, off);
+          }
           if (ok)
 #pragma unroll 1
-            for (int cc = lane; cc < G; cc += 32) put_word(a.inbox + (unsigned)cc * (unsigned)a.pstride + o, tag, s);
+            for (int cc = lane; cc < G; cc += 32) put_pair(a.inbox + (unsigned)cc * (unsigned)a.pstride + 2 * o, tag, s0, s1);
         }
       }
-      // hop 2: this CTA's copy of the reduced payload, into shared memory,
-      // each block C_{r r'} unpacked to full rows of stride pad4(J_n)
+      // hop 2: this CTA's copy of the reduced payload, into shared memory: g
+      // as R x J_n, each block C_{r r'} unpacked to full rows of stride
+      // pad4(J_n)
       {
         const unsigned long long* mine = a.inbox + (unsigned)c * (unsigned)a.pstride;
 #pragma unroll 1
-        for (int o0 = tid; o0 < P; o0 += 2 * T) {
-          unsigned long long w2[2];
-          const unsigned long long* p2[2];
-          uint32_t t2[2];
+        for (int o2 = tid; o2 < (P >> 1); o2 += T) {
+          ulonglong2 w1[1];
+          const unsigned long long* p1[1] = {mine + 2 * o2};
+          w1[0] = get_pair(p1[0]);
+          if (ok) ok = wait_pairs<1>(p1, w1, tag, a);
 #pragma unroll
           for (int u = 0; u < 2; ++u) {
-            p2[u] = (o0 + u * T < P) ? mine + o0 + u * T : nullptr;
-            w2[u] = p2[u] ? get_word(p2[u]) : 0ULL;
-            t2[u] = tag;
-          }
-          if (ok) ok = wait_all<2>(p2, w2, t2, a);
-#pragma unroll
-          for (int u = 0; u < 2; ++u) {
-            const int o = o0 + u * T;
-            if (o < P) {
-              const float v = val_of(w2[u]);
-              if (o < K) {
-                redsm[o] = v;
-              } else {
-                const int t = o - K;
-                const int q = fdiv(t, f_tJ), jj = t - q * tJ;
+            const int o = 2 * o2 + u;
+            const float v = val_of(u == 0 ? w1[0].x : w1[0].y);
+            if (o < Kx) {
+              const int r = fdiv(o >> 2, f_na4), j = o - r * Jq;
+              if (j < Jn) redsm[r * Jn + j] = v;
+            } else {
+              const int t = o - Kx;
+              const int q = fdiv(t >> 2, f_nq4), jj = t - q * tJp;
+              if (jj < tJ) {
                 const int ja = trij[jj] & 0xff, jb = trij[jj] >> 8;
                 float* blk = redsm + Kq + q * Jn * Jq;
                 blk[ja * Jq + jb] = v;
