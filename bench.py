@@ -52,6 +52,10 @@ def _args():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-bf16", action="store_true")
+    p.add_argument("--no-kruskal", action="store_true")
+    p.add_argument("--sweep", action="store_true",
+                   help="rank sweep of the paper's parameter study instead of the default line: one JSON "
+                        "line per (ranks, R_core) point on a fixed rating tensor (--scale, default 0.05)")
     return p.parse_args()
 
 
@@ -301,6 +305,38 @@ def run_gpu(a):
                 "bytes_per_nnz": _bytes_per_nnz(N, J, 2),
                 "note": "same schedule and initial state as the FP32 run; RMSE after the same epochs"}
         B.std_destroy(cx16)
+    # the Kruskal form of the factor-phase contraction (E_s = B(n) w_s, the
+    # same product as the Kronecker rows against the unfolded core)
+    kru = None
+    if not a.no_kruskal:
+        ok_ = B.std_default_options()
+        ok_.r_core = R
+        ok_.ptr_kind = 1
+        ok_.contraction = 1
+        ok_.stream = stream.cuda_stream
+        cxk = B.std_create(N, t.shape, w.ranks, c.shape[0], dc, dv, ok_)
+        B.std_set_params(cxk, [np.ascontiguousarray(x) for x in A0], [np.ascontiguousarray(x) for x in B0], 0)
+        rmk = None
+        for _ in range(a.warmup):
+            B.std_sgd_epoch(cxk, w.lr, w.lr, w.lam, w.lam, M)
+            B.std_rmse(cxk, tc.shape[0], dtc, dtv)
+        torch.cuda.synchronize()
+        k0 = torch.cuda.Event(enable_timing=True)
+        k1 = torch.cuda.Event(enable_timing=True)
+        k0.record(stream)
+        updk = []
+        for _ in range(a.steps):
+            stk = B.std_sgd_epoch(cxk, w.lr, w.lr, w.lam, w.lam, M)
+            rmk = B.std_rmse(cxk, tc.shape[0], dtc, dtv)
+            updk.append(stk["update_seconds"])
+        k1.record(stream)
+        torch.cuda.synchronize()
+        vk, ek = D.weak_scaling_rate(float(n_train * a.steps), k0.elapsed_time(k1) * 1e-3, device=dev)
+        kru = {"value": vk, "unit": "nnz/s", "ms_per_step": 1e3 * ek / a.steps,
+               "kernel_ms": 1e3 * sum(updk) / len(updk), "speedup_vs_kronecker": vk / value,
+               "test_rmse": rmk[0], "test_rmse_gap_vs_kronecker": abs(rmk[0] - rm[0]),
+               "note": "FP32; same schedule and initial state as the main line"}
+        B.std_destroy(cxk)
     del dc, dv
 
     # roofline of the dominant kernel (the persistent update kernel)
@@ -378,6 +414,7 @@ def run_gpu(a):
             "cpu_baseline": cpu,
             "e2e": e2e,
             "bf16": bf16,
+            "kruskal_contraction": kru,
             "gpu_launches": 4 * a.steps,
             "clocks": clocks,
             "test_rmse": rm[0] if rm else None,
@@ -390,10 +427,60 @@ def run_gpu(a):
     return 0
 
 
+def run_sweep(a):
+    """Epoch time and test RMSE over the rank sweep (one line per point)."""
+    import numpy as np
+    import torch
+
+    import __graft_entry__ as ge
+    ge.build()
+    from paper_2012_03550_gb300 import binding as B
+    from paper_2012_03550_gb300 import synth
+
+    scale = a.scale if a.scale != 1.0 else 0.05
+    w, points = synth.ranksweep(scale=scale)
+    t = w.tensor
+    c, v = t.split("train")
+    tc, tv = t.split("test")
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.Stream(device=dev)
+    dc, dv = torch.from_numpy(c).to(dev), torch.from_numpy(v).to(dev)
+    dtc, dtv = torch.from_numpy(tc).to(dev), torch.from_numpy(tv).to(dev)
+    for ranks, R in points:
+        A0, B0 = synth.init_params(t.shape, ranks, R, mode="rating", seed=1, mean_value=float(np.mean(v)))
+        opt = B.std_default_options()
+        opt.r_core = R
+        opt.ptr_kind = 1
+        opt.stream = stream.cuda_stream
+        ctx = B.std_create(t.order, t.shape, ranks, c.shape[0], dc, dv, opt)
+        B.std_set_params(ctx, [np.ascontiguousarray(x) for x in A0], [np.ascontiguousarray(x) for x in B0], 0)
+        for _ in range(a.warmup):
+            B.std_sgd_epoch(ctx, w.lr, w.lr, w.lam, w.lam, w.minibatch)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(a.steps):
+            B.std_sgd_epoch(ctx, w.lr, w.lr, w.lam, w.lam, w.minibatch)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / a.steps
+        rm = B.std_rmse(ctx, tc.shape[0], dtc, dtv)
+        B.std_destroy(ctx)
+        line = {"metric": "rank sweep: epoch time and test RMSE", "workload": w.name, "ranks": list(ranks),
+                "r_core": R, "minibatch": w.minibatch, "epochs": a.warmup + a.steps, "ms_per_epoch": ms,
+                "value": c.shape[0] / (ms * 1e-3), "unit": "nnz/s", "test_rmse": rm[0], "test_mae": rm[1],
+                "data": "synthetic"}
+        print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     a = _args()
     if a.impl == "reference":
         return run_reference(a)
+    if a.sweep:
+        return run_sweep(a)
     return run_gpu(a)
 
 

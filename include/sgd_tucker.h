@@ -77,6 +77,12 @@ typedef struct {
     void*    stream;      /* cudaStream_t for every kernel and copy; NULL = the legacy stream */
     uint64_t watchdog_ns; /* grid-barrier wait budget in ns; 0 = 2e9 (2 s) */
     uint64_t hbm_budget_bytes; /* cap on the context's device allocations; 0 = none */
+    int32_t  contraction; /* factor-phase E_s = G-hat_(n) S_s^T (Eq. 11, Algorithm 1 lines
+                             19-20): 0 = Kronecker row S_s against the unfolded core (default);
+                             1 = the same product through the core's Kruskal form (Eq. 4):
+                             E_s = B(n) w_s, w_s[r] = prod_{k != n} <a(k)_{i_k,:}, b(k)_{:,r}>,
+                             O(R sum_k J_k) instead of O(J_n prod_{k != n} J_k) per sample */
+    int32_t  reserved;    /* must be 0 */
 } std_options;
 
 /* Fill *opt with the defaults listed above. */
@@ -122,6 +128,8 @@ typedef struct {
  * uses its own size as M in every normaliser.  Per minibatch:
  *   core phase, n = 1..N, r = 1..R_core in order (Algorithm 1 lines 1-15):
  *     b(n)_r <- b(n)_r - lr_b (V / M + lambda_b b(n)_r),  V of Eq. 15;
+ *     lr_b = 0 leaves B unchanged and the core phase is skipped (the paper's
+ *     schedule that updates B only in some epochs, Sec. 5.3);
  *   G-hat from B (line 16, Eq. 4);
  *   factor phase, n = 1..N in order (lines 17-25): every row i touched by the
  *     minibatch, all rows of a mode reading the state before that mode's update:

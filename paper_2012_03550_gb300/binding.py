@@ -53,6 +53,8 @@ class std_options(ctypes.Structure):
         ("stream", ctypes.c_void_p),
         ("watchdog_ns", ctypes.c_uint64),
         ("hbm_budget_bytes", ctypes.c_uint64),
+        ("contraction", ctypes.c_int32),
+        ("reserved", ctypes.c_int32),
     ]
 
 

@@ -308,6 +308,7 @@ int run_batches(std_ctx* c, float lr_a, float lr_b, float lam_a, float lam_b, in
   a.lam_a = lam_a;
   a.lam_b = lam_b;
   a.norm_mode = c->opt.norm_mode;
+  a.contraction = c->opt.contraction;
   a.chunk_max = chunk;
   a.tag_base = tag_base;
   a.part = c->part;
@@ -371,6 +372,8 @@ void std_default_options(std_options* opt) {
   opt->stream = nullptr;
   opt->watchdog_ns = 0;
   opt->hbm_budget_bytes = 0;
+  opt->contraction = 0;
+  opt->reserved = 0;
 }
 
 const char* std_last_error(void) { return g_last_error.c_str(); }
@@ -411,6 +414,8 @@ int std_create(std_ctx** out, int32_t order, const int64_t* mode_sizes, const in
   if (opt.init_mode != 0 && opt.init_mode != 1) return set_error(STD_EINVAL, "init_mode must be 0 or 1");
   if (opt.ptr_kind != 0 && opt.ptr_kind != 1) return set_error(STD_EINVAL, "ptr_kind must be 0 or 1");
   if (opt.ctas < 0) return set_error(STD_EINVAL, "ctas must be >= 0");
+  if (opt.contraction != 0 && opt.contraction != 1) return set_error(STD_EINVAL, "contraction must be 0 or 1");
+  if (opt.reserved != 0) return set_error(STD_EINVAL, "reserved option field must be 0");
   Geometry g{};
   g.N = order;
   g.R = opt.r_core;

@@ -662,280 +662,283 @@ k_epoch(EpochArgs a) {
       for (int s = warp; s < cnt; s += nwarps)
         if (lane < mJ[0]) master[s * Jmax + lane] = __ldcg(mA[0] + (unsigned)crd[s * N] * (unsigned)mJp[0] + lane);
     __syncthreads();
-    // p[s][k][r] (warp per sample, lane per (k, r)) and, when they fit, the
-    // right Gram operand rows of every mode (they depend on A only)
-#pragma unroll 1
-    for (int s = warp; s < cnt; s += nwarps) {
-      const float* rs = rows + s * sumJ;
-#pragma unroll 1
-      for (int kr = lane; kr < NR; kr += 32) {
-        const int k = fdiv(kr, f_R), r = kr - k * R;
-        const float* ar = rs + mJoff[k];
-        const float* br = Bsm + mBoff[k] + r;
-        float acc0 = 0.f, acc1 = 0.f;
-        int j = 0;
-#pragma unroll 1
-        for (; j + 1 < mJ[k]; j += 2) {
-          acc0 = fmaf(ar[j], br[j * R], acc0);
-          acc1 = fmaf(ar[j + 1], br[(j + 1) * R], acc1);
-        }
-        if (j < mJ[k]) acc0 = fmaf(ar[j], br[j * R], acc0);
-        pbuf[s * NR + kr] = acc0 + acc1;
-      }
-      if (L.rpre)
-#pragma unroll 1
-        for (int n = 0; n < N; ++n) {
-          const int Jn = mJ[n];
-          right_row(right + s * rw + mRoff[n], rs + mJoff[n], Jn, tri(Jn), pad4(tri(Jn)), right_width(Jn), trij,
-                    lane);
-        }
-    }
-    __syncthreads();
-
-#pragma unroll 1
-    for (int n = 0; n < N; ++n) {
-      const int Jn = mJ[n];
-      const int tJ = tri(Jn);
-      const int tJp = pad4(tJ);
-      const int Jq = pad4(Jn);
-      const int K = R * Jn;
-      const int Kq = pad4(K);
-      const int Kx = R * Jq;                  // exchanged g rows, padded
-      const int P = Kx + npairs * tJp;        // exchanged payload (multiple of 4 words)
-      const uint32_t tag = tag0 + (uint32_t)n;
-      const int nq4 = tJp >> 2, na4 = Jq >> 2;
-      const int ntile = R * na4 + npairs * nq4;
-      const FastDiv f_na4 = mFna4[n], f_nq4 = mFnq4[n];
-      // left Gram operand rows, one sample per 16-lane group (R <= 16) or
-      // per warp: lane r forms w_r, the residual e_s (group sum), e_s w_r and
-      // w_r w_r' (r' < r); right operand rows of this mode unless built above
-      {
-        const int gl = R <= 16 ? 16 : 32;
-        const int gpw = 32 / gl;
-        const int sub = lane / gl, gla = lane - sub * gl;
-        const int gbase = sub * gl;
-#pragma unroll 1
-        for (int s0 = warp * gpw; s0 < cnt; s0 += nwarps * gpw) {
-          const int s = s0 + sub;
-          const bool live = (s < cnt) && (gla < R);
-          float w = 0.f, contrib = 0.f;
-          if (live) {
-            const float* ps = pbuf + s * NR + gla;
-            w = 1.f;
-#pragma unroll 1
-            for (int k = 0; k < N; ++k)
-              if (k != n) w *= ps[k * R];
-            contrib = w * ps[n * R];
+    // lr_b = 0 leaves B unchanged: the core phase is skipped
+    if (a.lr_b != 0.f) {
+      // p[s][k][r] (warp per sample, lane per (k, r)) and, when they fit, the
+      // right Gram operand rows of every mode (they depend on A only)
+  #pragma unroll 1
+      for (int s = warp; s < cnt; s += nwarps) {
+        const float* rs = rows + s * sumJ;
+  #pragma unroll 1
+        for (int kr = lane; kr < NR; kr += 32) {
+          const int k = fdiv(kr, f_R), r = kr - k * R;
+          const float* ar = rs + mJoff[k];
+          const float* br = Bsm + mBoff[k] + r;
+          float acc0 = 0.f, acc1 = 0.f;
+          int j = 0;
+  #pragma unroll 1
+          for (; j + 1 < mJ[k]; j += 2) {
+            acc0 = fmaf(ar[j], br[j * R], acc0);
+            acc1 = fmaf(ar[j + 1], br[(j + 1) * R], acc1);
           }
-#pragma unroll
-          for (int off = 16; off > 0; off >>= 1)
-            if (off < gl) contrib += __shfl_xor_sync(0xffffffffu, contrib, off);
-          float* lrow = left + s * lw;
-#pragma unroll 1
-          for (int rp = 0; rp + 1 < R; ++rp) {
-            const float wp = __shfl_sync(0xffffffffu, w, gbase + rp);
-            if (live && rp < gla) lrow[gla * (gla - 1) / 2 + rp] = w * wp;
-          }
-          if (live) lrow[npairs + gla] = (contrib - xs[s]) * w;
+          if (j < mJ[k]) acc0 = fmaf(ar[j], br[j * R], acc0);
+          pbuf[s * NR + kr] = acc0 + acc1;
         }
-        if (!L.rpre)
-#pragma unroll 1
-          for (int s = warp; s < cnt; s += nwarps)
-            right_row(right + s * rw, rows + s * sumJ + mJoff[n], Jn, tJ, tJp, right_width(Jn), trij, lane);
+        if (L.rpre)
+  #pragma unroll 1
+          for (int n = 0; n < N; ++n) {
+            const int Jn = mJ[n];
+            right_row(right + s * rw + mRoff[n], rs + mJoff[n], Jn, tri(Jn), pad4(tri(Jn)), right_width(Jn), trij,
+                      lane);
+          }
       }
       __syncthreads();
-      // Gram partial, thread tile = one left column x 4 right columns over
-      // the chunk, published as soon as it is summed
-      {
-        const float* rbase = right + mRoff[n];
-        unsigned long long* dst = a.part + (unsigned)c * (unsigned)a.pstride;
-#pragma unroll 1
-        for (int t = tid; t < ntile; t += T) {
-          int li, rc;
-          if (t < R * na4) {
-            const int r = fdiv(t, f_na4), jg = t - r * na4;
-            li = npairs + r;
-            rc = tJp + 4 * jg;
-          } else {
-            const int t2 = t - R * na4;
-            const int qi = fdiv(t2, f_nq4), jg = t2 - qi * nq4;
-            li = qi;
-            rc = 4 * jg;
-          }
-          const int obase = 4 * t;   // tiles are the payload's 4-word groups in order
-          float4 x0 = make_float4(0.f, 0.f, 0.f, 0.f), x1 = x0;
-          const float* lp = left + li;
-          const float* rp = rbase + rc;
-          int s = 0;
-#pragma unroll 1
-          for (; s + 1 < cnt; s += 2) {
-            const float l0 = lp[s * lw], l1 = lp[(s + 1) * lw];
-            const float4 r0 = *reinterpret_cast<const float4*>(rp + s * rw);
-            const float4 r1 = *reinterpret_cast<const float4*>(rp + (s + 1) * rw);
-            x0.x = fmaf(l0, r0.x, x0.x); x0.y = fmaf(l0, r0.y, x0.y);
-            x0.z = fmaf(l0, r0.z, x0.z); x0.w = fmaf(l0, r0.w, x0.w);
-            x1.x = fmaf(l1, r1.x, x1.x); x1.y = fmaf(l1, r1.y, x1.y);
-            x1.z = fmaf(l1, r1.z, x1.z); x1.w = fmaf(l1, r1.w, x1.w);
-          }
-          if (s < cnt) {
-            const float l0 = lp[s * lw];
-            const float4 r0 = *reinterpret_cast<const float4*>(rp + s * rw);
-            x0.x = fmaf(l0, r0.x, x0.x); x0.y = fmaf(l0, r0.y, x0.y);
-            x0.z = fmaf(l0, r0.z, x0.z); x0.w = fmaf(l0, r0.w, x0.w);
-          }
-          put_pair(dst + obase, tag, x0.x + x1.x, x0.y + x1.y);
-          put_pair(dst + obase + 2, tag, x0.z + x1.z, x0.w + x1.w);
-        }
-      }
-      // hop 1: CTA c sums its slice of the payload (word pairs) over all CTAs
-      // (in CTA order within each lane, then a fixed butterfly across lanes)
-      // and pushes each sum into every CTA's copy of the payload
-      bool ok = true;
-      {
-        const int P2 = P >> 1;
-        const int per = (P2 + G - 1) / G;
-        const int o_lo = c * per, o_hi = min(o_lo + per, P2);
-#pragma unroll 1
-        for (int o = o_lo + warp; o < o_hi; o += nwarps) {
-          ulonglong2 w8[8];
-          const unsigned long long* p8[8];
-#pragma unroll
-          for (int u = 0; u < 8; ++u) {
-            const int cc = lane + 32 * u;
-            p8[u] = cc < G ? a.part + (unsigned)cc * (unsigned)a.pstride + 2 * o : nullptr;
-            w8[u] = p8[u] ? get_pair(p8[u]) : make_ulonglong2(0ULL, 0ULL);
-          }
-          if (ok) ok = wait_pairs<8>(p8, w8, tag, a);
-          float s0 = 0.f, s1 = 0.f;
-#pragma unroll
-          for (int u = 0; u < 8; ++u)
-            if (p8[u]) {
-              s0 += val_of(w8[u].x);
-              s1 += val_of(w8[u].y);
+
+  #pragma unroll 1
+      for (int n = 0; n < N; ++n) {
+        const int Jn = mJ[n];
+        const int tJ = tri(Jn);
+        const int tJp = pad4(tJ);
+        const int Jq = pad4(Jn);
+        const int K = R * Jn;
+        const int Kq = pad4(K);
+        const int Kx = R * Jq;                  // exchanged g rows, padded
+        const int P = Kx + npairs * tJp;        // exchanged payload (multiple of 4 words)
+        const uint32_t tag = tag0 + (uint32_t)n;
+        const int nq4 = tJp >> 2, na4 = Jq >> 2;
+        const int ntile = R * na4 + npairs * nq4;
+        const FastDiv f_na4 = mFna4[n], f_nq4 = mFnq4[n];
+        // left Gram operand rows, one sample per 16-lane group (R <= 16) or
+        // per warp: lane r forms w_r, the residual e_s (group sum), e_s w_r and
+        // w_r w_r' (r' < r); right operand rows of this mode unless built above
+        {
+          const int gl = R <= 16 ? 16 : 32;
+          const int gpw = 32 / gl;
+          const int sub = lane / gl, gla = lane - sub * gl;
+          const int gbase = sub * gl;
+  #pragma unroll 1
+          for (int s0 = warp * gpw; s0 < cnt; s0 += nwarps * gpw) {
+            const int s = s0 + sub;
+            const bool live = (s < cnt) && (gla < R);
+            float w = 0.f, contrib = 0.f;
+            if (live) {
+              const float* ps = pbuf + s * NR + gla;
+              w = 1.f;
+  #pragma unroll 1
+              for (int k = 0; k < N; ++k)
+                if (k != n) w *= ps[k * R];
+              contrib = w * ps[n * R];
             }
-#pragma unroll
-          for (int off = 16; off > 0; off >>= 1) {
-            s0 += __shfl_xor_sync(0xffffffffu, s0, off);
-            s1 += __shfl_xor_sync(0xffffffffu, s1, off);
+  #pragma unroll
+            for (int off = 16; off > 0; off >>= 1)
+              if (off < gl) contrib += __shfl_xor_sync(0xffffffffu, contrib, off);
+            float* lrow = left + s * lw;
+  #pragma unroll 1
+            for (int rp = 0; rp + 1 < R; ++rp) {
+              const float wp = __shfl_sync(0xffffffffu, w, gbase + rp);
+              if (live && rp < gla) lrow[gla * (gla - 1) / 2 + rp] = w * wp;
+            }
+            if (live) lrow[npairs + gla] = (contrib - xs[s]) * w;
           }
-          if (ok)
-#pragma unroll 1
-            for (int cc = lane; cc < G; cc += 32) put_pair(a.inbox + (unsigned)cc * (unsigned)a.pstride + 2 * o, tag, s0, s1);
+          if (!L.rpre)
+  #pragma unroll 1
+            for (int s = warp; s < cnt; s += nwarps)
+              right_row(right + s * rw, rows + s * sumJ + mJoff[n], Jn, tJ, tJp, right_width(Jn), trij, lane);
         }
-      }
-      // hop 2: this CTA's copy of the reduced payload, into shared memory: g
-      // as R x J_n, each block C_{r r'} unpacked to full rows of stride
-      // pad4(J_n)
-      {
-        const unsigned long long* mine = a.inbox + (unsigned)c * (unsigned)a.pstride;
-#pragma unroll 1
-        for (int o2 = tid; o2 < (P >> 1); o2 += T) {
-          ulonglong2 w1[1];
-          const unsigned long long* p1[1] = {mine + 2 * o2};
-          w1[0] = get_pair(p1[0]);
-          if (ok) ok = wait_pairs<1>(p1, w1, tag, a);
-#pragma unroll
-          for (int u = 0; u < 2; ++u) {
-            const int o = 2 * o2 + u;
-            const float v = val_of(u == 0 ? w1[0].x : w1[0].y);
-            if (o < Kx) {
-              const int r = fdiv(o >> 2, f_na4), j = o - r * Jq;
-              if (j < Jn) redsm[r * Jn + j] = v;
+        __syncthreads();
+        // Gram partial, thread tile = one left column x 4 right columns over
+        // the chunk, published as soon as it is summed
+        {
+          const float* rbase = right + mRoff[n];
+          unsigned long long* dst = a.part + (unsigned)c * (unsigned)a.pstride;
+  #pragma unroll 1
+          for (int t = tid; t < ntile; t += T) {
+            int li, rc;
+            if (t < R * na4) {
+              const int r = fdiv(t, f_na4), jg = t - r * na4;
+              li = npairs + r;
+              rc = tJp + 4 * jg;
             } else {
-              const int t = o - Kx;
-              const int q = fdiv(t >> 2, f_nq4), jj = t - q * tJp;
-              if (jj < tJ) {
-                const int ja = trij[jj] & 0xff, jb = trij[jj] >> 8;
-                float* blk = redsm + Kq + q * Jn * Jq;
-                blk[ja * Jq + jb] = v;
-                blk[jb * Jq + ja] = v;
+              const int t2 = t - R * na4;
+              const int qi = fdiv(t2, f_nq4), jg = t2 - qi * nq4;
+              li = qi;
+              rc = 4 * jg;
+            }
+            const int obase = 4 * t;   // tiles are the payload's 4-word groups in order
+            float4 x0 = make_float4(0.f, 0.f, 0.f, 0.f), x1 = x0;
+            const float* lp = left + li;
+            const float* rp = rbase + rc;
+            int s = 0;
+  #pragma unroll 1
+            for (; s + 1 < cnt; s += 2) {
+              const float l0 = lp[s * lw], l1 = lp[(s + 1) * lw];
+              const float4 r0 = *reinterpret_cast<const float4*>(rp + s * rw);
+              const float4 r1 = *reinterpret_cast<const float4*>(rp + (s + 1) * rw);
+              x0.x = fmaf(l0, r0.x, x0.x); x0.y = fmaf(l0, r0.y, x0.y);
+              x0.z = fmaf(l0, r0.z, x0.z); x0.w = fmaf(l0, r0.w, x0.w);
+              x1.x = fmaf(l1, r1.x, x1.x); x1.y = fmaf(l1, r1.y, x1.y);
+              x1.z = fmaf(l1, r1.z, x1.z); x1.w = fmaf(l1, r1.w, x1.w);
+            }
+            if (s < cnt) {
+              const float l0 = lp[s * lw];
+              const float4 r0 = *reinterpret_cast<const float4*>(rp + s * rw);
+              x0.x = fmaf(l0, r0.x, x0.x); x0.y = fmaf(l0, r0.y, x0.y);
+              x0.z = fmaf(l0, r0.z, x0.z); x0.w = fmaf(l0, r0.w, x0.w);
+            }
+            put_pair(dst + obase, tag, x0.x + x1.x, x0.y + x1.y);
+            put_pair(dst + obase + 2, tag, x0.z + x1.z, x0.w + x1.w);
+          }
+        }
+        // hop 1: CTA c sums its slice of the payload (word pairs) over all CTAs
+        // (in CTA order within each lane, then a fixed butterfly across lanes)
+        // and pushes each sum into every CTA's copy of the payload
+        bool ok = true;
+        {
+          const int P2 = P >> 1;
+          const int per = (P2 + G - 1) / G;
+          const int o_lo = c * per, o_hi = min(o_lo + per, P2);
+  #pragma unroll 1
+          for (int o = o_lo + warp; o < o_hi; o += nwarps) {
+            ulonglong2 w8[8];
+            const unsigned long long* p8[8];
+  #pragma unroll
+            for (int u = 0; u < 8; ++u) {
+              const int cc = lane + 32 * u;
+              p8[u] = cc < G ? a.part + (unsigned)cc * (unsigned)a.pstride + 2 * o : nullptr;
+              w8[u] = p8[u] ? get_pair(p8[u]) : make_ulonglong2(0ULL, 0ULL);
+            }
+            if (ok) ok = wait_pairs<8>(p8, w8, tag, a);
+            float s0 = 0.f, s1 = 0.f;
+  #pragma unroll
+            for (int u = 0; u < 8; ++u)
+              if (p8[u]) {
+                s0 += val_of(w8[u].x);
+                s1 += val_of(w8[u].y);
+              }
+  #pragma unroll
+            for (int off = 16; off > 0; off >>= 1) {
+              s0 += __shfl_xor_sync(0xffffffffu, s0, off);
+              s1 += __shfl_xor_sync(0xffffffffu, s1, off);
+            }
+            if (ok)
+  #pragma unroll 1
+              for (int cc = lane; cc < G; cc += 32) put_pair(a.inbox + (unsigned)cc * (unsigned)a.pstride + 2 * o, tag, s0, s1);
+          }
+        }
+        // hop 2: this CTA's copy of the reduced payload, into shared memory: g
+        // as R x J_n, each block C_{r r'} unpacked to full rows of stride
+        // pad4(J_n)
+        {
+          const unsigned long long* mine = a.inbox + (unsigned)c * (unsigned)a.pstride;
+  #pragma unroll 1
+          for (int o2 = tid; o2 < (P >> 1); o2 += T) {
+            ulonglong2 w1[1];
+            const unsigned long long* p1[1] = {mine + 2 * o2};
+            w1[0] = get_pair(p1[0]);
+            if (ok) ok = wait_pairs<1>(p1, w1, tag, a);
+  #pragma unroll
+            for (int u = 0; u < 2; ++u) {
+              const int o = 2 * o2 + u;
+              const float v = val_of(u == 0 ? w1[0].x : w1[0].y);
+              if (o < Kx) {
+                const int r = fdiv(o >> 2, f_na4), j = o - r * Jq;
+                if (j < Jn) redsm[r * Jn + j] = v;
+              } else {
+                const int t = o - Kx;
+                const int q = fdiv(t >> 2, f_nq4), jj = t - q * tJp;
+                if (jj < tJ) {
+                  const int ja = trij[jj] & 0xff, jb = trij[jj] >> 8;
+                  float* blk = redsm + Kq + q * Jn * Jq;
+                  blk[ja * Jq + jb] = v;
+                  blk[jb * Jq + ja] = v;
+                }
               }
             }
           }
+          // zero padding columns of the unpacked blocks
+          if (Jq > Jn)
+  #pragma unroll 1
+            for (int i = tid; i < npairs * Jn; i += T)
+  #pragma unroll 1
+              for (int j = Jn; j < Jq; ++j) redsm[Kq + i * Jq + j] = 0.f;
         }
-        // zero padding columns of the unpacked blocks
-        if (Jq > Jn)
-#pragma unroll 1
-          for (int i = tid; i < npairs * Jn; i += T)
-#pragma unroll 1
-            for (int j = Jn; j < Jq; ++j) redsm[Kq + i * Jq + j] = 0.f;
-      }
-      if (!__syncthreads_and(ok)) return;
-      // Cyclic SGD over the columns of B(n) (lines 7-14) as a block forward
-      // substitution: warp w keeps V_w (lane j) and V_{w+16}; at step r the
-      // owner of column r moves it, and every later V_r'' gains C_{r'' r}
-      // Delta_r (Delta double-buffered by step parity, one named barrier per
-      // step).
-      {
-        const int nrw = R < nwarps ? R : nwarps;
-        if (warp < nrw) {
-          float* Bn = Bsm + mBoff[n];
-          const float* Cv = redsm + Kq;
-          const bool lj = lane < Jn;
-          const int ra = warp, rb = warp + nwarps;
-          float Va = (lj && ra < R) ? redsm[ra * Jn + lane] : 0.f;
-          float Vb = (lj && rb < R) ? redsm[rb * Jn + lane] : 0.f;
-          const float boa = (lj && ra < R) ? Bn[lane * R + ra] : 0.f;
-          const float bob = (lj && rb < R) ? Bn[lane * R + rb] : 0.f;
-          const int nv4 = Jq >> 2;
-#pragma unroll 1
-          for (int r = 0; r < R; ++r) {
-            float* D = Dsm + (r & 1) * 32;
-            if ((ra == r || rb == r) && lane < Jq) {
-              float d = 0.f;
-              if (lj) {
-                const float V = ra == r ? Va : Vb;
-                const float bo = ra == r ? boa : bob;
-                const float bn = bo - a.lr_b * (V * invm + a.lam_b * bo);
-                d = bn - bo;
-                Bn[lane * R + r] = bn;
-                if (probe && c == 0 && a.probeV) a.probeV[((unsigned)n * R + r) * kMaxJ + lane] = V;
+        if (!__syncthreads_and(ok)) return;
+        // Cyclic SGD over the columns of B(n) (lines 7-14) as a block forward
+        // substitution: warp w keeps V_w (lane j) and V_{w+16}; at step r the
+        // owner of column r moves it, and every later V_r'' gains C_{r'' r}
+        // Delta_r (Delta double-buffered by step parity, one named barrier per
+        // step).
+        {
+          const int nrw = R < nwarps ? R : nwarps;
+          if (warp < nrw) {
+            float* Bn = Bsm + mBoff[n];
+            const float* Cv = redsm + Kq;
+            const bool lj = lane < Jn;
+            const int ra = warp, rb = warp + nwarps;
+            float Va = (lj && ra < R) ? redsm[ra * Jn + lane] : 0.f;
+            float Vb = (lj && rb < R) ? redsm[rb * Jn + lane] : 0.f;
+            const float boa = (lj && ra < R) ? Bn[lane * R + ra] : 0.f;
+            const float bob = (lj && rb < R) ? Bn[lane * R + rb] : 0.f;
+            const int nv4 = Jq >> 2;
+  #pragma unroll 1
+            for (int r = 0; r < R; ++r) {
+              float* D = Dsm + (r & 1) * 32;
+              if ((ra == r || rb == r) && lane < Jq) {
+                float d = 0.f;
+                if (lj) {
+                  const float V = ra == r ? Va : Vb;
+                  const float bo = ra == r ? boa : bob;
+                  const float bn = bo - a.lr_b * (V * invm + a.lam_b * bo);
+                  d = bn - bo;
+                  Bn[lane * R + r] = bn;
+                  if (probe && c == 0 && a.probeV) a.probeV[((unsigned)n * R + r) * kMaxJ + lane] = V;
+                }
+                D[lane] = d;
               }
-              D[lane] = d;
-            }
-            named_sync(nrw * 32);
-            if (lj) {
-              const float4* D4 = reinterpret_cast<const float4*>(D);
-#pragma unroll 1
-              for (int h = 0; h < 2; ++h) {
-                const int r2 = h == 0 ? ra : rb;
-                if (r2 > r && r2 < R) {
-                  const float4* C4 = reinterpret_cast<const float4*>(Cv + ((r2 * (r2 - 1) / 2 + r) * Jn + lane) * Jq);
-                  float s0 = 0.f, s1 = 0.f;
-#pragma unroll 1
-                  for (int v = 0; v < nv4; ++v) {
-                    const float4 cv = C4[v], dv = D4[v];
-                    s0 = fmaf(cv.x, dv.x, s0);
-                    s1 = fmaf(cv.y, dv.y, s1);
-                    s0 = fmaf(cv.z, dv.z, s0);
-                    s1 = fmaf(cv.w, dv.w, s1);
+              named_sync(nrw * 32);
+              if (lj) {
+                const float4* D4 = reinterpret_cast<const float4*>(D);
+  #pragma unroll 1
+                for (int h = 0; h < 2; ++h) {
+                  const int r2 = h == 0 ? ra : rb;
+                  if (r2 > r && r2 < R) {
+                    const float4* C4 = reinterpret_cast<const float4*>(Cv + ((r2 * (r2 - 1) / 2 + r) * Jn + lane) * Jq);
+                    float s0 = 0.f, s1 = 0.f;
+  #pragma unroll 1
+                    for (int v = 0; v < nv4; ++v) {
+                      const float4 cv = C4[v], dv = D4[v];
+                      s0 = fmaf(cv.x, dv.x, s0);
+                      s1 = fmaf(cv.y, dv.y, s1);
+                      s0 = fmaf(cv.z, dv.z, s0);
+                      s1 = fmaf(cv.w, dv.w, s1);
+                    }
+                    if (h == 0) Va += s0 + s1;
+                    else Vb += s0 + s1;
                   }
-                  if (h == 0) Va += s0 + s1;
-                  else Vb += s0 + s1;
                 }
               }
             }
           }
         }
-      }
-      __syncthreads();
-      // p[s][n][r] with the new B(n): warp per sample, lane r
-#pragma unroll 1
-      for (int s = warp; s < cnt; s += nwarps)
-        if (lane < R) {
-          const float* ar = rows + s * sumJ + mJoff[n];
-          const float* br = Bsm + mBoff[n] + lane;
-          float acc0 = 0.f, acc1 = 0.f;
-          int j = 0;
-#pragma unroll 1
-          for (; j + 1 < Jn; j += 2) {
-            acc0 = fmaf(ar[j], br[j * R], acc0);
-            acc1 = fmaf(ar[j + 1], br[(j + 1) * R], acc1);
+        __syncthreads();
+        // p[s][n][r] with the new B(n): warp per sample, lane r
+  #pragma unroll 1
+        for (int s = warp; s < cnt; s += nwarps)
+          if (lane < R) {
+            const float* ar = rows + s * sumJ + mJoff[n];
+            const float* br = Bsm + mBoff[n] + lane;
+            float acc0 = 0.f, acc1 = 0.f;
+            int j = 0;
+  #pragma unroll 1
+            for (; j + 1 < Jn; j += 2) {
+              acc0 = fmaf(ar[j], br[j * R], acc0);
+              acc1 = fmaf(ar[j + 1], br[(j + 1) * R], acc1);
+            }
+            if (j < Jn) acc0 = fmaf(ar[j], br[j * R], acc0);
+            pbuf[s * NR + n * R + lane] = acc0 + acc1;
           }
-          if (j < Jn) acc0 = fmaf(ar[j], br[j * R], acc0);
-          pbuf[s * NR + n * R + lane] = acc0 + acc1;
-        }
-      __syncthreads();
+        __syncthreads();
+      }
     }
 
     // ------------------------------------------------------------------
@@ -1022,7 +1025,7 @@ k_epoch(EpochArgs a) {
           // G_(n) for the contraction, [j][c]: warp per j, lanes over c;
           // column c sits at the offset of its other-mode digits in G-hat
           const int KP = BF ? bf16_row_stride(Pn) : Pp;
-          const int Jrows = BF ? round_up(Jn, 16) : Jn;
+          const int Jrows = a.contraction == 1 ? 0 : (BF ? round_up(Jn, 16) : Jn);
 #pragma unroll 1
           for (int j = warp; j < Jrows; j += nwarps)
 #pragma unroll 1
@@ -1070,8 +1073,45 @@ k_epoch(EpochArgs a) {
       if (!__syncthreads_and(ok)) return;
       // Kronecker rows S_s (Eq. 10), warp per sample, lanes over columns
       const int nm1 = N - 1;
+      const bool kru = a.contraction == 1;
       const bool full_s = BF || cnt * Pp <= L.sfloats;
-      if (BF) {
+      if (kru) {
+        // Kruskal form of the same contraction (Eq. 4 in Eq. 11):
+        // E_s = G_(n) S_s^T = B(n) w_s, w_s[r] = prod_{k != n} <a_k(s), b(k)_r>;
+        // warp per sample, lane r forms w_r, lane j forms E_j, then the
+        // residual e_s = a_n . E_s - x_s (warp sum) and the contributions
+#pragma unroll 1
+        for (int s = warp; s < cnt; s += nwarps) {
+          const float* rs = rows + s * sumJ;
+          float w = 0.f;
+          if (lane < R) {
+            w = 1.f;
+#pragma unroll 1
+            for (int k = 0; k < N; ++k) {
+              if (k == n) continue;
+              const float* ak = rs + mJoff[k];
+              const float* bk = Bsm + mBoff[k] + lane;
+              float d0 = 0.f, d1 = 0.f;
+              int j = 0;
+#pragma unroll 1
+              for (; j + 1 < mJ[k]; j += 2) {
+                d0 = fmaf(ak[j], bk[j * R], d0);
+                d1 = fmaf(ak[j + 1], bk[(j + 1) * R], d1);
+              }
+              if (j < mJ[k]) d0 = fmaf(ak[j], bk[j * R], d0);
+              w *= d0 + d1;
+            }
+          }
+          float E = 0.f;
+          const float* bn = Bsm + mBoff[n] + (lane < Jn ? lane : 0) * R;
+#pragma unroll 1
+          for (int r = 0; r < R; ++r) E = fmaf(bn[r], __shfl_sync(0xffffffffu, w, r), E);
+          float part = lane < Jn ? rs[mJoff[n] + lane] * E : 0.f;
+#pragma unroll
+          for (int off = 16; off > 0; off >>= 1) part += __shfl_xor_sync(0xffffffffu, part, off);
+          if (lane < Jn) qbuf[s * Jmax + lane] = (part - fx[s]) * E;
+        }
+      } else if (BF) {
         const int KP = bf16_row_stride(Pn);
 #pragma unroll 1
         for (int s = warp; s < round_up(cnt, 16); s += nwarps) {
@@ -1090,7 +1130,9 @@ k_epoch(EpochArgs a) {
       }
       __syncthreads();
       const int nheads = s_nheads;
-      if (BF) {
+      if (kru) {
+        // E_s and the contributions were formed above
+      } else if (BF) {
         // Tensor-core contraction: E (samples x J_n) = S (samples x P_n) .
         // G_(n)^T with BF16 operands and FP32 accumulation, mma.sync
         // m16n8k16 tiles (one warp per 16 x 8 output tile, full K).

@@ -129,6 +129,7 @@ struct EpochArgs {
   int64_t b0, b1;        // minibatch range
   float lr_a, lr_b, lam_a, lam_b;
   int norm_mode;
+  int contraction;       // 0 Kronecker rows x unfolded core; 1 Kruskal form E = B(n) w
   int chunk_max;
   // cross-CTA exchange words: (sequence tag << 32) | float bits
   uint32_t tag_base;           // tag of (minibatch b, mode n) = tag_base + 8 (b - b0) + n

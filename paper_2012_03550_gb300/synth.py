@@ -310,6 +310,19 @@ def config3(scale: float = 1.0, seed: int = 0) -> Workload:
                     8192, 1e-3, 1e-3, 10)
 
 
+# The paper's parameter study varies the model ranks on a fixed dataset: J_n
+# from 5 to 25 and R_core from 10 to 25.  Sweep points: J_1 in {5..25} with
+# J_2 = J_3 = 5 and R_core = 5, then R_core in {10..25} with J = (5, 5, 5).
+RANK_SWEEP = [((J, 5, 5), 5) for J in (5, 10, 15, 20, 25)] + [((5, 5, 5), R) for R in (10, 15, 20, 25)]
+
+
+def ranksweep(scale: float = 0.05, seed: int = 0):
+    """The rank-sweep workload: one rating tensor with config 2's shape and
+    distributions at `scale` (the data stay fixed across the sweep), and the
+    (ranks, R_core) points of RANK_SWEEP.  M = 4096, lr = lambda = 1e-3."""
+    return config2(scale=scale, seed=seed), list(RANK_SWEEP)
+
+
 def config4_specs(count: int = 256, seed: int = 0, nnz_scale: float = 1.0):
     """Shapes of the batched workload: `count` independent 3-order tensors with
     mode sizes lognormal(ln 7000, 1) clipped to [1e3, 5e4], nonzeros

@@ -134,7 +134,8 @@ def test_create_rejects_out_of_range_index(B):
 # One minibatch: gradients and parameters
 # ---------------------------------------------------------------------------
 
-def _step_case(B, synth, tensor, ranks, R, M, batch, lr=(0.3, 0.2), lam=(0.01, 0.02), norm_mode=0, init="normal"):
+def _step_case(B, synth, tensor, ranks, R, M, batch, lr=(0.3, 0.2), lam=(0.01, 0.02), norm_mode=0, init="normal",
+               **opts):
     """Probe minibatch `batch` of epoch 0 from one state on both sides.  For
     batch > 0 the state is the oracle's FP64 state after batches [0, batch),
     rounded to FP32 and given to both sides (a one-step comparison)."""
@@ -147,7 +148,7 @@ def _step_case(B, synth, tensor, ranks, R, M, batch, lr=(0.3, 0.2), lam=(0.01, 0
         A0 = [a.astype(np.float32) for a in adv.A]
         B0 = [b.astype(np.float32) for b in adv.B]
     ref = O.Model(tensor.shape, ranks, R, A0, B0)
-    with _gpu(B, tensor.shape, ranks, R, c, v, A0, B0, norm_mode=norm_mode) as g:
+    with _gpu(B, tensor.shape, ranks, R, c, v, A0, B0, norm_mode=norm_mode, **opts) as g:
         sched = O.perm_range(c.shape[0], 2, 0, batch * M, min(M, c.shape[0] - batch * M))
         pr = g.batches(lr[0], lr[1], lam[0], lam[1], M, batch, batch + 1, probe=True)
         V, F, nseg = ref.step(c[sched], v[sched], lr[0], lr[1], lam[0], lam[1], norm_mode=norm_mode, probe=True)
@@ -213,6 +214,102 @@ def test_step_gradients_row_count_normaliser(B, synth, cfg1, norm_mode):
 def test_step_gradients_edge_shapes(B, synth, shape, ranks, R, M, nnz):
     t = synth.make_tensor(shape, nnz, [("uniform",)] * len(shape), ranks, 0.1, 0.0, seed=17)
     _step_case(B, synth, t, ranks, R, M, batch=0)
+
+
+# The rank-sweep extremes of the paper's parameter study: a wide mode (J_1 =
+# 25, the largest Kronecker rows and Gram blocks) and a wide core (R_core =
+# 25, 300 Gram blocks and 25 cyclic steps per mode).
+@pytest.mark.parametrize("ranks,R", [((25, 5, 5), 5), ((5, 5, 5), 25), ((15, 5, 5), 5)])
+def test_step_gradients_rank_sweep_points(B, synth, ranks, R):
+    t = synth.make_tensor((300, 200, 100), 6000, [("zipf", 1.1), ("zipf", 1.3), ("uniform",)], (5, 5, 5),
+                          0.05, 0.0, seed=23)
+    _step_case(B, synth, t, ranks, R, 2048, batch=1, lr=(0.05, 0.05))
+
+
+def test_epoch_rmse_parity_rank_sweep_wide_core(B, synth):
+    t = synth.make_tensor((300, 200, 100), 6000, [("zipf", 1.1), ("zipf", 1.3), ("uniform",)], (5, 5, 5),
+                          0.05, 0.1, seed=29)
+    ranks, R, M, lr, lam = (5, 5, 5), 25, 512, 0.01, 1e-3
+    c, v = t.split("train")
+    tc, tv = t.split("test")
+    A0, B0 = synth.init_params(t.shape, ranks, R, mode="normal", seed=1)
+    ref = O.Model(t.shape, ranks, R, A0, B0)
+    worst = 0.0
+    with _gpu(B, t.shape, ranks, R, c, v, A0, B0) as g:
+        for ep in range(3):
+            g.epoch(lr, lr, lam, lam, M)
+            ref.epoch(c, v, M, 2, ep, lr, lr, lam, lam)
+            for cc, vv in ((c, v), (tc, tv)):
+                r_g, m_g = g.rmse(cc, vv)
+                r_o, m_o = ref.rmse_mae(cc, vv)
+                worst = max(worst, abs(r_g - r_o), abs(m_g - m_o))
+    assert worst <= 1e-3, worst
+
+
+# The Kruskal form of the factor-phase contraction (E_s = B(n) w_s) is the
+# same product as the Kronecker rows against the unfolded core (Eq. 4 in
+# Eq. 11), so it is held to the same bars against the same oracle.
+def test_step_gradients_kruskal_contraction_config1(B, synth, cfg1):
+    _step_case(B, synth, cfg1.tensor, cfg1.ranks, 5, 256, batch=0, contraction=1)
+
+
+def test_step_gradients_kruskal_contraction_rating_zipf(B, synth):
+    w = synth.config2(scale=0.004)
+    _step_case(B, synth, w.tensor, w.ranks, 5, 4096, batch=1, init="rating", lr=(0.05, 0.05), contraction=1)
+
+
+def test_step_gradients_kruskal_contraction_4order_and_edge(B, synth):
+    w = synth.config3(scale=0.004)
+    _step_case(B, synth, w.tensor, w.ranks, 5, 8192, batch=0, contraction=1)
+    t = synth.make_tensor((30, 20, 10, 8, 6), 2000, [("uniform",)] * 5, (2, 3, 2, 2, 3), 0.1, 0.0, seed=17)
+    _step_case(B, synth, t, (2, 3, 2, 2, 3), 3, 64, batch=0, contraction=1)
+
+
+def test_epoch_rmse_parity_kruskal_contraction(B, synth, cfg1):
+    c, v = cfg1.tensor.split("train")
+    tc, tv = cfg1.tensor.split("test")
+    A0, B0 = synth.init_params(cfg1.tensor.shape, cfg1.ranks, 5, mode="normal", seed=1)
+    ref = O.Model(cfg1.tensor.shape, cfg1.ranks, 5, A0, B0)
+    worst = 0.0
+    with _gpu(B, cfg1.tensor.shape, cfg1.ranks, 5, c, v, A0, B0, contraction=1) as g:
+        for ep in range(4):
+            g.epoch(0.5, 0.5, cfg1.lam, cfg1.lam, cfg1.minibatch)
+            ref.epoch(c, v, cfg1.minibatch, 2, ep, 0.5, 0.5, cfg1.lam, cfg1.lam)
+            r_g, m_g = g.rmse(tc, tv)
+            r_o, m_o = ref.rmse_mae(tc, tv)
+            worst = max(worst, abs(r_g - r_o), abs(m_g - m_o))
+    assert worst <= 1e-3, worst
+
+
+# The paper's own setting (Sec. 5.1, 5.3): initialisation N(0.5, 0.1^2),
+# gamma_A = 0.002, gamma_B = 0.001, lambda_A = lambda_B = 0.01, one sample per
+# step (M = 1), the row's sample count as normaliser, and B updated only in
+# the first and the last epoch (lr_b = 0 in between leaves B untouched).
+def test_paper_setting_m1_core_schedule(B, synth):
+    t = synth.make_tensor((60, 50, 40), 1500, [("uniform",)] * 3, (5, 5, 5), 0.05, 0.1, seed=31)
+    ranks, R = (5, 5, 5), 5
+    c, v = t.split("train")
+    tc, tv = t.split("test")
+    A0, B0 = synth.init_params(t.shape, ranks, R, mode="paper", seed=1)
+    ref = O.Model(t.shape, ranks, R, A0, B0)
+    epochs, ga, gb, lam = 4, 0.002, 0.001, 0.01
+    worst = 0.0
+    with _gpu(B, t.shape, ranks, R, c, v, A0, B0, norm_mode=1) as g:
+        for ep in range(epochs):
+            lr_b = gb if ep in (0, epochs - 1) else 0.0
+            _, Bb, _, _ = g.get_params()
+            g.epoch(ga, lr_b, lam, lam, 1)
+            ref.epoch(c, v, 1, 2, ep, ga, lr_b, lam, lam, 1)
+            Ag, Ba, _, _ = g.get_params()
+            if lr_b == 0.0:
+                for n in range(3):
+                    assert np.array_equal(Ba[n], Bb[n])   # B untouched, bit for bit
+            r_g, m_g = g.rmse(tc, tv)
+            r_o, m_o = ref.rmse_mae(tc, tv)
+            worst = max(worst, abs(r_g - r_o), abs(m_g - m_o))
+            for n in range(3):
+                assert float(np.abs(Ag[n] - ref.A[n]).max()) <= 1e-4 * float(np.abs(ref.A[n]).max())
+    assert worst <= 1e-3, worst
 
 
 # ---------------------------------------------------------------------------
