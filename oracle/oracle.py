@@ -76,6 +76,12 @@ def _declare(L):
     L.orc_epoch.restype = _int
     L.orc_epoch.argtypes = common + [_P, _i64, _P, _P, _i64, _u64, _u64, _i64, _i64,
                                      _dbl, _dbl, _dbl, _dbl, _int]
+    L.orc_step_momentum.restype = _int
+    L.orc_step_momentum.argtypes = common + [_P, _i64, _P, _P, _dbl, _dbl, _dbl, _dbl, _int, _int, _P, _P, _P,
+                                             _dbl, _P, _P]
+    L.orc_epoch_momentum.restype = _int
+    L.orc_epoch_momentum.argtypes = common + [_P, _i64, _P, _P, _i64, _u64, _u64, _i64, _i64,
+                                              _dbl, _dbl, _dbl, _dbl, _int, _dbl, _P, _P]
 
 
 def _ptr(a: np.ndarray):
@@ -141,7 +147,7 @@ class Model:
     """FP64 SGD_Tucker state: A_n (I_n x J_n), B_n (J_n x R), G-hat (prod J)."""
 
     def __init__(self, shape: Sequence[int], ranks: Sequence[int], r_core: int,
-                 A: Sequence[np.ndarray], B: Sequence[np.ndarray]):
+                 A: Sequence[np.ndarray], B: Sequence[np.ndarray], momentum: float = 0.0):
         self.N = len(shape)
         self.shape = np.ascontiguousarray(shape, dtype=np.int64)
         self.ranks = np.ascontiguousarray(ranks, dtype=np.int32)
@@ -152,9 +158,21 @@ class Model:
             assert self.A[n].shape == (int(shape[n]), int(ranks[n]))
             assert self.B[n].shape == (int(ranks[n]), self.R)
         self.G = np.zeros(int(np.prod(self.ranks.astype(np.int64))), dtype=np.float64)
+        # heavy-ball momentum: velocities of the factor rows and Kruskal columns
+        self.mu = float(momentum)
+        self.VA = [np.zeros_like(a) for a in self.A] if self.mu != 0.0 else None
+        self.VB = [np.zeros_like(b) for b in self.B] if self.mu != 0.0 else None
 
     def copy(self) -> "Model":
-        return Model(self.shape, self.ranks, self.R, self.A, self.B)
+        return Model(self.shape, self.ranks, self.R, self.A, self.B, self.mu)
+
+    def _vel(self):
+        if self.VA is None:
+            return [0.0, None, None]
+        VAp = (ctypes.c_void_p * self.N)(*[a.ctypes.data for a in self.VA])
+        VBp = (ctypes.c_void_p * self.N)(*[b.ctypes.data for b in self.VB])
+        self._keepv = (VAp, VBp)
+        return [self.mu, ctypes.cast(VAp, ctypes.c_void_p), ctypes.cast(VBp, ctypes.c_void_p)]
 
     def _args(self):
         Ap = (ctypes.c_void_p * self.N)(*[a.ctypes.data for a in self.A])
@@ -219,9 +237,9 @@ class Model:
             F = np.zeros((self.N, m, jmax), dtype=np.float64)
             nseg = np.zeros(self.N, dtype=np.int64)
             pV, pF, pS = _ptr(V), _ptr(F), _ptr(nseg)
-        _check(lib().orc_step(*self._args(), _ptr(self.G), m, _ptr(coords), _ptr(values),
-                              float(lr_a), float(lr_b), float(lam_a), float(lam_b), int(norm_mode),
-                              int(bool(literal)), pV, pF, pS))
+        _check(lib().orc_step_momentum(*self._args(), _ptr(self.G), m, _ptr(coords), _ptr(values),
+                                       float(lr_a), float(lr_b), float(lam_a), float(lam_b), int(norm_mode),
+                                       int(bool(literal)), pV, pF, pS, *self._vel()))
         if probe:
             return V, F, nseg
         return None
@@ -233,7 +251,8 @@ class Model:
         n = coords.shape[0]
         if batch_end is None:
             batch_end = (n + M - 1) // M
-        _check(lib().orc_epoch(*self._args(), _ptr(self.G), n, _ptr(coords), _ptr(values), int(M),
-                               int(seed), int(epoch), int(batch_begin), int(batch_end),
-                               float(lr_a), float(lr_b), float(lam_a), float(lam_b), int(norm_mode)))
+        _check(lib().orc_epoch_momentum(*self._args(), _ptr(self.G), n, _ptr(coords), _ptr(values), int(M),
+                                        int(seed), int(epoch), int(batch_begin), int(batch_end),
+                                        float(lr_a), float(lr_b), float(lam_a), float(lam_b), int(norm_mode),
+                                        *self._vel()))
         self.build_core()

@@ -372,6 +372,17 @@ static double orc_sgd(double w, double grad, double M, double lambda, double gam
     return w - gamma * (grad / M + lambda * w);
 }
 
+/* Heavy-ball momentum (Polyak 1964), the accelerated SGD the paper names as
+ * future work (Sec. 6): with g = grad / M + lambda w the velocity becomes
+ * v <- mu v + g and the parameter w <- w - gamma v.  mu = 0 gives orc_sgd. */
+static double orc_sgd_momentum(double w, double *v, double grad, double M, double lambda, double gamma,
+                               double mu)
+{
+    const double g = grad / M + lambda * w;
+    *v = mu * (*v) + g;
+    return w - gamma * (*v);
+}
+
 /* ------------------------------------------------------------------------ */
 /* Factor phase, Algorithm 1 lines 17-25 for one mode n and one row i_n      */
 /* whose samples are sample_ids[0..cnt).                                     */
@@ -546,10 +557,33 @@ int orc_factor_gradient(int N, const int64_t *I, const int32_t *J, int R, double
  * i_n, the line-22 vector F (layout [n][u][Jmax], u < m), with the number of
  * segments per mode in probe_nseg[n].
  */
+int orc_step_momentum(int N, const int64_t *I, const int32_t *J, int R, double **A, double **B, double *G,
+                      int64_t m, const int32_t *coords, const float *values,
+                      double gamma_a, double gamma_b, double lambda_a, double lambda_b,
+                      int norm_mode, int literal, double *probe_V, double *probe_F, int64_t *probe_nseg,
+                      double mu, double **VA, double **VB);
+
 int orc_step(int N, const int64_t *I, const int32_t *J, int R, double **A, double **B, double *G,
              int64_t m, const int32_t *coords, const float *values,
              double gamma_a, double gamma_b, double lambda_a, double lambda_b,
              int norm_mode, int literal, double *probe_V, double *probe_F, int64_t *probe_nseg)
+{
+    return orc_step_momentum(N, I, J, R, A, B, G, m, coords, values, gamma_a, gamma_b, lambda_a, lambda_b,
+                             norm_mode, literal, probe_V, probe_F, probe_nseg, 0.0, NULL, NULL);
+}
+
+/*
+ * orc_step with heavy-ball momentum: VA[n] (I_n x J_n) and VB[n] (J_n x R)
+ * hold the velocities of the factor rows and of the Kruskal columns; every
+ * update of Algorithm 1 (lines 14 and 23) goes through orc_sgd_momentum.  A row
+ * untouched by the minibatch keeps its velocity (as it keeps its value).
+ * VA = VB = NULL gives plain SGD.
+ */
+int orc_step_momentum(int N, const int64_t *I, const int32_t *J, int R, double **A, double **B, double *G,
+                      int64_t m, const int32_t *coords, const float *values,
+                      double gamma_a, double gamma_b, double lambda_a, double lambda_b,
+                      int norm_mode, int literal, double *probe_V, double *probe_F, int64_t *probe_nseg,
+                      double mu, double **VA, double **VB)
 {
     orc_model md;
     int rc = orc_setup(&md, N, I, J, R, A, B, G);
@@ -581,7 +615,10 @@ int orc_step(int N, const int64_t *I, const int32_t *J, int R, double **A, doubl
                 for (int j = 0; j < Jn; ++j) probe_V[((int64_t)n * R + r) * Jmax + j] = V[j];
             for (int j = 0; j < Jn; ++j) {                            /* line 14 */
                 double *b = &md.B[n][(int64_t)j * R + r];
-                *b = orc_sgd(*b, V[j], (double)m, lambda_b, gamma_b);
+                if (VB)
+                    *b = orc_sgd_momentum(*b, &VB[n][(int64_t)j * R + r], V[j], (double)m, lambda_b, gamma_b, mu);
+                else
+                    *b = orc_sgd(*b, V[j], (double)m, lambda_b, gamma_b);
             }
         }
     }
@@ -601,9 +638,14 @@ int orc_step(int N, const int64_t *I, const int32_t *J, int R, double **A, doubl
             if (probe_F)
                 for (int j = 0; j < Jn; ++j) probe_F[((int64_t)n * m + u) * Jmax + j] = F[j];
             double denom = norm_mode == 1 ? (double)cnt : (double)m;
-            double *a = md.A[n] + (int64_t)coords[(int64_t)ids[0] * N + n] * Jn;
-            for (int j = 0; j < Jn; ++j)                              /* line 23 */
-                a[j] = orc_sgd(a[j], F[j], denom, lambda_a, gamma_a);
+            const int64_t row = coords[(int64_t)ids[0] * N + n];
+            double *a = md.A[n] + row * Jn;
+            for (int j = 0; j < Jn; ++j) {                            /* line 23 */
+                if (VA)
+                    a[j] = orc_sgd_momentum(a[j], &VA[n][row * Jn + j], F[j], denom, lambda_a, gamma_a, mu);
+                else
+                    a[j] = orc_sgd(a[j], F[j], denom, lambda_a, gamma_a);
+            }
         }
     }
 done:
@@ -616,10 +658,27 @@ done:
  * training entries (coords n_train x N, values n_train): minibatch b is the
  * entries pi_e(t), t in [bM, min(bM+M, n_train)).
  */
+int orc_epoch_momentum(int N, const int64_t *I, const int32_t *J, int R, double **A, double **B, double *G,
+                       int64_t n_train, const int32_t *coords, const float *values, int64_t M,
+                       uint64_t seed, uint64_t epoch, int64_t batch_begin, int64_t batch_end,
+                       double gamma_a, double gamma_b, double lambda_a, double lambda_b, int norm_mode,
+                       double mu, double **VA, double **VB);
+
 int orc_epoch(int N, const int64_t *I, const int32_t *J, int R, double **A, double **B, double *G,
               int64_t n_train, const int32_t *coords, const float *values, int64_t M,
               uint64_t seed, uint64_t epoch, int64_t batch_begin, int64_t batch_end,
               double gamma_a, double gamma_b, double lambda_a, double lambda_b, int norm_mode)
+{
+    return orc_epoch_momentum(N, I, J, R, A, B, G, n_train, coords, values, M, seed, epoch, batch_begin,
+                              batch_end, gamma_a, gamma_b, lambda_a, lambda_b, norm_mode, 0.0, NULL, NULL);
+}
+
+/* orc_epoch with heavy-ball momentum (velocities VA, VB as in orc_step_momentum). */
+int orc_epoch_momentum(int N, const int64_t *I, const int32_t *J, int R, double **A, double **B, double *G,
+                       int64_t n_train, const int32_t *coords, const float *values, int64_t M,
+                       uint64_t seed, uint64_t epoch, int64_t batch_begin, int64_t batch_end,
+                       double gamma_a, double gamma_b, double lambda_a, double lambda_b, int norm_mode,
+                       double mu, double **VA, double **VB)
 {
     if (M < 1 || n_train < 1 || N < 1 || N > ORC_MAXN) return ORC_EINVAL;
     int64_t nb = (n_train + M - 1) / M;
@@ -641,8 +700,8 @@ int orc_epoch(int N, const int64_t *I, const int32_t *J, int R, double **A, doub
             for (int n = 0; n < N; ++n) bc[q * N + n] = coords[(int64_t)y * N + n];
             bv[q] = values[y];
         }
-        rc = orc_step(N, I, J, R, A, B, G, m, bc, bv, gamma_a, gamma_b, lambda_a, lambda_b,
-                      norm_mode, 0, NULL, NULL, NULL);
+        rc = orc_step_momentum(N, I, J, R, A, B, G, m, bc, bv, gamma_a, gamma_b, lambda_a, lambda_b,
+                               norm_mode, 0, NULL, NULL, NULL, mu, VA, VB);
     }
     free(bc); free(bv);
     return rc;

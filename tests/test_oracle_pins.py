@@ -274,6 +274,67 @@ def test_matrix_factorisation_special_case():
     np.testing.assert_array_equal(md.B[0], np.eye(J))
 
 
+def test_momentum_matrix_factorisation_two_steps():
+    # Heavy-ball momentum on the N = 2, B = I case: textbook alternating
+    # matrix-factorisation SGD with a velocity per row (v <- mu v + g,
+    # w <- w - gamma v, g the regularised gradient), two minibatches.
+    J, mu = 3, 0.7
+    g = _rng(11)
+    U = g.standard_normal((5, J))
+    Vm = g.standard_normal((4, J))
+    md = O.Model((5, 4), (J, J), J, [U, Vm], [np.eye(J), np.eye(J)], momentum=mu)
+    batches = [(np.array([[2, 1], [2, 3], [0, 1]], dtype=np.int32), np.array([0.7, -1.2, 0.4], dtype=np.float32)),
+               (np.array([[2, 0], [1, 1], [0, 1], [4, 3]], dtype=np.int32),
+                np.array([0.1, 0.9, -0.5, 0.3], dtype=np.float32))]
+    gam, lam = 0.3, 0.05
+    u, v = U.copy(), Vm.copy()
+    vu, vv = np.zeros_like(u), np.zeros_like(v)
+    for coords, x in batches:
+        md.step(coords, x, gam, 0.0, lam, 0.0)
+        M = coords.shape[0]
+        for i in np.unique(coords[:, 0]):
+            grad = np.zeros(J)
+            for s in np.where(coords[:, 0] == i)[0]:
+                k = coords[s, 1]
+                grad += (u[i] @ v[k] - float(x[s])) * v[k]
+            vu[i] = mu * vu[i] + (grad / M + lam * u[i])
+            u[i] = u[i] - gam * vu[i]
+        v_new = v.copy()
+        for k in np.unique(coords[:, 1]):
+            grad = np.zeros(J)
+            for s in np.where(coords[:, 1] == k)[0]:
+                i = coords[s, 0]
+                grad += (u[i] @ v[k] - float(x[s])) * u[i]
+            vv[k] = mu * vv[k] + (grad / M + lam * v[k])
+            v_new[k] = v[k] - gam * vv[k]
+        v = v_new
+    np.testing.assert_allclose(md.A[0], u, rtol=1e-13, atol=1e-14)
+    np.testing.assert_allclose(md.A[1], v, rtol=1e-13, atol=1e-14)
+    np.testing.assert_allclose(md.VA[0], vu, rtol=1e-13, atol=1e-14)
+
+
+def test_momentum_first_step_is_plain_sgd_and_zero_momentum_is_sgd():
+    # The velocity starts at zero, so the first step with any mu is the plain
+    # step; with mu = 0 every step is the plain step.
+    shape, ranks, R = (8, 7, 6), (3, 2, 3), 2
+    coords, x = _random_batch(shape, 40, seed=57)
+    base = _random_model(shape, ranks, R, seed=58, scale=0.5)
+    plain = O.Model(shape, ranks, R, base.A, base.B)
+    mom = O.Model(shape, ranks, R, base.A, base.B, momentum=0.9)
+    zero = O.Model(shape, ranks, R, base.A, base.B, momentum=0.0)
+    for md in (plain, mom, zero):
+        md.step(coords, x, 0.1, 0.05, 0.01, 0.02)
+    for n in range(3):
+        np.testing.assert_array_equal(mom.A[n], plain.A[n])
+        np.testing.assert_array_equal(mom.B[n], plain.B[n])
+    coords2, x2 = _random_batch(shape, 40, seed=59)
+    for md in (plain, mom, zero):
+        md.step(coords2, x2, 0.1, 0.05, 0.01, 0.02)
+    for n in range(3):
+        np.testing.assert_array_equal(zero.A[n], plain.A[n])
+        assert not np.array_equal(mom.A[n], plain.A[n])
+
+
 # ---------------------------------------------------------------------------
 # Descent (Theorem 3): each block step is a small gradient step on a convex
 # quadratic, so the sampled objective decreases.
