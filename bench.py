@@ -53,6 +53,7 @@ def _args():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-bf16", action="store_true")
     p.add_argument("--no-kruskal", action="store_true")
+    p.add_argument("--no-momentum", action="store_true")
     p.add_argument("--sweep", action="store_true",
                    help="rank sweep of the paper's parameter study instead of the default line: one JSON "
                         "line per (ranks, R_core) point on a fixed rating tensor (--scale, default 0.05)")
@@ -305,38 +306,47 @@ def run_gpu(a):
                 "bytes_per_nnz": _bytes_per_nnz(N, J, 2),
                 "note": "same schedule and initial state as the FP32 run; RMSE after the same epochs"}
         B.std_destroy(cx16)
+    def variant(**fields):
+        """Same workload, schedule and initial state under other options."""
+        ov = B.std_default_options()
+        ov.r_core = R
+        ov.ptr_kind = 1
+        ov.stream = stream.cuda_stream
+        for k_, v_ in fields.items():
+            setattr(ov, k_, v_)
+        cxv = B.std_create(N, t.shape, w.ranks, c.shape[0], dc, dv, ov)
+        B.std_set_params(cxv, [np.ascontiguousarray(x) for x in A0], [np.ascontiguousarray(x) for x in B0], 0)
+        for _ in range(a.warmup):
+            B.std_sgd_epoch(cxv, w.lr, w.lr, w.lam, w.lam, M)
+            B.std_rmse(cxv, tc.shape[0], dtc, dtv)
+        torch.cuda.synchronize()
+        v0 = torch.cuda.Event(enable_timing=True)
+        v1 = torch.cuda.Event(enable_timing=True)
+        v0.record(stream)
+        updv, rmv = [], None
+        for _ in range(a.steps):
+            stv = B.std_sgd_epoch(cxv, w.lr, w.lr, w.lam, w.lam, M)
+            rmv = B.std_rmse(cxv, tc.shape[0], dtc, dtv)
+            updv.append(stv["update_seconds"])
+        v1.record(stream)
+        torch.cuda.synchronize()
+        vv, ev = D.weak_scaling_rate(float(n_train * a.steps), v0.elapsed_time(v1) * 1e-3, device=dev)
+        B.std_destroy(cxv)
+        return {"value": vv, "unit": "nnz/s", "ms_per_step": 1e3 * ev / a.steps,
+                "kernel_ms": 1e3 * sum(updv) / len(updv), "speedup_vs_main": vv / value,
+                "test_rmse": rmv[0], "test_rmse_gap_vs_main": abs(rmv[0] - rm[0])}
+
     # the Kruskal form of the factor-phase contraction (E_s = B(n) w_s, the
     # same product as the Kronecker rows against the unfolded core)
     kru = None
     if not a.no_kruskal:
-        ok_ = B.std_default_options()
-        ok_.r_core = R
-        ok_.ptr_kind = 1
-        ok_.contraction = 1
-        ok_.stream = stream.cuda_stream
-        cxk = B.std_create(N, t.shape, w.ranks, c.shape[0], dc, dv, ok_)
-        B.std_set_params(cxk, [np.ascontiguousarray(x) for x in A0], [np.ascontiguousarray(x) for x in B0], 0)
-        rmk = None
-        for _ in range(a.warmup):
-            B.std_sgd_epoch(cxk, w.lr, w.lr, w.lam, w.lam, M)
-            B.std_rmse(cxk, tc.shape[0], dtc, dtv)
-        torch.cuda.synchronize()
-        k0 = torch.cuda.Event(enable_timing=True)
-        k1 = torch.cuda.Event(enable_timing=True)
-        k0.record(stream)
-        updk = []
-        for _ in range(a.steps):
-            stk = B.std_sgd_epoch(cxk, w.lr, w.lr, w.lam, w.lam, M)
-            rmk = B.std_rmse(cxk, tc.shape[0], dtc, dtv)
-            updk.append(stk["update_seconds"])
-        k1.record(stream)
-        torch.cuda.synchronize()
-        vk, ek = D.weak_scaling_rate(float(n_train * a.steps), k0.elapsed_time(k1) * 1e-3, device=dev)
-        kru = {"value": vk, "unit": "nnz/s", "ms_per_step": 1e3 * ek / a.steps,
-               "kernel_ms": 1e3 * sum(updk) / len(updk), "speedup_vs_kronecker": vk / value,
-               "test_rmse": rmk[0], "test_rmse_gap_vs_kronecker": abs(rmk[0] - rm[0]),
-               "note": "FP32; same schedule and initial state as the main line"}
-        B.std_destroy(cxk)
+        kru = variant(contraction=1)
+        kru["note"] = "FP32; same schedule and initial state as the main line"
+    # heavy-ball momentum (mu = 0.9) on the same workload
+    mom = None
+    if not a.no_momentum:
+        mom = variant(momentum=0.9)
+        mom["note"] = "FP32, mu = 0.9, same learning rate; RMSE after the same epochs"
     del dc, dv
 
     # roofline of the dominant kernel (the persistent update kernel)
@@ -415,6 +425,7 @@ def run_gpu(a):
             "e2e": e2e,
             "bf16": bf16,
             "kruskal_contraction": kru,
+            "momentum": mom,
             "gpu_launches": 4 * a.steps,
             "clocks": clocks,
             "test_rmse": rm[0] if rm else None,

@@ -82,7 +82,11 @@ typedef struct {
                              1 = the same product through the core's Kruskal form (Eq. 4):
                              E_s = B(n) w_s, w_s[r] = prod_{k != n} <a(k)_{i_k,:}, b(k)_{:,r}>,
                              O(R sum_k J_k) instead of O(J_n prod_{k != n} J_k) per sample */
-    int32_t  reserved;    /* must be 0 */
+    float    momentum;    /* heavy-ball momentum mu in [0, 1) for every update of Algorithm 1
+                             (lines 14 and 23): v <- mu v + g, w <- w - lr v with g the
+                             regularised gradient; 0 = plain SGD (default).  The accelerated SGD
+                             the paper names as future work (Sec. 6).  Velocities start at zero,
+                             are kept per parameter on the device, and std_set_params resets them */
 } std_options;
 
 /* Fill *opt with the defaults listed above. */

@@ -54,7 +54,7 @@ class std_options(ctypes.Structure):
         ("watchdog_ns", ctypes.c_uint64),
         ("hbm_budget_bytes", ctypes.c_uint64),
         ("contraction", ctypes.c_int32),
-        ("reserved", ctypes.c_int32),
+        ("momentum", ctypes.c_float),
     ]
 
 

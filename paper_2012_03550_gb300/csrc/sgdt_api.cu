@@ -47,6 +47,8 @@ struct std_ctx {
   uint32_t* coo = nullptr;
   float* A[kMaxN] = {};
   uint16_t* Ab[kMaxN] = {};   // BF16 mirrors (precision 1)
+  float* vA[kMaxN] = {};      // momentum velocities of the factor rows (momentum != 0)
+  float* vB = nullptr;        // momentum velocities of the Kruskal columns
   float* B = nullptr;
   float* core = nullptr;
   int* err = nullptr;
@@ -309,6 +311,9 @@ int run_batches(std_ctx* c, float lr_a, float lr_b, float lam_a, float lam_b, in
   a.lam_b = lam_b;
   a.norm_mode = c->opt.norm_mode;
   a.contraction = c->opt.contraction;
+  a.momentum = c->opt.momentum;
+  for (int n = 0; n < c->g.N; ++n) a.vA[n] = c->vA[n];
+  a.vB = c->vB;
   a.chunk_max = chunk;
   a.tag_base = tag_base;
   a.part = c->part;
@@ -373,7 +378,7 @@ void std_default_options(std_options* opt) {
   opt->watchdog_ns = 0;
   opt->hbm_budget_bytes = 0;
   opt->contraction = 0;
-  opt->reserved = 0;
+  opt->momentum = 0.f;
 }
 
 const char* std_last_error(void) { return g_last_error.c_str(); }
@@ -384,7 +389,9 @@ int std_destroy(std_ctx* c) {
   for (int n = 0; n < kMaxN; ++n) {
     if (c->A[n]) cudaFree(c->A[n]);
     if (c->Ab[n]) cudaFree(c->Ab[n]);
+    if (c->vA[n]) cudaFree(c->vA[n]);
   }
+  if (c->vB) cudaFree(c->vB);
   void* ptrs[] = {c->coo, c->B, c->core, c->err, c->bar, c->sched_mem, c->part, c->inbox,
                   c->piece, c->mail, c->probe_mem, c->stage, c->rpart, c->result};
   for (void* p : ptrs)
@@ -415,7 +422,7 @@ int std_create(std_ctx** out, int32_t order, const int64_t* mode_sizes, const in
   if (opt.ptr_kind != 0 && opt.ptr_kind != 1) return set_error(STD_EINVAL, "ptr_kind must be 0 or 1");
   if (opt.ctas < 0) return set_error(STD_EINVAL, "ctas must be >= 0");
   if (opt.contraction != 0 && opt.contraction != 1) return set_error(STD_EINVAL, "contraction must be 0 or 1");
-  if (opt.reserved != 0) return set_error(STD_EINVAL, "reserved option field must be 0");
+  if (!(opt.momentum >= 0.f && opt.momentum < 1.f)) return set_error(STD_EINVAL, "momentum must be in [0, 1)");
   Geometry g{};
   g.N = order;
   g.R = opt.r_core;
@@ -477,6 +484,16 @@ int std_create(std_ctx** out, int32_t order, const int64_t* mode_sizes, const in
     for (int n = 0; n < order; ++n)
       TRY(dev_alloc(c, (void**)&c->Ab[n], (size_t)g.I[n] * g.Jb[n] * 2, "BF16 factor mirror"));
   TRY(dev_alloc(c, (void**)&c->B, (size_t)boff * 4, "Kruskal matrices"));
+  if (opt.momentum != 0.f) {
+    for (int n = 0; n < order; ++n) {
+      TRY(dev_alloc(c, (void**)&c->vA[n], (size_t)g.I[n] * g.Jp[n] * 4, "factor velocities"));
+      TRY(cudaMemsetAsync(c->vA[n], 0, (size_t)g.I[n] * g.Jp[n] * 4, c->stream) == cudaSuccess
+              ? STD_OK : cuda_error(cudaGetLastError(), "memset"));
+    }
+    TRY(dev_alloc(c, (void**)&c->vB, (size_t)boff * 4, "Kruskal velocities"));
+    TRY(cudaMemsetAsync(c->vB, 0, (size_t)boff * 4, c->stream) == cudaSuccess
+            ? STD_OK : cuda_error(cudaGetLastError(), "memset"));
+  }
   TRY(dev_alloc(c, (void**)&c->core, (size_t)g.prodJ * 4, "core"));
   TRY(cudaMemsetAsync(c->err, 0, 16, c->stream) == cudaSuccess ? STD_OK : cuda_error(cudaGetLastError(), "memset"));
   const int32_t* dcoords = indices;
@@ -709,6 +726,12 @@ int std_set_params(std_ctx* c, const float* const* A, const float* const* B, int
   }
   STD_CUDA(launch_build_core(g, c->B, c->core, c->stream), "core build");
   if (c->opt.precision == 1) STD_CUDA(launch_mirror_bf16(g, c->A, c->Ab, c->stream), "BF16 mirror");
+  if (c->vB) {
+    for (int n = 0; n < g.N; ++n)
+      STD_CUDA(cudaMemsetAsync(c->vA[n], 0, (size_t)g.I[n] * g.Jp[n] * 4, c->stream), "velocity reset");
+    STD_CUDA(cudaMemsetAsync(c->vB, 0, (size_t)g.boff[g.N - 1] * 4 + (size_t)g.J[g.N - 1] * g.R * 4, c->stream),
+             "velocity reset");
+  }
   STD_CUDA(cudaStreamSynchronize(c->stream), "set params sync");
   if (epoch >= 0) c->epoch = epoch;
   return STD_OK;

@@ -132,7 +132,7 @@ __host__ __device__ inline int bf16_row_stride(int Pn) {
 }
 
 struct SmemLayout {
-  int B, G, GT, GTh, Sh, S, ldig, cdig, rowtab, trij, sc[2], rows, master, p, left, right, red, D, q, head, fown,
+  int B, VB, G, GT, GTh, Sh, S, ldig, cdig, rowtab, trij, sc[2], rows, master, p, left, right, red, D, q, head, fown,
       pbuf, total_words;
   int lw, rw, sfloats, rpre;
 };
@@ -167,6 +167,7 @@ __host__ __device__ inline SmemLayout smem_layout_v(const Geometry& g, int chunk
   L.sfloats = (bf || v == 2) ? 0 : (chunk * pad4(Pmax) < kSBudget ? chunk * pad4(Pmax) : kSBudget);
   const int kpmax = bf16_row_stride(Pmax);
   L.B = take(sumJR);
+  L.VB = take(sumJR);
   L.G = take(g.prodJ);
   L.GT = take(bf ? 0 : g.Jmax * pad4(Pmax));
   L.GTh = take(bf ? round_up(g.Jmax, 16) * kpmax / 2 : 0);
@@ -501,12 +502,14 @@ k_epoch(EpochArgs a) {
       mGs[kMaxN], mRoff[kMaxN];
   __shared__ FastDiv mFna4[kMaxN], mFnq4[kMaxN], mFtJ[kMaxN], mFJ[kMaxN], mFper[kMaxN];
   __shared__ float* mA[kMaxN];
+  __shared__ float* mvA[kMaxN];
   __shared__ unsigned short* mAb[kMaxN];
   __shared__ int s_nheads;
   const int N = a.g.N, R = a.g.R;
   const int chunk_max = a.chunk_max;
   const SmemLayout L = smem_layout(a.g, chunk_max, gridDim.x, BF ? 1 : 0);
   float* Bsm = sm + L.B;
+  float* VBsm = sm + L.VB;   // Kruskal-column velocities (momentum)
   float* Gsm = sm + L.G;
   float* GT = sm + L.GT;
   __nv_bfloat16* GTh = reinterpret_cast<__nv_bfloat16*>(sm + L.GTh);
@@ -548,6 +551,7 @@ k_epoch(EpochArgs a) {
       mJb[k] = a.g.Jb[k];
       mGs[k] = a.g.gstride[k];
       mA[k] = a.A[k];
+      mvA[k] = a.vA[k];
       mAb[k] = reinterpret_cast<unsigned short*>(a.Ab[k]);
     }
     int toff = 0, roff = 0;
@@ -571,7 +575,10 @@ k_epoch(EpochArgs a) {
   int sumJR = 0;
   for (int n = 0; n < N; ++n) sumJR += mJ[n] * R;
 #pragma unroll 1
-  for (int i = tid; i < sumJR; i += T) Bsm[i] = __ldcg(a.B + i);
+  for (int i = tid; i < sumJR; i += T) {
+    Bsm[i] = __ldcg(a.B + i);
+    VBsm[i] = a.momentum != 0.f ? __ldcg(a.vB + i) : 0.f;
+  }
 #pragma unroll 1
   for (int lin = tid; lin < prodJ; lin += T) {
     int t = lin;
@@ -888,7 +895,14 @@ k_epoch(EpochArgs a) {
                 if (lj) {
                   const float V = ra == r ? Va : Vb;
                   const float bo = ra == r ? boa : bob;
-                  const float bn = bo - a.lr_b * (V * invm + a.lam_b * bo);
+                  const float gb = V * invm + a.lam_b * bo;
+                  float step = gb;
+                  if (a.momentum != 0.f) {
+                    float* vb = VBsm + mBoff[n] + lane * R + r;
+                    step = a.momentum * *vb + gb;
+                    *vb = step;
+                  }
+                  const float bn = bo - a.lr_b * step;
                   d = bn - bo;
                   Bn[lane * R + r] = bn;
                   if (probe && c == 0 && a.probeV) a.probeV[((unsigned)n * R + r) * kMaxJ + lane] = V;
@@ -1270,7 +1284,14 @@ k_epoch(EpochArgs a) {
             const float denom = a.norm_mode == 1 ? (float)(en - st + 1) : fm;
             const unsigned row = (unsigned)fcrd[s0 * N + n];
             const float av = BF ? master[s0 * Jmax + lane] : rows[s0 * sumJ + mJoff[n] + lane];
-            const float nv = av - a.lr_a * (F / denom + a.lam_a * av);
+            const float ga = F / denom + a.lam_a * av;
+            float step = ga;
+            if (a.momentum != 0.f) {
+              float* vp = mvA[n] + row * (unsigned)mJp[n] + lane;
+              step = a.momentum * __ldcg(vp) + ga;
+              __stcg(vp, step);
+            }
+            const float nv = av - a.lr_a * step;
             __stcg(mA[n] + row * (unsigned)mJp[n] + lane, nv);
             if (BF) __stcg(mAb[n] + row * (unsigned)mJb[n] + lane, __bfloat16_as_ushort(__float2bfloat16_rn(nv)));
             if (n + 1 < N) put_word(a.mail + ((unsigned)n * (unsigned)M + st) * (unsigned)Jmax + lane, tag, nv);
@@ -1283,7 +1304,10 @@ k_epoch(EpochArgs a) {
 
   if (c == 0) {
 #pragma unroll 1
-    for (int i = tid; i < sumJR; i += T) a.B[i] = Bsm[i];
+    for (int i = tid; i < sumJR; i += T) {
+      a.B[i] = Bsm[i];
+      if (a.momentum != 0.f) a.vB[i] = VBsm[i];
+    }
 #pragma unroll 1
     for (int lin = tid; lin < prodJ; lin += T) {
       const uint32_t packed = ldig[lin];

@@ -130,6 +130,9 @@ struct EpochArgs {
   float lr_a, lr_b, lam_a, lam_b;
   int norm_mode;
   int contraction;       // 0 Kronecker rows x unfolded core; 1 Kruskal form E = B(n) w
+  float momentum;        // heavy-ball mu (0 = plain SGD)
+  float* vA[kMaxN];      // factor-row velocities, I_n x Jp_n (momentum != 0)
+  float* vB;             // Kruskal-column velocities, concatenated like B (momentum != 0)
   int chunk_max;
   // cross-CTA exchange words: (sequence tag << 32) | float bits
   uint32_t tag_base;           // tag of (minibatch b, mode n) = tag_base + 8 (b - b0) + n

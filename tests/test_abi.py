@@ -95,7 +95,8 @@ def test_create_rejects_bad_shapes_on_the_host(lib, order, sizes, ranks, r_core,
 def test_create_rejects_bad_options_and_nnz(lib):
     idx = np.zeros((1, 3), np.int32)
     val = np.zeros(1, np.float32)
-    for field, value in [("precision", 2), ("norm_mode", 3), ("ptr_kind", 5), ("ctas", -1), ("init_mode", 9)]:
+    for field, value in [("precision", 2), ("norm_mode", 3), ("ptr_kind", 5), ("ctas", -1), ("init_mode", 9),
+                         ("contraction", 2), ("momentum", 1.0), ("momentum", -0.1), ("momentum", float("nan"))]:
         o = lib.std_default_options()
         setattr(o, field, value)
         with pytest.raises(lib.StdError) as ei:

@@ -312,6 +312,41 @@ def test_paper_setting_m1_core_schedule(B, synth):
     assert worst <= 1e-3, worst
 
 
+# Heavy-ball momentum (the accelerated SGD the paper names as future work):
+# several consecutive minibatches, so that the velocities carry over, against
+# the oracle with the same momentum.
+@pytest.mark.parametrize("mu,precision_args", [(0.9, {}), (0.5, {"contraction": 1})])
+def test_momentum_consecutive_minibatches(B, synth, cfg1, mu, precision_args):
+    c, v = cfg1.tensor.split("train")
+    A0, B0 = synth.init_params(cfg1.tensor.shape, cfg1.ranks, 5, mode="normal", seed=1)
+    ref = O.Model(cfg1.tensor.shape, cfg1.ranks, 5, A0, B0, momentum=mu)
+    lr, lam, M, nb = (0.2, 0.1), (0.01, 0.02), 256, 6
+    with _gpu(B, cfg1.tensor.shape, cfg1.ranks, 5, c, v, A0, B0, momentum=mu, **precision_args) as g:
+        g.batches(lr[0], lr[1], lam[0], lam[1], M, 0, nb)
+        ref.epoch(c, v, M, 2, 0, lr[0], lr[1], lam[0], lam[1], 0, 0, nb)
+        Ag, Bg, _, _ = g.get_params()
+    for n in range(3):
+        assert float(np.abs(Ag[n] - ref.A[n]).max()) <= 1e-5 * float(np.abs(ref.A[n]).max())
+        assert float(np.abs(Bg[n] - ref.B[n]).max()) <= 1e-5 * float(np.abs(ref.B[n]).max())
+
+
+def test_momentum_epoch_rmse_parity(B, synth, cfg1):
+    c, v = cfg1.tensor.split("train")
+    tc, tv = cfg1.tensor.split("test")
+    A0, B0 = synth.init_params(cfg1.tensor.shape, cfg1.ranks, 5, mode="normal", seed=1)
+    mu, lr = 0.8, 0.1
+    ref = O.Model(cfg1.tensor.shape, cfg1.ranks, 5, A0, B0, momentum=mu)
+    worst = 0.0
+    with _gpu(B, cfg1.tensor.shape, cfg1.ranks, 5, c, v, A0, B0, momentum=mu) as g:
+        for ep in range(4):
+            g.epoch(lr, lr, cfg1.lam, cfg1.lam, cfg1.minibatch)
+            ref.epoch(c, v, cfg1.minibatch, 2, ep, lr, lr, cfg1.lam, cfg1.lam)
+            r_g, m_g = g.rmse(tc, tv)
+            r_o, m_o = ref.rmse_mae(tc, tv)
+            worst = max(worst, abs(r_g - r_o), abs(m_g - m_o))
+    assert worst <= 1e-3, worst
+
+
 # ---------------------------------------------------------------------------
 # Epochs: per-epoch train/test RMSE within 1e-3 absolute over 10 epochs
 # ---------------------------------------------------------------------------
