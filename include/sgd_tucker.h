@@ -203,6 +203,43 @@ int std_set_params(std_ctx* ctx, const float* const* A, const float* const* B, i
 const char* std_last_error(void);
 
 /*
+ * Batched epochs: many independent decompositions (each its own std_ctx) in
+ * one persistent launch.  The GPU's co-resident CTAs are split into groups of
+ * `ctas_per_tensor` CTAs; each group runs the epoch of its tensors one after
+ * the other (longest first onto the least-loaded group), so small tensors no
+ * longer leave the GPU idle behind one tensor's chain of dependent phases
+ * (Algorithm 1).  Each tensor's epoch is exactly the one std_sgd_epoch would
+ * run with that many CTAs.
+ *   count, ctxs       the contexts (same precision, same stream; each at most
+ *                     once); they must outlive the batch, which does not own them
+ *   ctas_per_tensor   CTAs per tensor; 0 = chosen on the first std_batch_epoch
+ *                     by timing each power of two that fits on a run of the
+ *                     first minibatches that writes no parameter
+ * Errors: STD_EINVAL, STD_ECUDA.
+ */
+typedef struct std_batch std_batch;
+int std_batch_create(std_batch** out, int32_t count, std_ctx* const* ctxs, int32_t ctas_per_tensor);
+
+typedef struct {
+    double  seconds;          /* device time of the batched epoch (samplers, tilers, update kernel) */
+    double  update_seconds;   /* device time of the batched update kernel alone */
+    double  nnz_per_s;        /* total training nonzeros / seconds */
+    int64_t nnz;              /* total training nonzeros visited */
+    int32_t tensors;
+    int32_t ctas_per_tensor;  /* the group size used */
+} std_batch_stats;
+
+/* One epoch of every tensor of the batch (same hyperparameters and minibatch
+ * size for all; the definition of an epoch is std_sgd_epoch's).  Every
+ * context's epoch counter advances.  Errors: STD_EINVAL, STD_EUNSUPPORTED,
+ * STD_ENOMEM, STD_ECUDA, STD_ETIMEOUT. */
+int std_batch_epoch(std_batch* batch, float lr_a, float lr_b, float lambda_a, float lambda_b,
+                    int32_t minibatch, std_batch_stats* out);
+
+/* Release the batch (not its contexts; NULL is a no-op). */
+int std_batch_destroy(std_batch* batch);
+
+/*
  * RMSE and MAE without any device allocation.  The paper has no counterpart:
  * this is for callers that cannot let a library allocate device memory, such
  * as a serving process whose device memory is all reserved by its own pool

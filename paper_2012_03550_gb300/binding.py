@@ -70,6 +70,17 @@ class std_epoch_stats(ctypes.Structure):
     ]
 
 
+class std_batch_stats(ctypes.Structure):
+    _fields_ = [
+        ("seconds", ctypes.c_double),
+        ("update_seconds", ctypes.c_double),
+        ("nnz_per_s", ctypes.c_double),
+        ("nnz", ctypes.c_int64),
+        ("tensors", ctypes.c_int32),
+        ("ctas_per_tensor", ctypes.c_int32),
+    ]
+
+
 class std_probe(ctypes.Structure):
     _fields_ = [
         ("core_V", ctypes.c_void_p),
@@ -98,6 +109,10 @@ SIGNATURES = {
     "std_last_error": (ctypes.c_char_p, []),
     "std_rmse_static": (ctypes.c_int, [ctypes.c_int32, _P, _P, ctypes.c_int32, _P, _P, ctypes.c_int64, _P, _P,
                                        _P, _P]),
+    "std_batch_create": (ctypes.c_int, [_P, ctypes.c_int32, _P, ctypes.c_int32]),
+    "std_batch_epoch": (ctypes.c_int, [_P, ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_float,
+                                       ctypes.c_int32, _P]),
+    "std_batch_destroy": (ctypes.c_int, [_P]),
 }
 
 
@@ -313,3 +328,43 @@ class Tucker:
         A = [np.ascontiguousarray(a, dtype=np.float32) for a in A] if A is not None else None
         B = [np.ascontiguousarray(b, dtype=np.float32) for b in B] if B is not None else None
         std_set_params(self.ctx, A, B, epoch)
+
+
+def std_batch_create(ctxs, ctas_per_tensor=0):
+    arr = (ctypes.c_void_p * len(ctxs))(*[c.value if isinstance(c, ctypes.c_void_p) else c for c in ctxs])
+    out = ctypes.c_void_p()
+    _check(lib().std_batch_create(ctypes.byref(out), len(ctxs), ctypes.cast(arr, ctypes.c_void_p),
+                                  int(ctas_per_tensor)))
+    return out
+
+
+def std_batch_epoch(batch, lr_a, lr_b, lambda_a, lambda_b, minibatch):
+    st = std_batch_stats()
+    _check(lib().std_batch_epoch(batch, lr_a, lr_b, lambda_a, lambda_b, int(minibatch), ctypes.byref(st)))
+    return {f: getattr(st, f) for f, _ in std_batch_stats._fields_}
+
+
+def std_batch_destroy(batch):
+    _check(lib().std_batch_destroy(batch))
+
+
+class Batch:
+    """Owning wrapper of a batch over existing Tucker objects (which it does not own)."""
+
+    def __init__(self, tuckers, ctas_per_tensor=0):
+        self.members = list(tuckers)
+        self.ptr = std_batch_create([t.ctx for t in self.members], ctas_per_tensor)
+
+    def epoch(self, lr_a, lr_b, lam_a, lam_b, minibatch):
+        return std_batch_epoch(self.ptr, lr_a, lr_b, lam_a, lam_b, minibatch)
+
+    def close(self):
+        if self.ptr is not None:
+            std_batch_destroy(self.ptr)
+            self.ptr = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

@@ -2,8 +2,10 @@
 // device memory of a context, and the launch sequence of each call.
 #include <cmath>
 #include <cstdio>
+#include <algorithm>
 #include <cstring>
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "sgdt_internal.cuh"
@@ -261,6 +263,44 @@ int check_hyper(float lr_a, float lr_b, float lam_a, float lam_b, int32_t M) {
   return STD_OK;
 }
 
+// Kernel arguments of minibatches [b0, b1) of the context's current schedule.
+EpochArgs epoch_args(std_ctx* c, float lr_a, float lr_b, float lam_a, float lam_b, int64_t b0, int64_t b1,
+                     int chunk, uint32_t tag_base) {
+  EpochArgs a{};
+  a.g = c->g;
+  for (int n = 0; n < c->g.N; ++n) {
+    a.A[n] = c->A[n];
+    a.Ab[n] = c->Ab[n];
+    a.vA[n] = c->vA[n];
+  }
+  a.precision = c->opt.precision;
+  a.B = c->B;
+  a.core = c->core;
+  a.s = c->sched;
+  a.b0 = b0;
+  a.b1 = b1;
+  a.lr_a = lr_a;
+  a.lr_b = lr_b;
+  a.lam_a = lam_a;
+  a.lam_b = lam_b;
+  a.norm_mode = c->opt.norm_mode;
+  a.contraction = c->opt.contraction;
+  a.momentum = c->opt.momentum;
+  a.vB = c->vB;
+  a.chunk_max = chunk;
+  a.tag_base = tag_base;
+  a.part = c->part;
+  a.inbox = c->inbox;
+  a.piece = c->piece;
+  a.mail = c->mail;
+  a.pstride = exchange_pstride(payload_floats(c->g));
+  a.bar = c->bar;
+  a.err = c->err;
+  a.watchdog_ns = c->opt.watchdog_ns ? c->opt.watchdog_ns : 2000000000ULL;
+  a.probe_batch = -1;
+  return a;
+}
+
 // Runs minibatches [b0, b1) of the current schedule.  With record_end, ev1
 // is recorded on the stream right after the kernel (the caller records ev0).
 int run_batches(std_ctx* c, float lr_a, float lr_b, float lam_a, float lam_b, int32_t M, int64_t b0, int64_t b1,
@@ -293,37 +333,7 @@ int run_batches(std_ctx* c, float lr_a, float lr_b, float lam_a, float lam_b, in
     pV = c->probe_mem;
     pF = c->probe_mem + (size_t)c->g.N * c->g.R * kMaxJ;
   }
-  EpochArgs a{};
-  a.g = c->g;
-  for (int n = 0; n < c->g.N; ++n) {
-    a.A[n] = c->A[n];
-    a.Ab[n] = c->Ab[n];
-  }
-  a.precision = c->opt.precision;
-  a.B = c->B;
-  a.core = c->core;
-  a.s = c->sched;
-  a.b0 = b0;
-  a.b1 = b1;
-  a.lr_a = lr_a;
-  a.lr_b = lr_b;
-  a.lam_a = lam_a;
-  a.lam_b = lam_b;
-  a.norm_mode = c->opt.norm_mode;
-  a.contraction = c->opt.contraction;
-  a.momentum = c->opt.momentum;
-  for (int n = 0; n < c->g.N; ++n) a.vA[n] = c->vA[n];
-  a.vB = c->vB;
-  a.chunk_max = chunk;
-  a.tag_base = tag_base;
-  a.part = c->part;
-  a.inbox = c->inbox;
-  a.piece = c->piece;
-  a.mail = c->mail;
-  a.pstride = exchange_pstride(payload);
-  a.bar = c->bar;
-  a.err = c->err;
-  a.watchdog_ns = c->opt.watchdog_ns ? c->opt.watchdog_ns : 2000000000ULL;
+  EpochArgs a = epoch_args(c, lr_a, lr_b, lam_a, lam_b, b0, b1, chunk, tag_base);
   a.probe_batch = probe ? b0 : -1;
   a.probeV = pV;
   a.probeF = pF;
@@ -734,6 +744,236 @@ int std_set_params(std_ctx* c, const float* const* A, const float* const* B, int
   }
   STD_CUDA(cudaStreamSynchronize(c->stream), "set params sync");
   if (epoch >= 0) c->epoch = epoch;
+  return STD_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Batched epochs: many independent tensors in one persistent launch.
+// ---------------------------------------------------------------------------
+
+struct std_batch {
+  std::vector<std_ctx*> ctxs;
+  cudaStream_t stream = nullptr;
+  int precision = 0;
+  int group = 0;          // CTAs per tensor; 0 until tuned
+  bool tuned = false;
+  int* err = nullptr;     // one error word shared by every tensor of a launch
+  EpochArgs* d_items = nullptr;
+  int* d_order = nullptr;
+  int* d_first = nullptr;
+  size_t cap_items = 0, cap_groups = 0;
+  std::vector<EpochArgs> h_items;
+  std::vector<int> h_order, h_first;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr, evm = nullptr;
+};
+
+namespace {
+
+// Smallest chunk a CTA of the batched kernel handles for tensor c at group
+// size G, or 0 when the shape does not fit a CTA.
+size_t batch_smem(std_ctx* c, int M, int G) {
+  const int chunk = (M + G - 1) / G;
+  if (chunk > epoch_chunk_cap(c->g)) return 0;
+  const size_t sm = epoch_smem_bytes(c->g, chunk, G, c->opt.precision);
+  return sm > 227 * 1024 ? 0 : sm;
+}
+
+// One launch of minibatches [b0, min(b1, nb_t)) of every tensor at group size
+// G; dry = no parameter writes (timing runs of the tuner).
+int batch_launch(std_batch* bt, float lr_a, float lr_b, float lam_a, float lam_b, int32_t M, int64_t b0,
+                 int64_t b1, int G, bool dry) {
+  const int T = (int)bt->ctxs.size();
+  size_t smem = 0;
+  bt->h_items.resize(T);
+  std::vector<std::pair<int64_t, int>> work;
+  for (int t = 0; t < T; ++t) {
+    std_ctx* c = bt->ctxs[t];
+    int rc = ensure_schedule(c, M);
+    if (rc) return rc;
+    const size_t sm = batch_smem(c, M, G);
+    if (sm == 0) return set_error(STD_EUNSUPPORTED, "a tensor of the batch does not fit a CTA at this group size");
+    smem = sm > smem ? sm : smem;
+    rc = ensure_scratch(c, G, payload_floats(c->g), M);
+    if (rc) return rc;
+    const int64_t nb = (c->nnz + M - 1) / M;
+    const int64_t e0 = b0 < nb ? b0 : nb, e1 = b1 < nb ? b1 : nb;
+    uint32_t tag_base = 0;
+    rc = reserve_tags(c, e1 - e0, &tag_base);
+    if (rc) return rc;
+    EpochArgs a = epoch_args(c, lr_a, lr_b, lam_a, lam_b, e0, e1, (M + G - 1) / G, tag_base);
+    a.err = bt->err;
+    a.dry = dry ? 1 : 0;
+    if (dry) a.momentum = 0.f;
+    bt->h_items[t] = a;
+    STD_CUDA(cudaMemsetAsync(c->bar, 0, sizeof(unsigned long long), bt->stream), "barrier clear");
+    work.push_back({(e1 - e0) * (int64_t)M * (c->g.sumJ + c->g.prodJ / c->g.Jmax), t});
+  }
+  STD_CUDA(epoch_multi_setup(bt->precision, smem), "batched kernel attributes");
+  const int maxc = epoch_multi_max_ctas(bt->precision, smem);
+  int groups = maxc / G;
+  if (groups > T) groups = T;
+  if (groups < 1) return set_error(STD_EUNSUPPORTED, "batched kernel cannot be resident at this group size");
+  // longest processing time first: tensors by decreasing work to the least-loaded group
+  std::sort(work.begin(), work.end(), [](const std::pair<int64_t, int>& x, const std::pair<int64_t, int>& y) {
+    return x.first != y.first ? x.first > y.first : x.second < y.second;
+  });
+  std::vector<int64_t> load(groups, 0);
+  std::vector<std::vector<int>> lists(groups);
+  for (auto& w : work) {
+    int q = 0;
+    for (int k = 1; k < groups; ++k)
+      if (load[k] < load[q]) q = k;
+    load[q] += w.first;
+    lists[q].push_back(w.second);
+  }
+  bt->h_order.clear();
+  bt->h_first.assign(1, 0);
+  for (int q = 0; q < groups; ++q) {
+    for (int t : lists[q]) bt->h_order.push_back(t);
+    bt->h_first.push_back((int)bt->h_order.size());
+  }
+  if ((size_t)T > bt->cap_items || (size_t)groups + 1 > bt->cap_groups) {
+    cudaFree(bt->d_items);
+    cudaFree(bt->d_order);
+    cudaFree(bt->d_first);
+    bt->d_items = nullptr;
+    bt->d_order = nullptr;
+    bt->d_first = nullptr;
+    const size_t ci = (size_t)T, cg = (size_t)(T + 1);
+    STD_CUDA(cudaMalloc((void**)&bt->d_items, ci * sizeof(EpochArgs)), "batch arguments");
+    STD_CUDA(cudaMalloc((void**)&bt->d_order, ci * sizeof(int)), "batch order");
+    STD_CUDA(cudaMalloc((void**)&bt->d_first, cg * sizeof(int)), "batch groups");
+    bt->cap_items = ci;
+    bt->cap_groups = cg;
+  }
+  STD_CUDA(cudaMemcpyAsync(bt->d_items, bt->h_items.data(), (size_t)T * sizeof(EpochArgs), cudaMemcpyHostToDevice,
+                           bt->stream), "batch arguments upload");
+  STD_CUDA(cudaMemcpyAsync(bt->d_order, bt->h_order.data(), (size_t)T * sizeof(int), cudaMemcpyHostToDevice,
+                           bt->stream), "batch order upload");
+  STD_CUDA(cudaMemcpyAsync(bt->d_first, bt->h_first.data(), (size_t)(groups + 1) * sizeof(int),
+                           cudaMemcpyHostToDevice, bt->stream), "batch groups upload");
+  MultiArgs m{};
+  m.items = bt->d_items;
+  m.order = bt->d_order;
+  m.first = bt->d_first;
+  m.group = G;
+  STD_CUDA(cudaEventRecord(bt->evm, bt->stream), "event");
+  STD_CUDA(launch_epoch_multi(m, bt->precision, groups * G, smem, bt->stream), "batched kernel launch");
+  STD_CUDA(cudaEventRecord(bt->ev1, bt->stream), "event");
+  int h = 0;
+  STD_CUDA(cudaMemcpyAsync(&h, bt->err, sizeof(int), cudaMemcpyDeviceToHost, bt->stream), "batch error read");
+  STD_CUDA(cudaStreamSynchronize(bt->stream), "batch sync");
+  if (h != 0) {
+    STD_CUDA(cudaMemset(bt->err, 0, sizeof(int)), "batch error reset");
+    if (h == STD_ETIMEOUT) return set_error(STD_ETIMEOUT, "batched epoch kernel: barrier watchdog expired");
+    return set_error(h, "batched epoch kernel: device error");
+  }
+  return STD_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int std_batch_create(std_batch** out, int32_t count, std_ctx* const* ctxs, int32_t ctas_per_tensor) {
+  if (!out) return set_error(STD_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (count < 1 || !ctxs) return set_error(STD_EINVAL, "a batch needs at least one context");
+  if (ctas_per_tensor < 0) return set_error(STD_EINVAL, "ctas_per_tensor must be >= 0");
+  for (int t = 0; t < count; ++t) {
+    if (!ctxs[t]) return set_error(STD_EINVAL, "NULL context in the batch");
+    if (ctxs[t]->opt.precision != ctxs[0]->opt.precision)
+      return set_error(STD_EINVAL, "every context of a batch must use the same precision");
+    if (ctxs[t]->stream != ctxs[0]->stream)
+      return set_error(STD_EINVAL, "every context of a batch must use the same stream");
+    for (int u = 0; u < t; ++u)
+      if (ctxs[u] == ctxs[t]) return set_error(STD_EINVAL, "a context appears twice in the batch");
+  }
+  std_batch* bt = new std_batch();
+  bt->ctxs.assign(ctxs, ctxs + count);
+  bt->stream = ctxs[0]->stream;
+  bt->precision = ctxs[0]->opt.precision;
+  bt->group = ctas_per_tensor;
+  bt->tuned = ctas_per_tensor > 0;
+  cudaError_t e = cudaMalloc((void**)&bt->err, sizeof(int));
+  if (e == cudaSuccess) e = cudaMemset(bt->err, 0, sizeof(int));
+  if (e == cudaSuccess) e = cudaEventCreate(&bt->ev0);
+  if (e == cudaSuccess) e = cudaEventCreate(&bt->ev1);
+  if (e == cudaSuccess) e = cudaEventCreate(&bt->evm);
+  if (e != cudaSuccess) {
+    std_batch_destroy(bt);
+    return cuda_error(e, "batch setup");
+  }
+  *out = bt;
+  return STD_OK;
+}
+
+int std_batch_destroy(std_batch* bt) {
+  if (!bt) return STD_OK;
+  cudaStreamSynchronize(bt->stream);
+  cudaFree(bt->err);
+  cudaFree(bt->d_items);
+  cudaFree(bt->d_order);
+  cudaFree(bt->d_first);
+  if (bt->ev0) cudaEventDestroy(bt->ev0);
+  if (bt->ev1) cudaEventDestroy(bt->ev1);
+  if (bt->evm) cudaEventDestroy(bt->evm);
+  delete bt;
+  return STD_OK;
+}
+
+int std_batch_epoch(std_batch* bt, float lr_a, float lr_b, float lambda_a, float lambda_b, int32_t minibatch,
+                    std_batch_stats* out) {
+  if (!bt) return set_error(STD_EINVAL, "batch is NULL");
+  int rc = check_hyper(lr_a, lr_b, lambda_a, lambda_b, minibatch);
+  if (rc) return rc;
+  if (!bt->tuned) {
+    // autotuner: each group size that fits times a dry run (no parameter
+    // writes) of the first minibatches of every tensor; the fastest wins
+    float best = -1.f;
+    int best_g = 0;
+    for (int G = 1; G <= 32; G *= 2) {
+      bool fits = true;
+      for (std_ctx* c : bt->ctxs)
+        if (batch_smem(c, minibatch, G) == 0) fits = false;
+      if (!fits) continue;
+      rc = batch_launch(bt, lr_a, lr_b, lambda_a, lambda_b, minibatch, 0, 4, G, true);
+      if (rc == STD_EUNSUPPORTED) continue;
+      if (rc) return rc;
+      float ms = 0.f;
+      STD_CUDA(cudaEventElapsedTime(&ms, bt->evm, bt->ev1), "event time");
+      if (best < 0.f || ms < best) {
+        best = ms;
+        best_g = G;
+      }
+    }
+    if (best_g == 0) return set_error(STD_EUNSUPPORTED, "no group size fits every tensor of the batch");
+    bt->group = best_g;
+    bt->tuned = true;
+  }
+  STD_CUDA(cudaEventRecord(bt->ev0, bt->stream), "event");
+  int64_t nb_max = 0, nnz = 0;
+  for (std_ctx* c : bt->ctxs) {
+    const int64_t nb = (c->nnz + minibatch - 1) / minibatch;
+    nb_max = nb > nb_max ? nb : nb_max;
+    nnz += c->nnz;
+  }
+  rc = batch_launch(bt, lr_a, lr_b, lambda_a, lambda_b, minibatch, 0, nb_max, bt->group, false);
+  if (rc) return rc;
+  for (std_ctx* c : bt->ctxs) c->epoch += 1;
+  float ms = 0.f, ms_upd = 0.f;
+  STD_CUDA(cudaEventElapsedTime(&ms, bt->ev0, bt->ev1), "event time");
+  STD_CUDA(cudaEventElapsedTime(&ms_upd, bt->evm, bt->ev1), "event time");
+  if (out) {
+    out->seconds = ms * 1e-3;
+    out->update_seconds = ms_upd * 1e-3;
+    out->nnz = nnz;
+    out->nnz_per_s = ms > 0.f ? (double)nnz / (ms * 1e-3) : 0.0;
+    out->tensors = (int32_t)bt->ctxs.size();
+    out->ctas_per_tensor = bt->group;
+  }
   return STD_OK;
 }
 

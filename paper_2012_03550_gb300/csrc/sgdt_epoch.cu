@@ -367,16 +367,18 @@ __device__ __forceinline__ bool wait_pairs(const unsigned long long* const (&p)[
   }
 }
 
-// Grid barrier over all CTAs of the cooperative launch.  The counter only
-// grows; barrier k completes when it reaches k * G.  A wait longer than the
+// Barrier over the G CTAs that work on one tensor (all CTAs of a
+// single-tensor launch, or one group of a batched launch; co-resident in a
+// cooperative launch).  The counter only grows; barrier k completes when it
+// reaches k * G.  A wait longer than the
 // watchdog budget (or an error raised by another CTA) makes every CTA return
 // false; the host then reports STD_ETIMEOUT.
-__device__ bool grid_barrier(const EpochArgs& a, unsigned long long& generation) {
+__device__ bool grid_barrier(const EpochArgs& a, unsigned long long& generation, int G) {
   __shared__ int s_ok;
   __syncthreads();
   if (threadIdx.x == 0) {
     ++generation;
-    const unsigned long long target = generation * (unsigned long long)gridDim.x;
+    const unsigned long long target = generation * (unsigned long long)G;
     red_release_add_u64(a.bar, 1ULL);
     int ok = 1;
     if (ld_acquire_u64(a.bar) < target) {
@@ -416,13 +418,13 @@ struct Phase {
   int m, chunk, lo, hi, cnt;
 };
 
-__device__ __forceinline__ Phase phase_of(const EpochArgs& a, int64_t b) {
+__device__ __forceinline__ Phase phase_of(const EpochArgs& a, int64_t b, int G, int c) {
   Phase ph;
   const int M = a.s.M;
   const int64_t t0 = b * (int64_t)M;
   ph.m = (int)((a.s.n - t0) < (int64_t)M ? (a.s.n - t0) : (int64_t)M);
-  ph.chunk = (ph.m + gridDim.x - 1) / gridDim.x;
-  ph.lo = blockIdx.x * ph.chunk;
+  ph.chunk = (ph.m + G - 1) / G;
+  ph.lo = c * ph.chunk;
   ph.hi = min(ph.lo + ph.chunk, ph.m);
   ph.cnt = ph.hi > ph.lo ? ph.hi - ph.lo : 0;
   return ph;
@@ -432,8 +434,8 @@ __device__ __forceinline__ Phase phase_of(const EpochArgs& a, int64_t b) {
 // minibatch b into a shared schedule buffer (coordinates [s][N], values, run
 // bounds, links [s][N]).
 __device__ __forceinline__ void prefetch_schedule(const EpochArgs& a, int N, int64_t b, int mode, int* buf,
-                                                  int chunk_max, FastDiv fper) {
-  const Phase ph = phase_of(a, b);
+                                                  int chunk_max, FastDiv fper, int G, int c) {
+  const Phase ph = phase_of(a, b, G, c);
   const size_t base = (size_t)(b * (int64_t)a.s.M + ph.lo);
   int* crd = buf;
   int* xs = buf + N * chunk_max;
@@ -493,9 +495,9 @@ __device__ __forceinline__ void right_row(float* dst, const float* an, int Jn, i
 
 }  // namespace
 
+// The epoch of one tensor on the G CTAs c = 0..G-1 that own it.
 template <bool BF>
-__global__ void __launch_bounds__(kEpochThreads, 1)
-k_epoch(EpochArgs a) {
+__device__ __forceinline__ void epoch_body(const EpochArgs& a, const int G, const int c) {
   extern __shared__ __align__(16) float sm[];
   // per-mode constants, indexed by the (runtime) mode
   __shared__ int mJ[kMaxN], mJoff[kMaxN], mBoff[kMaxN], mJp[kMaxN], mJb[kMaxN], mPn[kMaxN], mToff[kMaxN],
@@ -507,7 +509,7 @@ k_epoch(EpochArgs a) {
   __shared__ int s_nheads;
   const int N = a.g.N, R = a.g.R;
   const int chunk_max = a.chunk_max;
-  const SmemLayout L = smem_layout(a.g, chunk_max, gridDim.x, BF ? 1 : 0);
+  const SmemLayout L = smem_layout(a.g, chunk_max, G, BF ? 1 : 0);
   float* Bsm = sm + L.B;
   float* VBsm = sm + L.VB;   // Kruskal-column velocities (momentum)
   float* Gsm = sm + L.G;
@@ -531,7 +533,7 @@ k_epoch(EpochArgs a) {
   int* head = reinterpret_cast<int*>(sm + L.head);
   float* pieces_sm = sm + L.pbuf;
 
-  const int G = gridDim.x, c = blockIdx.x, tid = threadIdx.x, T = blockDim.x;
+  const int tid = threadIdx.x, T = blockDim.x;
   const int lane = tid & 31, warp = tid >> 5, nwarps = T >> 5;
   const int M = a.s.M;
   const int sumJ = a.g.sumJ, Jmax = a.g.Jmax, prodJ = a.g.prodJ;
@@ -618,13 +620,13 @@ k_epoch(EpochArgs a) {
     trij[q] = (q - tri(jb)) | (jb << 8);   // packed upper-triangle index q = jb (jb + 1) / 2 + ja
   }
   int buf = 0;
-  if (a.b0 < a.b1) prefetch_schedule(a, N, a.b0, 0, scb[0], chunk_max, mFper[0]);
+  if (a.b0 < a.b1) prefetch_schedule(a, N, a.b0, 0, scb[0], chunk_max, mFper[0], G, c);
   cp_async_commit();
   __syncthreads();
 
 #pragma unroll 1
   for (int64_t b = a.b0; b < a.b1; ++b) {
-    const Phase ph = phase_of(a, b);
+    const Phase ph = phase_of(a, b, G, c);
     const int cnt = ph.cnt, lo = ph.lo, hi = ph.hi;
     const bool probe = (b == a.probe_batch);
     const float fm = (float)ph.m;
@@ -632,11 +634,11 @@ k_epoch(EpochArgs a) {
     const uint32_t tag0 = a.tag_base + (uint32_t)((b - a.b0) * 8);
 
     // every row update of the previous minibatch is visible after this
-    if (b > a.b0 && !grid_barrier(a, generation)) return;
+    if (b > a.b0 && !grid_barrier(a, generation, G)) return;
     cp_async_wait_all();
     __syncthreads();
     // factor mode 2's chunk arrives while the core phase runs
-    prefetch_schedule(a, N, b, 1, scb[buf ^ 1], chunk_max, mFper[1]);
+    prefetch_schedule(a, N, b, 1, scb[buf ^ 1], chunk_max, mFper[1], G, c);
     cp_async_commit();
 
     // ------------------------------------------------------------------
@@ -991,7 +993,7 @@ k_epoch(EpochArgs a) {
         // the next phase's chunk: mode n+1 of this minibatch, or mode 1 of the next
         const int64_t nb = (n + 1 < N) ? b : b + 1;
         const int nmode = (n + 1 < N) ? n + 1 : 0;
-        if (nb < a.b1) prefetch_schedule(a, N, nb, nmode, scb[buf ^ 1], chunk_max, mFper[nmode]);
+        if (nb < a.b1) prefetch_schedule(a, N, nb, nmode, scb[buf ^ 1], chunk_max, mFper[nmode], G, c);
         cp_async_commit();
       }
       const int* fcrd = scb[buf];
@@ -1289,11 +1291,13 @@ k_epoch(EpochArgs a) {
             if (a.momentum != 0.f) {
               float* vp = mvA[n] + row * (unsigned)mJp[n] + lane;
               step = a.momentum * __ldcg(vp) + ga;
-              __stcg(vp, step);
+              if (!a.dry) __stcg(vp, step);
             }
             const float nv = av - a.lr_a * step;
-            __stcg(mA[n] + row * (unsigned)mJp[n] + lane, nv);
-            if (BF) __stcg(mAb[n] + row * (unsigned)mJb[n] + lane, __bfloat16_as_ushort(__float2bfloat16_rn(nv)));
+            if (!a.dry) {
+              __stcg(mA[n] + row * (unsigned)mJp[n] + lane, nv);
+              if (BF) __stcg(mAb[n] + row * (unsigned)mJb[n] + lane, __bfloat16_as_ushort(__float2bfloat16_rn(nv)));
+            }
             if (n + 1 < N) put_word(a.mail + ((unsigned)n * (unsigned)M + st) * (unsigned)Jmax + lane, tag, nv);
             if (probe && a.probeF) a.probeF[((unsigned)n * M + st) * kMaxJ + lane] = F;
           }
@@ -1302,7 +1306,7 @@ k_epoch(EpochArgs a) {
     buf ^= 1;
   }
 
-  if (c == 0) {
+  if (c == 0 && !a.dry) {
 #pragma unroll 1
     for (int i = tid; i < sumJR; i += T) {
       a.B[i] = Bsm[i];
@@ -1322,10 +1326,42 @@ k_epoch(EpochArgs a) {
   }
 }
 
+// One tensor on the whole grid.
+template <bool BF>
+__global__ void __launch_bounds__(kEpochThreads, 1)
+k_epoch(EpochArgs a) {
+  epoch_body<BF>(a, gridDim.x, blockIdx.x);
+}
+
+// Many independent tensors in one persistent launch: the grid is split into
+// groups of m.group CTAs; group q runs the epochs of the tensors
+// m.order[m.first[q] .. m.first[q+1]) one after the other, each on its own
+// arguments (copied into shared memory) and exchange buffers.
+template <bool BF>
+__global__ void __launch_bounds__(kEpochThreads, 1)
+k_epoch_multi(MultiArgs m) {
+  __shared__ __align__(16) EpochArgs s_a;
+  const int grp = blockIdx.x / m.group, c = blockIdx.x - grp * m.group;
+#pragma unroll 1
+  for (int q = m.first[grp]; q < m.first[grp + 1]; ++q) {
+    const int* src = reinterpret_cast<const int*>(m.items + m.order[q]);
+    int* dst = reinterpret_cast<int*>(&s_a);
+#pragma unroll 1
+    for (int i = threadIdx.x; i < (int)(sizeof(EpochArgs) / 4); i += blockDim.x) dst[i] = src[i];
+    __syncthreads();
+    epoch_body<BF>(s_a, m.group, c);
+    __syncthreads();
+  }
+}
+
 namespace {
 
 const void* kernel_for(int precision) {
   return precision == 1 ? (const void*)k_epoch<true> : (const void*)k_epoch<false>;
+}
+
+const void* multi_kernel_for(int precision) {
+  return precision == 1 ? (const void*)k_epoch_multi<true> : (const void*)k_epoch_multi<false>;
 }
 
 }  // namespace
@@ -1362,6 +1398,25 @@ cudaError_t launch_epoch(const EpochArgs& a, int ctas, size_t smem, cudaStream_t
   EpochArgs copy = a;
   void* args[] = {&copy};
   return cudaLaunchCooperativeKernel(kernel_for(a.precision), dim3(ctas), dim3(kEpochThreads), args, smem, st);
+}
+
+cudaError_t epoch_multi_setup(int precision, size_t smem) {
+  return cudaFuncSetAttribute(multi_kernel_for(precision), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+}
+
+int epoch_multi_max_ctas(int precision, size_t smem) {
+  const void* fn = multi_kernel_for(precision);
+  int dev = 0, sms = 0, per = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fn, kEpochThreads, smem) != cudaSuccess) return 0;
+  return per * sms;
+}
+
+cudaError_t launch_epoch_multi(const MultiArgs& m, int precision, int ctas, size_t smem, cudaStream_t st) {
+  MultiArgs copy = m;
+  void* args[] = {&copy};
+  return cudaLaunchCooperativeKernel(multi_kernel_for(precision), dim3(ctas), dim3(kEpochThreads), args, smem, st);
 }
 
 }  // namespace sgdt

@@ -131,6 +131,7 @@ struct EpochArgs {
   int norm_mode;
   int contraction;       // 0 Kronecker rows x unfolded core; 1 Kruskal form E = B(n) w
   float momentum;        // heavy-ball mu (0 = plain SGD)
+  int dry;               // 1: compute everything, write no parameter (timing runs)
   float* vA[kMaxN];      // factor-row velocities, I_n x Jp_n (momentum != 0)
   float* vB;             // Kruskal-column velocities, concatenated like B (momentum != 0)
   int chunk_max;
@@ -150,6 +151,15 @@ struct EpochArgs {
   float* probeF;         // [N][M][kMaxJ], indexed by the run's first sorted position
 };
 
+// A batched launch: EpochArgs of every tensor (device array), and for each
+// group q of `group` CTAs the tensors order[first[q] .. first[q+1]).
+struct MultiArgs {
+  const EpochArgs* items;
+  const int* order;
+  const int* first;
+  int group;
+};
+
 // Factor-matrix pointers passed to kernels by value.
 struct AParams {
   float* A[kMaxN];
@@ -166,6 +176,9 @@ size_t epoch_smem_bytes(const Geometry& g, int chunk_max, int ctas, int precisio
 cudaError_t epoch_kernel_setup(int precision, size_t smem);
 int epoch_max_ctas(int precision, size_t smem);
 cudaError_t launch_epoch(const EpochArgs& a, int ctas, size_t smem, cudaStream_t st);
+cudaError_t epoch_multi_setup(int precision, size_t smem);
+int epoch_multi_max_ctas(int precision, size_t smem);
+cudaError_t launch_epoch_multi(const MultiArgs& m, int precision, int ctas, size_t smem, cudaStream_t st);
 cudaError_t launch_init_params(const Geometry& g, float* const* A, float* B, int mode, double mu,
                                double sigma, uint64_t seed, cudaStream_t st);
 cudaError_t launch_check_coords(const Geometry& g, const int32_t* coords, int64_t k, int* err,
