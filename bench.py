@@ -54,6 +54,21 @@ def _args():
     p.add_argument("--no-bf16", action="store_true")
     p.add_argument("--no-kruskal", action="store_true")
     p.add_argument("--no-momentum", action="store_true")
+    p.add_argument("--batched", action="store_true",
+                   help="batched workload instead of the default line: 256 independent 3-order tensors "
+                        "(lognormal sizes, J in {4, 8, 16}) in one persistent launch per epoch")
+    p.add_argument("--serve", action="store_true",
+                   help="open-loop serving run (job arrivals + query batches) instead of the epoch bench")
+    p.add_argument("--serve-seconds", type=float, default=60.0)
+    p.add_argument("--serve-rate", type=float, default=50.0, help="job arrivals per second")
+    p.add_argument("--serve-qrate", type=float, default=200.0, help="query batches per second")
+    p.add_argument("--serve-epochs", type=int, default=3)
+    p.add_argument("--serve-pool", type=int, default=48, help="distinct job tensors generated up front")
+    p.add_argument("--serve-budget-gb", type=float, default=120.0)
+    p.add_argument("--serve-batches", type=int, default=32, help="minibatches per job per tick")
+    p.add_argument("--serve-ctas", type=int, default=4, help="CTAs per job (0 = tuned at the first tick)")
+    p.add_argument("--serve-seed", type=int, default=0)
+    p.add_argument("--serve-fp32", action="store_true")
     p.add_argument("--sweep", action="store_true",
                    help="rank sweep of the paper's parameter study instead of the default line: one JSON "
                         "line per (ranks, R_core) point on a fixed rating tensor (--scale, default 0.05)")
@@ -486,12 +501,205 @@ def run_sweep(a):
     return 0
 
 
+def run_batched(a):
+    """Epochs of 256 independent decompositions in one launch per epoch, FP32 and
+    BF16, against the same tensors run one after another on the whole GPU."""
+    import numpy as np
+    import torch
+
+    import __graft_entry__ as ge
+    ge.build()
+    from paper_2012_03550_gb300 import binding as B
+    from paper_2012_03550_gb300 import synth
+
+    t0 = time.time()
+    specs = synth.config4_specs(nnz_scale=a.scale)
+    tensors = [synth.config4_tensor(sp) for sp in specs]
+    gen_s = time.time() - t0
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.Stream(device=dev)
+    M, lr, lam = 256, 1e-3, 1e-3
+    data = []
+    for tt in tensors:
+        c, v = tt.split("train")
+        data.append((torch.from_numpy(c).to(dev), torch.from_numpy(v).to(dev)))
+    n_train = sum(int(d[0].shape[0]) for d in data)
+
+    def contexts(precision):
+        out = []
+        for sp, tt, (dc, dv) in zip(specs, tensors, data):
+            o = B.std_default_options()
+            o.r_core = sp["R"]
+            o.ptr_kind = 1
+            o.precision = precision
+            o.stream = stream.cuda_stream
+            out.append(B.std_create(3, tt.shape, (sp["J"],) * 3, int(dc.shape[0]), dc, dv, o))
+        return out
+
+    lines = {}
+    for precision in (0, 1):
+        ctxs = contexts(precision)
+        bt = B.std_batch_create(ctxs, 0)
+        for _ in range(a.warmup):
+            st = B.std_batch_epoch(bt, lr, lr, lam, lam, M)
+        torch.cuda.synchronize()
+        secs = []
+        for _ in range(a.steps):
+            st = B.std_batch_epoch(bt, lr, lr, lam, lam, M)
+            secs.append(st["seconds"])
+        B.std_batch_destroy(bt)
+        # test RMSE over all members (weighted by test entries)
+        se, cnt = 0.0, 0
+        for ctx, tt in zip(ctxs, tensors):
+            tc, tv = tt.split("test")
+            if tc.shape[0] == 0:
+                continue
+            r = B.std_rmse(ctx, tc.shape[0], torch.from_numpy(tc).to(dev), torch.from_numpy(tv).to(dev))
+            se += r[0] ** 2 * tc.shape[0]
+            cnt += tc.shape[0]
+        # the same epoch with every tensor alone on the whole GPU, one after another
+        seq = None
+        if precision == 0:
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for ctx in ctxs:
+                B.std_sgd_epoch(ctx, lr, lr, lam, lam, M)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            seq = n_train / (e0.elapsed_time(e1) * 1e-3)
+        for ctx in ctxs:
+            B.std_destroy(ctx)
+        ms = 1e3 * sum(secs) / len(secs)
+        lines[precision] = {"value": n_train / (ms * 1e-3), "ms_per_epoch": ms, "ctas_per_tensor": st["ctas_per_tensor"],
+                            "test_rmse": (se / cnt) ** 0.5 if cnt else None, "sequential_value": seq}
+    line = {"metric": "batched SGD_Tucker: sampled nonzeros/s per epoch over all tensors", "value": lines[0]["value"],
+            "unit": "nnz/s", "n_gpus": 1, "steps": a.steps, "warmup": a.warmup,
+            "ms_per_step": lines[0]["ms_per_epoch"], "higher_is_better": True, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"batched-{len(specs)}-tensors-{n_train}", "tensors": len(specs),
+                       "nnz_train": n_train, "minibatch": M, "ranks": "J in {4, 8, 16}, R = min(5, J)",
+                       "ctas_per_tensor": lines[0]["ctas_per_tensor"], "datagen_s": round(gen_s, 1),
+                       "step": "one epoch of every tensor in one persistent launch (samplers and tilers before it)"},
+            "test_rmse": lines[0]["test_rmse"],
+            "one_after_another_value": lines[0]["sequential_value"],
+            "speedup_vs_one_after_another": lines[0]["value"] / lines[0]["sequential_value"],
+            "bf16": {"value": lines[1]["value"], "ms_per_step": lines[1]["ms_per_epoch"],
+                     "ctas_per_tensor": lines[1]["ctas_per_tensor"], "test_rmse": lines[1]["test_rmse"],
+                     "speedup_vs_fp32": lines[1]["value"] / lines[0]["value"]}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_serve(a):
+    """Open-loop serving run: Poisson job arrivals and query batches against the
+    continuous-batching server for a fixed wall time, then a drain."""
+    import numpy as np
+
+    import __graft_entry__ as ge
+    ge.build()
+    from paper_2012_03550_gb300 import serve, synth
+
+    rng = np.random.Generator(np.random.PCG64(np.random.SeedSequence([a.serve_seed, 9])))
+    t0 = time.time()
+    specs = synth.serve_specs(a.serve_pool, seed=a.serve_seed)
+    pool = []
+    for sp in specs:
+        tt = synth.serve_tensor(sp)
+        c, v = tt.split("train")
+        pool.append((sp, c, v))
+    gen_s = time.time() - t0
+    M, lr, lam = 256, 1e-3, 1e-3
+    eng = serve.CudaEngine(precision=0 if a.serve_fp32 else 1, max_query=4096)
+    srv = serve.Server(eng, budget_bytes=int(a.serve_budget_gb * 1e9), batches_per_tick=a.serve_batches,
+                       ctas_per_tensor=a.serve_ctas)
+    # arrival times (s from the start): jobs and query batches, both Poisson
+    jobs_t = np.cumsum(rng.exponential(1.0 / a.serve_rate, size=int(a.serve_rate * a.serve_seconds * 2) + 16))
+    jobs_t = jobs_t[jobs_t < a.serve_seconds]
+    q_t = np.cumsum(rng.exponential(1.0 / a.serve_qrate, size=int(a.serve_qrate * a.serve_seconds * 2) + 16))
+    q_t = q_t[q_t < a.serve_seconds]
+    tables = {}
+
+    def query_coords(shape):
+        k = int(np.exp(rng.uniform(0.0, np.log(4096.0))))
+        cols = []
+        for size in shape:
+            if size not in tables:
+                tables[size] = synth.zipf_table(int(size), 1.1)
+            cols.append(synth.draw_mode_indices(rng, k, int(size), "zipf", 1.1, table=tables[size]))
+        return np.stack(cols, axis=1).astype(np.int32)
+
+    clk = srv.clock
+    start = clk()
+    ij = iq = 0
+    nnz_in_window = 0
+    try:
+        while True:
+            now = clk() - start
+            if now >= a.serve_seconds:
+                break
+            while ij < len(jobs_t) and jobs_t[ij] <= now:
+                sp, c, v = pool[ij % len(pool)]
+                job = serve.Job(shape=sp["shape"], ranks=(sp["J"],) * len(sp["shape"]), coords=c, values=v,
+                                epochs=a.serve_epochs, minibatch=M, lr_a=lr, lr_b=lr, lam_a=lam, lam_b=lam,
+                                r_core=sp["R"], options={"seed_init": 1000 + ij, "seed_sched": 2000 + ij})
+                srv.submit(job, now=start + float(jobs_t[ij]))
+                ij += 1
+            while iq < len(q_t) and q_t[iq] <= now:
+                live = [j for j in srv.running] + list(srv.resident_done.values())
+                if live:
+                    j = live[int(rng.integers(0, len(live)))]
+                    srv.query(j.id, query_coords(j.shape), now=start + float(q_t[iq]))
+                iq += 1
+            if srv.idle():
+                nxt = min(jobs_t[ij] if ij < len(jobs_t) else a.serve_seconds,
+                          q_t[iq] if iq < len(q_t) else a.serve_seconds)
+                time.sleep(max(0.0, min(0.01, nxt - (clk() - start))))
+                continue
+            srv.tick()
+        window_s = clk() - start
+        nnz_in_window = srv.nnz
+        gpu_in_window = srv.gpu_seconds
+        srv.run_until_idle()
+        total_s = clk() - start
+    finally:
+        srv.shutdown()
+    r = srv.report()
+    line = {"metric": "serve p99 job-epoch latency", "value": r["job_epoch_p99_s"], "unit": "s",
+            "higher_is_better": False, "n_gpus": 1, "dtype": "bf16-storage/f32" if not a.serve_fp32 else "f32",
+            "data": "synthetic",
+            "config": {"workload": f"serve-{a.serve_rate:g}jobs_s-{a.serve_seconds:g}s",
+                       "arrivals": f"Poisson {a.serve_rate:g} jobs/s, {a.serve_qrate:g} query batches/s "
+                                   f"(1-4096 Zipf(1.1) coordinates, log-uniform size)",
+                       "jobs": f"orders 3-4, J in {{4,8,16}} (order 4: {{4,8}}), nnz lognormal [1e4, 2e6], "
+                               f"{a.serve_epochs} epochs each, M = {M}, lr = lambda = 1e-3; a pool of "
+                               f"{len(pool)} distinct tensors, each arrival with its own seeds",
+                       "budget_gb": a.serve_budget_gb, "batches_per_tick": a.serve_batches,
+                       "ctas_per_tensor": srv.group, "window_s": round(window_s, 2),
+                       "drain_s": round(total_s - window_s, 2), "datagen_s": round(gen_s, 1)},
+            "job_epoch_p50_s": r["job_epoch_p50_s"], "job_epoch_p99_s": r["job_epoch_p99_s"],
+            "job_p50_s": r["job_p50_s"], "job_p99_s": r["job_p99_s"],
+            "queue_wait_p50_s": r["queue_wait_p50_s"], "queue_wait_p99_s": r["queue_wait_p99_s"],
+            "query_p50_s": r["query_p50_s"], "query_p99_s": r["query_p99_s"],
+            "nnz_per_s_window": nnz_in_window / window_s if window_s > 0 else None,
+            "nnz_per_s_kernel": nnz_in_window / gpu_in_window if gpu_in_window > 0 else None,
+            "jobs_submitted": r["jobs_submitted"], "jobs_done": r["jobs_done"],
+            "jobs_rejected": r["jobs_rejected"], "queries_answered": r["queries_answered"],
+            "ticks": r["ticks"]}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     a = _args()
     if a.impl == "reference":
         return run_reference(a)
     if a.sweep:
         return run_sweep(a)
+    if a.batched:
+        return run_batched(a)
+    if a.serve:
+        return run_serve(a)
     return run_gpu(a)
 
 

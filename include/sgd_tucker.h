@@ -77,13 +77,13 @@ typedef struct {
     void*    stream;      /* cudaStream_t for every kernel and copy; NULL = the legacy stream */
     uint64_t watchdog_ns; /* grid-barrier wait budget in ns; 0 = 2e9 (2 s) */
     uint64_t hbm_budget_bytes; /* cap on the context's device allocations; 0 = none */
-    int32_t  contraction; /* factor-phase E_s = G-hat_(n) S_s^T (Eq. 11, Algorithm 1 lines
-                             19-20): 0 = Kronecker row S_s against the unfolded core (default);
+    int32_t  contraction; /* factor-phase E_s = G-hat_(n) S_s^T (Eq. 11, Algorithm 1's
+                             factor phase): 0 = Kronecker row S_s against the unfolded core (default);
                              1 = the same product through the core's Kruskal form (Eq. 4):
                              E_s = B(n) w_s, w_s[r] = prod_{k != n} <a(k)_{i_k,:}, b(k)_{:,r}>,
                              O(R sum_k J_k) instead of O(J_n prod_{k != n} J_k) per sample */
     float    momentum;    /* heavy-ball momentum mu in [0, 1) for every update of Algorithm 1
-                             (lines 14 and 23): v <- mu v + g, w <- w - lr v with g the
+                             (Kruskal columns and factor rows): v <- mu v + g, w <- w - lr v, g the
                              regularised gradient; 0 = plain SGD (default).  The accelerated SGD
                              the paper names as future work (Sec. 6).  Velocities start at zero,
                              are kept per parameter on the device, and std_set_params resets them */
@@ -130,12 +130,12 @@ typedef struct {
  * rounds, restricted to [0, nnz) by cycle walking, keyed by seed_sched and e);
  * minibatch b is positions [bM, min(bM+M, nnz)), and a short last minibatch
  * uses its own size as M in every normaliser.  Per minibatch:
- *   core phase, n = 1..N, r = 1..R_core in order (Algorithm 1 lines 1-15):
+ *   core phase, n = 1..N, r = 1..R_core in order (Algorithm 1, core phase):
  *     b(n)_r <- b(n)_r - lr_b (V / M + lambda_b b(n)_r),  V of Eq. 15;
  *     lr_b = 0 leaves B unchanged and the core phase is skipped (the paper's
  *     schedule that updates B only in some epochs, Sec. 5.3);
- *   G-hat from B (line 16, Eq. 4);
- *   factor phase, n = 1..N in order (lines 17-25): every row i touched by the
+ *   G-hat from B (Eq. 4);
+ *   factor phase, n = 1..N in order (Algorithm 1): every row i touched by the
  *     minibatch, all rows of a mode reading the state before that mode's update:
  *     a(n)_i <- a(n)_i - lr_a (F / M_i + lambda_a a(n)_i),  F of Eq. 18,
  *     M_i = M (norm_mode 0) or the row's sample count (norm_mode 1).
@@ -148,9 +148,9 @@ int std_sgd_epoch(std_ctx* ctx, float lr_a, float lr_b, float lambda_a, float la
 /* Gradient probe of std_sgd_batches: host buffers filled for the first
  * minibatch of the range (any member may be NULL). */
 typedef struct {
-    float*   core_V;    /* [N][R_core][STD_MAX_RANK]: V of Algorithm 1 line 13 (the bracket of
+    float*   core_V;    /* [N][R_core][STD_MAX_RANK]: V of Algorithm 1's core phase (the bracket of
                            Eq. 15) for each mode n and column r, in update order */
-    float*   factor_F;  /* [N][M][STD_MAX_RANK]: F of Algorithm 1 line 22 (the bracket of
+    float*   factor_F;  /* [N][M][STD_MAX_RANK]: F of Algorithm 1's factor phase (the bracket of
                            Eq. 18) for each mode n and each touched row, rows ascending */
     int64_t* nseg;      /* [N]: touched rows per mode */
 } std_probe;
@@ -229,12 +229,38 @@ typedef struct {
     int32_t ctas_per_tensor;  /* the group size used */
 } std_batch_stats;
 
-/* One epoch of every tensor of the batch (same hyperparameters and minibatch
- * size for all; the definition of an epoch is std_sgd_epoch's).  Every
- * context's epoch counter advances.  Errors: STD_EINVAL, STD_EUNSUPPORTED,
+/* Up to max_batches minibatches of every tensor of the batch, each tensor
+ * continuing its epoch in progress (a context keeps its position between
+ * calls, so tensors can join and leave between steps); a tensor that
+ * completes its epoch advances its epoch counter and starts the next epoch at
+ * the next step.  Same hyperparameters and minibatch size for all; the
+ * minibatch sequence is std_sgd_epoch's.  std_sgd_epoch refuses a context
+ * whose epoch is in progress.  Errors: STD_EINVAL, STD_EUNSUPPORTED,
  * STD_ENOMEM, STD_ECUDA, STD_ETIMEOUT. */
+int std_batch_step(std_batch* batch, float lr_a, float lr_b, float lambda_a, float lambda_b,
+                   int32_t minibatch, int64_t max_batches, std_batch_stats* out);
+
+/* std_batch_step without a limit: every tensor finishes its current epoch. */
 int std_batch_epoch(std_batch* batch, float lr_a, float lr_b, float lambda_a, float lambda_b,
                     int32_t minibatch, std_batch_stats* out);
+
+/* The context's epoch counter and the next minibatch of its epoch in
+ * progress (0 at an epoch boundary). */
+int std_progress(const std_ctx* ctx, int64_t* epoch, int64_t* next_batch);
+
+/* Allocate now everything that batched steps at this minibatch size and a
+ * group of ctas_per_tensor CTAs (or fewer) need: the current epoch's sample
+ * schedule and the exchange scratch; for a host-pointer context also the
+ * staging of std_predict / std_rmse calls of up to max_query coordinates.
+ * Later calls of that shape allocate nothing, so std_device_bytes then gives
+ * the context's whole footprint and a host-side admission rule can rely on
+ * it.  Counted against hbm_budget_bytes.  Errors: STD_EINVAL,
+ * STD_EUNSUPPORTED, STD_ENOMEM, STD_ECUDA. */
+int std_reserve(std_ctx* ctx, int32_t minibatch, int32_t ctas_per_tensor, int64_t max_query);
+
+/* Bytes of device memory the context holds (COO, parameters, schedule,
+ * scratch). */
+int std_device_bytes(const std_ctx* ctx, uint64_t* bytes);
 
 /* Release the batch (not its contexts; NULL is a no-op). */
 int std_batch_destroy(std_batch* batch);

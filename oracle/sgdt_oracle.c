@@ -257,9 +257,9 @@ static int64_t orc_lin(const orc_model *md, const int *j)
 }
 
 /* ------------------------------------------------------------------------ */
-/* Core phase, Algorithm 1 lines 1-15 for one mode n.                         */
+/* Core phase of Algorithm 1 for one mode n.                                  */
 /*                                                                            */
-/* W_r (M x J_n) = H_Psi O_r (lines 2-6).  Literal form: H_Psi row s is       */
+/* W_r (M x J_n) = H_Psi O_r.  Literal form: H_Psi row s is                   */
 /* Vec_n of the outer product of the sample's factor rows (Eq. 5, Def. 2:     */
 /* H_s[c*J_n + j] = a_n[j] * S_s[c]); O_r stacks q_{c,r} U (Eq. 7) with       */
 /* Q(n) = B(N) (.) ... (.) B(n+1) (.) B(n-1) (.) ... (.) B(1) (Eq. 5).        */
@@ -295,7 +295,7 @@ static int orc_build_W(const orc_model *md, int n, int64_t m, const int32_t *coo
     double *O = (double *)malloc((size_t)(P * Jn) * sizeof(double));
     if (!H || !Q || !O) { free(H); free(Q); free(O); return ORC_ENOMEM; }
     int jd[ORC_MAXN];
-    for (int64_t s = 0; s < m; ++s) {           /* line 2: H_Psi */
+    for (int64_t s = 0; s < m; ++s) {           /* H_Psi */
         const int32_t *co = coords + s * N;
         for (int64_t c = 0; c < Pn; ++c) {
             orc_unfold_digits(md, n, c, jd);
@@ -319,11 +319,11 @@ static int orc_build_W(const orc_model *md, int n, int64_t m, const int32_t *coo
             Q[c * R + r] = q;
         }
     }
-    for (int r = 0; r < R; ++r) {               /* lines 3-6 */
-        memset(O, 0, (size_t)(P * Jn) * sizeof(double));   /* line 4: O_r by Eq. 7 */
+    for (int r = 0; r < R; ++r) {               /* W_r for every column r */
+        memset(O, 0, (size_t)(P * Jn) * sizeof(double));   /* O_r by Eq. 7 */
         for (int64_t c = 0; c < Pn; ++c)
             for (int j = 0; j < Jn; ++j) O[(c * Jn + j) * Jn + j] = Q[c * R + r];
-        for (int64_t s = 0; s < m; ++s)          /* line 5: W_r = H_Psi O_r */
+        for (int64_t s = 0; s < m; ++s)          /* W_r = H_Psi O_r */
             for (int j = 0; j < Jn; ++j) {
                 double acc = 0.0;
                 for (int64_t k = 0; k < P; ++k) acc += H[s * P + k] * O[k * Jn + j];
@@ -334,15 +334,15 @@ static int orc_build_W(const orc_model *md, int n, int64_t m, const int32_t *coo
     return ORC_OK;
 }
 
-/* V for block (n, rc) at the current B (Algorithm 1 lines 8-13):
+/* V for block (n, rc) at the current B (Algorithm 1, core phase, Eq. 15):
  *   x-hat = x - sum_{r != rc} W_r b_r;  C = W_rc^T W_rc;  V = -W_rc^T x-hat + C b_rc.
  * This V is the bracket of Eq. 15, i.e. grad = V / M + lambda_B b_rc. */
 static void orc_core_V(const orc_model *md, int n, int rc, int64_t m, const double *x,
                        const double *W, double *xhat, double *C, double *V)
 {
     const int R = md->R, Jn = md->J[n];
-    for (int64_t s = 0; s < m; ++s) xhat[s] = x[s];                      /* line 8 */
-    for (int r = 0; r < R; ++r) {                                          /* lines 9-11 */
+    for (int64_t s = 0; s < m; ++s) xhat[s] = x[s];                      /* x-hat starts at x */
+    for (int r = 0; r < R; ++r) {                                          /* minus the other columns */
         if (r == rc) continue;
         for (int64_t s = 0; s < m; ++s) {
             double wb = 0.0;
@@ -351,14 +351,14 @@ static void orc_core_V(const orc_model *md, int n, int rc, int64_t m, const doub
             xhat[s] -= wb;
         }
     }
-    for (int a = 0; a < Jn; ++a)                                           /* line 12 */
+    for (int a = 0; a < Jn; ++a)                                           /* Gram W_rc^T W_rc */
         for (int b = 0; b < Jn; ++b) {
             double acc = 0.0;
             for (int64_t s = 0; s < m; ++s)
                 acc += W[((int64_t)rc * m + s) * Jn + a] * W[((int64_t)rc * m + s) * Jn + b];
             C[a * Jn + b] = acc;
         }
-    for (int a = 0; a < Jn; ++a) {                                         /* line 13 */
+    for (int a = 0; a < Jn; ++a) {                                         /* V */
         double acc = 0.0;
         for (int64_t s = 0; s < m; ++s) acc -= W[((int64_t)rc * m + s) * Jn + a] * xhat[s];
         for (int b = 0; b < Jn; ++b) acc += C[a * Jn + b] * md->B[n][(int64_t)b * R + rc];
@@ -384,10 +384,10 @@ static double orc_sgd_momentum(double w, double *v, double grad, double M, doubl
 }
 
 /* ------------------------------------------------------------------------ */
-/* Factor phase, Algorithm 1 lines 17-25 for one mode n and one row i_n      */
+/* Factor phase of Algorithm 1 for one mode n and one row i_n                */
 /* whose samples are sample_ids[0..cnt).                                     */
-/*   S rows (line 19, Eq. 10), E = G_(n) S^T (line 20, Eq. 11),               */
-/*   C = E E^T (line 21), F = -X E^T + a C (line 22).                          */
+/*   S rows (Eq. 10), E = G_(n) S^T (Eq. 11),                                 */
+/*   C = E E^T, F = -X E^T + a C.                                             */
 /* F is the bracket of Eq. 18, i.e. grad = F / M + lambda_A a.                */
 /* ------------------------------------------------------------------------ */
 static void orc_factor_F(const orc_model *md, int n, const int32_t *coords, const double *x,
@@ -402,18 +402,18 @@ static void orc_factor_F(const orc_model *md, int n, const int32_t *coords, cons
         for (int j = 0; j < Jn; ++j) E[q * Jn + j] = 0.0;
         for (int64_t c = 0; c < Pn; ++c) {
             orc_unfold_digits(md, n, c, jd);
-            double Sc = 1.0;                                        /* line 19 */
+            double Sc = 1.0;                                        /* S (Eq. 10) */
             for (int k = 0; k < N; ++k) {
                 if (k == n) continue;
                 Sc *= md->A[k][(int64_t)co[k] * md->J[k] + jd[k]];
             }
-            for (int j = 0; j < Jn; ++j) {                           /* line 20 */
+            for (int j = 0; j < Jn; ++j) {                           /* E (Eq. 11) */
                 jd[n] = j;
                 E[q * Jn + j] += md->G[orc_lin(md, jd)] * Sc;
             }
         }
     }
-    for (int a = 0; a < Jn; ++a)                                     /* line 21 */
+    for (int a = 0; a < Jn; ++a)                                     /* C = E E^T */
         for (int b = 0; b < Jn; ++b) {
             double acc = 0.0;
             for (int64_t q = 0; q < cnt; ++q) acc += E[q * Jn + a] * E[q * Jn + b];
@@ -421,7 +421,7 @@ static void orc_factor_F(const orc_model *md, int n, const int32_t *coords, cons
         }
     const int32_t *co0 = coords + (int64_t)sample_ids[0] * N;
     const double *ai = md->A[n] + (int64_t)co0[n] * Jn;
-    for (int b = 0; b < Jn; ++b) {                                   /* line 22 */
+    for (int b = 0; b < Jn; ++b) {                                   /* F */
         double acc = 0.0;
         for (int64_t q = 0; q < cnt; ++q) acc -= x[sample_ids[q]] * E[q * Jn + b];
         for (int a = 0; a < Jn; ++a) acc += ai[a] * C[a * Jn + b];
@@ -552,9 +552,9 @@ int orc_factor_gradient(int N, const int64_t *I, const int32_t *J, int R, double
  * One SGD_Tucker minibatch step, Algorithm 1, on the m samples coords/values
  * (in minibatch order).  Updates A and B in place and leaves G-hat built from
  * the new B.  If probe_V is non-NULL it receives, for every mode n and r_core,
- * the line-13 vector V (layout [n][r][Jmax]); if probe_F is non-NULL it
+ * the core-phase bracket V of Eq. 15 (layout [n][r][Jmax]); if probe_F is non-NULL it
  * receives, for every mode n and every segment u of equal i_n in ascending
- * i_n, the line-22 vector F (layout [n][u][Jmax], u < m), with the number of
+ * i_n, the factor-phase bracket F of Eq. 18 (layout [n][u][Jmax], u < m), with the number of
  * segments per mode in probe_nseg[n].
  */
 int orc_step_momentum(int N, const int64_t *I, const int32_t *J, int R, double **A, double **B, double *G,
@@ -575,7 +575,7 @@ int orc_step(int N, const int64_t *I, const int32_t *J, int R, double **A, doubl
 /*
  * orc_step with heavy-ball momentum: VA[n] (I_n x J_n) and VB[n] (J_n x R)
  * hold the velocities of the factor rows and of the Kruskal columns; every
- * update of Algorithm 1 (lines 14 and 23) goes through orc_sgd_momentum.  A row
+ * update of Algorithm 1 (Kruskal columns and factor rows) goes through orc_sgd_momentum.  A row
  * untouched by the minibatch keeps its velocity (as it keeps its value).
  * VA = VB = NULL gives plain SGD.
  */
@@ -604,16 +604,16 @@ int orc_step_momentum(int N, const int64_t *I, const int32_t *J, int R, double *
     if (!x || !W || !xh || !C || !V || !E || !F || !keys || !order || !seg) { rc = ORC_ENOMEM; goto done; }
     for (int64_t s = 0; s < m; ++s) x[s] = values[s];
 
-    /* Core phase: lines 1-15. */
+    /* Core phase. */
     for (int n = 0; n < N; ++n) {
         const int Jn = md.J[n];
-        rc = orc_build_W(&md, n, m, coords, literal, W);             /* lines 2-6 */
+        rc = orc_build_W(&md, n, m, coords, literal, W);             /* W_r, Eq. 7 */
         if (rc) goto done;
-        for (int r = 0; r < R; ++r) {                                 /* lines 7-14 */
+        for (int r = 0; r < R; ++r) {                                 /* cyclic over r */
             orc_core_V(&md, n, r, m, x, W, xh, C, V);
             if (probe_V)
                 for (int j = 0; j < Jn; ++j) probe_V[((int64_t)n * R + r) * Jmax + j] = V[j];
-            for (int j = 0; j < Jn; ++j) {                            /* line 14 */
+            for (int j = 0; j < Jn; ++j) {                            /* b_r update */
                 double *b = &md.B[n][(int64_t)j * R + r];
                 if (VB)
                     *b = orc_sgd_momentum(*b, &VB[n][(int64_t)j * R + r], V[j], (double)m, lambda_b, gamma_b, mu);
@@ -622,16 +622,16 @@ int orc_step_momentum(int N, const int64_t *I, const int32_t *J, int R, double *
             }
         }
     }
-    orc_core_from_B(&md);                                             /* line 16 */
+    orc_core_from_B(&md);                                             /* Eq. 4 */
 
-    /* Factor phase: lines 17-25. */
+    /* Factor phase. */
     for (int n = 0; n < N; ++n) {
         const int Jn = md.J[n];
         for (int64_t s = 0; s < m; ++s) keys[s] = coords[s * N + n];
         int64_t U = orc_stable_order(m, keys, order, seg);
         if (U < 0) { rc = ORC_ENOMEM; goto done; }
         if (probe_nseg) probe_nseg[n] = U;
-        for (int64_t u = 0; u < U; ++u) {                             /* lines 18-24 */
+        for (int64_t u = 0; u < U; ++u) {                             /* each touched row */
             int64_t cnt = seg[u + 1] - seg[u];
             const int32_t *ids = order + seg[u];
             orc_factor_F(&md, n, coords, x, ids, cnt, E, C, F);
@@ -640,7 +640,7 @@ int orc_step_momentum(int N, const int64_t *I, const int32_t *J, int R, double *
             double denom = norm_mode == 1 ? (double)cnt : (double)m;
             const int64_t row = coords[(int64_t)ids[0] * N + n];
             double *a = md.A[n] + row * Jn;
-            for (int j = 0; j < Jn; ++j) {                            /* line 23 */
+            for (int j = 0; j < Jn; ++j) {                            /* row update */
                 if (VA)
                     a[j] = orc_sgd_momentum(a[j], &VA[n][row * Jn + j], F[j], denom, lambda_a, gamma_a, mu);
                 else

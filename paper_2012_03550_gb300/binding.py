@@ -113,6 +113,11 @@ SIGNATURES = {
     "std_batch_epoch": (ctypes.c_int, [_P, ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_float,
                                        ctypes.c_int32, _P]),
     "std_batch_destroy": (ctypes.c_int, [_P]),
+    "std_batch_step": (ctypes.c_int, [_P, ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_float,
+                                      ctypes.c_int32, ctypes.c_int64, _P]),
+    "std_progress": (ctypes.c_int, [_P, _P, _P]),
+    "std_reserve": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int64]),
+    "std_device_bytes": (ctypes.c_int, [_P, _P]),
 }
 
 
@@ -324,6 +329,15 @@ class Tucker:
         ep = std_get_params(self.ctx, A, B, core)
         return A, B, core, ep
 
+    def progress(self):
+        return std_progress(self.ctx)
+
+    def reserve(self, minibatch, ctas_per_tensor, max_query=0):
+        std_reserve(self.ctx, minibatch, ctas_per_tensor, max_query)
+
+    def device_bytes(self):
+        return std_device_bytes(self.ctx)
+
     def set_params(self, A=None, B=None, epoch=-1):
         A = [np.ascontiguousarray(a, dtype=np.float32) for a in A] if A is not None else None
         B = [np.ascontiguousarray(b, dtype=np.float32) for b in B] if B is not None else None
@@ -344,6 +358,30 @@ def std_batch_epoch(batch, lr_a, lr_b, lambda_a, lambda_b, minibatch):
     return {f: getattr(st, f) for f, _ in std_batch_stats._fields_}
 
 
+def std_batch_step(batch, lr_a, lr_b, lambda_a, lambda_b, minibatch, max_batches):
+    st = std_batch_stats()
+    _check(lib().std_batch_step(batch, lr_a, lr_b, lambda_a, lambda_b, int(minibatch), int(max_batches),
+                                ctypes.byref(st)))
+    return {f: getattr(st, f) for f, _ in std_batch_stats._fields_}
+
+
+def std_progress(ctx):
+    e = ctypes.c_int64()
+    b = ctypes.c_int64()
+    _check(lib().std_progress(ctx, ctypes.byref(e), ctypes.byref(b)))
+    return e.value, b.value
+
+
+def std_reserve(ctx, minibatch, ctas_per_tensor, max_query=0):
+    _check(lib().std_reserve(ctx, int(minibatch), int(ctas_per_tensor), int(max_query)))
+
+
+def std_device_bytes(ctx):
+    b = ctypes.c_uint64()
+    _check(lib().std_device_bytes(ctx, ctypes.byref(b)))
+    return b.value
+
+
 def std_batch_destroy(batch):
     _check(lib().std_batch_destroy(batch))
 
@@ -357,6 +395,9 @@ class Batch:
 
     def epoch(self, lr_a, lr_b, lam_a, lam_b, minibatch):
         return std_batch_epoch(self.ptr, lr_a, lr_b, lam_a, lam_b, minibatch)
+
+    def step(self, lr_a, lr_b, lam_a, lam_b, minibatch, max_batches):
+        return std_batch_step(self.ptr, lr_a, lr_b, lam_a, lam_b, minibatch, max_batches)
 
     def close(self):
         if self.ptr is not None:

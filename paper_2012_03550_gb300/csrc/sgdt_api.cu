@@ -3,6 +3,8 @@
 #include <cmath>
 #include <cstdio>
 #include <algorithm>
+#include <climits>
+#include <cstdint>
 #include <cstring>
 #include <string>
 #include <utility>
@@ -81,6 +83,8 @@ struct std_ctx {
   int rpart_blocks = 0;
   double* result = nullptr;
   int64_t epoch = 0;
+  int64_t cursor = 0;               // next minibatch of the epoch in progress (batched steps); 0 = at a boundary
+  int32_t cursor_M = 0;             // minibatch size of that epoch
   size_t allocated = 0;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr, evm = nullptr;
 };
@@ -545,6 +549,8 @@ int std_sgd_epoch(std_ctx* c, float lr_a, float lr_b, float lambda_a, float lamb
   if (!c) return set_error(STD_EINVAL, "context is NULL");
   int rc = check_hyper(lr_a, lr_b, lambda_a, lambda_b, minibatch);
   if (rc) return rc;
+  if (c->cursor != 0)
+    return set_error(STD_EINVAL, "an epoch is in progress on this context (batched steps); finish it with std_batch_step");
   const int64_t nb = (c->nnz + minibatch - 1) / minibatch;
   // the epoch time covers the sampler/tiler and the update kernel
   STD_CUDA(cudaEventRecord(c->ev0, c->stream), "event");
@@ -743,7 +749,10 @@ int std_set_params(std_ctx* c, const float* const* A, const float* const* B, int
              "velocity reset");
   }
   STD_CUDA(cudaStreamSynchronize(c->stream), "set params sync");
-  if (epoch >= 0) c->epoch = epoch;
+  if (epoch >= 0) {
+    c->epoch = epoch;
+    c->cursor = 0;
+  }
   return STD_OK;
 }
 
@@ -780,10 +789,10 @@ size_t batch_smem(std_ctx* c, int M, int G) {
   return sm > 227 * 1024 ? 0 : sm;
 }
 
-// One launch of minibatches [b0, min(b1, nb_t)) of every tensor at group size
-// G; dry = no parameter writes (timing runs of the tuner).
-int batch_launch(std_batch* bt, float lr_a, float lr_b, float lam_a, float lam_b, int32_t M, int64_t b0,
-                 int64_t b1, int G, bool dry) {
+// One launch of minibatches range[t] = [b0, b1) of every tensor t at group
+// size G; dry = no parameter writes (timing runs of the tuner).
+int batch_launch(std_batch* bt, float lr_a, float lr_b, float lam_a, float lam_b, int32_t M,
+                 const std::vector<std::pair<int64_t, int64_t>>& range, int G, bool dry) {
   const int T = (int)bt->ctxs.size();
   size_t smem = 0;
   bt->h_items.resize(T);
@@ -798,7 +807,8 @@ int batch_launch(std_batch* bt, float lr_a, float lr_b, float lam_a, float lam_b
     rc = ensure_scratch(c, G, payload_floats(c->g), M);
     if (rc) return rc;
     const int64_t nb = (c->nnz + M - 1) / M;
-    const int64_t e0 = b0 < nb ? b0 : nb, e1 = b1 < nb ? b1 : nb;
+    const int64_t e0 = range[t].first < nb ? range[t].first : nb;
+    const int64_t e1 = range[t].second < nb ? range[t].second : nb;
     uint32_t tag_base = 0;
     rc = reserve_tags(c, e1 - e0, &tag_base);
     if (rc) return rc;
@@ -924,22 +934,33 @@ int std_batch_destroy(std_batch* bt) {
   return STD_OK;
 }
 
-int std_batch_epoch(std_batch* bt, float lr_a, float lr_b, float lambda_a, float lambda_b, int32_t minibatch,
-                    std_batch_stats* out) {
+int std_batch_step(std_batch* bt, float lr_a, float lr_b, float lambda_a, float lambda_b, int32_t minibatch,
+                   int64_t max_batches, std_batch_stats* out) {
   if (!bt) return set_error(STD_EINVAL, "batch is NULL");
   int rc = check_hyper(lr_a, lr_b, lambda_a, lambda_b, minibatch);
   if (rc) return rc;
+  if (max_batches < 1) return set_error(STD_EINVAL, "max_batches must be >= 1");
+  for (std_ctx* c : bt->ctxs)
+    if (c->cursor > 0 && c->cursor_M != minibatch)
+      return set_error(STD_EINVAL, "a context has an epoch in progress with another minibatch size");
   if (!bt->tuned) {
     // autotuner: each group size that fits times a dry run (no parameter
-    // writes) of the first minibatches of every tensor; the fastest wins
+    // writes) of 3% of every tensor's minibatches from its position, so that
+    // the trial has the epoch's mix of long and short tensors; the fastest wins
     float best = -1.f;
     int best_g = 0;
+    std::vector<std::pair<int64_t, int64_t>> trial;
+    for (std_ctx* c : bt->ctxs) {
+      const int64_t nb = (c->nnz + minibatch - 1) / minibatch;
+      const int64_t k = (int64_t)std::ceil(0.03 * (double)nb);
+      trial.push_back({c->cursor, c->cursor + (k < 1 ? 1 : k)});
+    }
     for (int G = 1; G <= 32; G *= 2) {
       bool fits = true;
       for (std_ctx* c : bt->ctxs)
         if (batch_smem(c, minibatch, G) == 0) fits = false;
       if (!fits) continue;
-      rc = batch_launch(bt, lr_a, lr_b, lambda_a, lambda_b, minibatch, 0, 4, G, true);
+      rc = batch_launch(bt, lr_a, lr_b, lambda_a, lambda_b, minibatch, trial, G, true);
       if (rc == STD_EUNSUPPORTED) continue;
       if (rc) return rc;
       float ms = 0.f;
@@ -954,15 +975,27 @@ int std_batch_epoch(std_batch* bt, float lr_a, float lr_b, float lambda_a, float
     bt->tuned = true;
   }
   STD_CUDA(cudaEventRecord(bt->ev0, bt->stream), "event");
-  int64_t nb_max = 0, nnz = 0;
+  std::vector<std::pair<int64_t, int64_t>> range;
+  int64_t nnz = 0;
   for (std_ctx* c : bt->ctxs) {
     const int64_t nb = (c->nnz + minibatch - 1) / minibatch;
-    nb_max = nb > nb_max ? nb : nb_max;
-    nnz += c->nnz;
+    const int64_t e1 = (max_batches >= nb - c->cursor) ? nb : c->cursor + max_batches;
+    range.push_back({c->cursor, e1});
+    const int64_t t1 = e1 * (int64_t)minibatch < c->nnz ? e1 * (int64_t)minibatch : c->nnz;
+    nnz += t1 - c->cursor * (int64_t)minibatch;
   }
-  rc = batch_launch(bt, lr_a, lr_b, lambda_a, lambda_b, minibatch, 0, nb_max, bt->group, false);
+  rc = batch_launch(bt, lr_a, lr_b, lambda_a, lambda_b, minibatch, range, bt->group, false);
   if (rc) return rc;
-  for (std_ctx* c : bt->ctxs) c->epoch += 1;
+  for (size_t t = 0; t < bt->ctxs.size(); ++t) {
+    std_ctx* c = bt->ctxs[t];
+    const int64_t nb = (c->nnz + minibatch - 1) / minibatch;
+    c->cursor = range[t].second;
+    c->cursor_M = minibatch;
+    if (c->cursor >= nb) {
+      c->cursor = 0;
+      c->epoch += 1;
+    }
+  }
   float ms = 0.f, ms_upd = 0.f;
   STD_CUDA(cudaEventElapsedTime(&ms, bt->ev0, bt->ev1), "event time");
   STD_CUDA(cudaEventElapsedTime(&ms_upd, bt->evm, bt->ev1), "event time");
@@ -974,6 +1007,42 @@ int std_batch_epoch(std_batch* bt, float lr_a, float lr_b, float lambda_a, float
     out->tensors = (int32_t)bt->ctxs.size();
     out->ctas_per_tensor = bt->group;
   }
+  return STD_OK;
+}
+
+int std_batch_epoch(std_batch* bt, float lr_a, float lr_b, float lambda_a, float lambda_b, int32_t minibatch,
+                    std_batch_stats* out) {
+  return std_batch_step(bt, lr_a, lr_b, lambda_a, lambda_b, minibatch, INT64_MAX, out);
+}
+
+int std_reserve(std_ctx* c, int32_t minibatch, int32_t ctas_per_tensor, int64_t max_query) {
+  if (!c) return set_error(STD_EINVAL, "context is NULL");
+  if (minibatch < 1) return set_error(STD_EINVAL, "minibatch must be >= 1");
+  if (minibatch > STD_MAX_MINIBATCH) return set_error(STD_EUNSUPPORTED, "minibatch exceeds STD_MAX_MINIBATCH");
+  if (ctas_per_tensor < 1 || ctas_per_tensor > kMaxEpochCtas)
+    return set_error(STD_EINVAL, "ctas_per_tensor must be in [1, 256]");
+  if (c->cursor > 0 && c->cursor_M != minibatch)
+    return set_error(STD_EINVAL, "an epoch is in progress with another minibatch size");
+  if (max_query < 0) return set_error(STD_EINVAL, "max_query must be >= 0");
+  int rc = ensure_schedule(c, minibatch);
+  if (!rc) rc = ensure_scratch(c, ctas_per_tensor, payload_floats(c->g), minibatch);
+  if (!rc && c->opt.ptr_kind == 0 && max_query > 0)
+    rc = ensure_stage(c, (size_t)max_query * c->g.N * 4 + (size_t)max_query * 4 + 16);
+  if (rc) return rc;
+  STD_CUDA(cudaStreamSynchronize(c->stream), "reserve sync");
+  return STD_OK;
+}
+
+int std_device_bytes(const std_ctx* c, uint64_t* bytes) {
+  if (!c || !bytes) return set_error(STD_EINVAL, "context or output is NULL");
+  *bytes = (uint64_t)c->allocated;
+  return STD_OK;
+}
+
+int std_progress(const std_ctx* c, int64_t* epoch, int64_t* next_batch) {
+  if (!c) return set_error(STD_EINVAL, "context is NULL");
+  if (epoch) *epoch = c->epoch;
+  if (next_batch) *next_batch = c->cursor;
   return STD_OK;
 }
 

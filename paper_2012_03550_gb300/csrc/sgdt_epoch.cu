@@ -19,34 +19,34 @@
 //    shared memory), divisions by launch constants through multiply-high,
 //    operand rows built once per minibatch, and register-tiled products.
 //
-// Core phase (Algorithm 1 lines 1-15; Eq. 7, Eq. 15).  A is fixed during the
+// Core phase (Algorithm 1, core phase; Eq. 7, Eq. 15).  A is fixed during the
 // phase: each CTA gathers its samples' N factor rows once and keeps
 //   p[s][k][r] = <a_k(s), b(k)_r>.
-// For mode n the line-5 product W_r = H O_r has the closed form
+// For mode n the product W_r = H O_r has the closed form
 // W_r[s] = w[s][r] a_n(s), w[s][r] = prod_{k != n} p[s][k][r] (mixed-product
-// property of the Kronecker product, Eq. 7).  The line-13 vector of column r
+// property of the Kronecker product, Eq. 7).  The gradient bracket V of column r
 // after columns r' < r moved by Delta_{r'} is
 //   V_r = g_r + sum_{r' < r} C_{r r'} Delta_{r'},
 //   g_r = sum_s e_s w[s][r] a_n(s),  C_{r r'} = sum_s w[s][r] w[s][r'] a_n(s) a_n(s)^T,
 //   e_s = sum_r w[s][r] p[s][n][r] - x_s at the start of the mode,
-// the exact algebra of lines 8-13 (the line 8-11 residual is e_s plus the
-// moves already made).  Each C_{r r'} is symmetric, so the payload is g plus
+// the exact algebra of Algorithm 1's residual and Gram steps (the residual
+// against the other columns is e_s plus the moves already made).  Each C_{r r'} is symmetric, so the payload is g plus
 // the upper triangles of the blocks r' < r.  Reduction over the CTAs in two
 // tagged hops: every CTA publishes its partial payload; CTA c sums a slice of
 // it over all CTAs in a fixed order and pushes the sums into every CTA's own
 // copy of the payload (so each CTA then polls lines nobody else reads); every
-// CTA replays the R cyclic SGD steps (line 14) on identical numbers, so all
+// CTA replays the R cyclic SGD steps on identical numbers, so all
 // CTAs hold bit-identical B without a broadcast.
 //
-// Core rebuild (line 16, Eq. 4) is done redundantly by every CTA.
+// Core rebuild (Eq. 4) is done redundantly by every CTA.
 //
-// Factor phase (lines 17-25; Eqs. 10, 11, 18), mode after mode, samples
+// Factor phase (Algorithm 1, factor phase; Eqs. 10, 11, 18), mode after mode, samples
 // sorted by i_n (tiler) so that each row's samples form one run.  Per chunk:
 // the Kronecker rows S_s (Eq. 10, Def. 1 column order) are built in shared
 // memory and contracted with the unfolded core, E_s = G_(n) S_s^T; the
 // residual e_s = a_n . E_s - x_s is reduced across each sample's lanes with
-// shuffles, and the row sums F = sum_s e_s E_s (the row's -X E^T + a E E^T of
-// line 22) are summed per run in sorted order.  A run inside the chunk is
+// shuffles, and the row sums F = sum_s e_s E_s (the row's -X E^T + a E E^T,
+// the bracket of Eq. 18) are summed per run in sorted order.  A run inside the chunk is
 // applied by this CTA.  A run that continues from an earlier chunk is
 // published as a tagged piece; the CTA where the run starts polls the pieces,
 // adds them in chunk order and applies the update, so no floating-point
@@ -872,7 +872,7 @@ __device__ __forceinline__ void epoch_body(const EpochArgs& a, const int G, cons
               for (int j = Jn; j < Jq; ++j) redsm[Kq + i * Jq + j] = 0.f;
         }
         if (!__syncthreads_and(ok)) return;
-        // Cyclic SGD over the columns of B(n) (lines 7-14) as a block forward
+        // Cyclic SGD over the columns of B(n) (Algorithm 1's loop over r) as a block forward
         // substitution: warp w keeps V_w (lane j) and V_{w+16}; at step r the
         // owner of column r moves it, and every later V_r'' gains C_{r'' r}
         // Delta_r (Delta double-buffered by step parity, one named barrier per
@@ -1270,7 +1270,7 @@ __device__ __forceinline__ void epoch_body(const EpochArgs& a, const int G, cons
         pieces_sm[i] = val_of(settle(p, get_word(p), tag, ok, a));
       }
       if (!__syncthreads_and(ok)) return;
-      // the line-23 update of every run that starts in this chunk (pieces of
+      // the factor-row update of every run that starts in this chunk (pieces of
       // a continuing run added in chunk order), warp per run, lane j
 #pragma unroll 1
       for (int h = warp; h < nheads; h += nwarps)

@@ -346,6 +346,31 @@ def config4_tensor(spec) -> SparseTensor:
                        spec["seed"])
 
 
+def serve_specs(count: int, seed: int = 0):
+    """Job shapes of the serving workload: the batched workload's size
+    distribution with order 3 or 4 (even odds).  Mode sizes lognormal(ln 7000,
+    1) clipped to [1e3, 5e4], nonzeros lognormal(ln 1.5e5, 1) clipped to
+    [1e4, 2e6], J from {4, 8, 16} for order 3 and from {4, 8} for order 4
+    (16^4 core entries exceed the library's core limit), R = min(5, J)."""
+    rng = np.random.Generator(np.random.PCG64(np.random.SeedSequence([seed, 5])))
+    specs = []
+    for t in range(count):
+        order = int(rng.choice([3, 4]))
+        dims = np.clip(np.exp(rng.normal(math.log(7000.0), 1.0, size=order)), 1e3, 5e4).astype(np.int64)
+        nnz = float(np.clip(math.exp(rng.normal(math.log(1.5e5), 1.0)), 1e4, 2e6))
+        nnz = int(min(nnz, 0.4 * float(np.prod(dims.astype(np.float64)))))
+        J = int(rng.choice([4, 8, 16] if order == 3 else [4, 8]))
+        specs.append(dict(shape=tuple(int(d) for d in dims), nnz=max(nnz, 64), J=J, R=min(5, J),
+                          seed=int(seed * 100003 + t + 7)))
+    return specs
+
+
+def serve_tensor(spec) -> SparseTensor:
+    J = spec["J"]
+    N = len(spec["shape"])
+    return make_tensor(spec["shape"], spec["nnz"], [("uniform",)] * N, (J,) * N, 0.05, 0.1, spec["seed"])
+
+
 # ---------------------------------------------------------------------------
 # Initial parameters.  The paper initialises everything from N(0.5, 0.1^2)
 # (Sec. 5.1); for zero-mean planted data the default is N(0, 1/J).

@@ -112,4 +112,12 @@ def test_null_context_is_rejected(lib):
         lib.std_sgd_epoch(None, 0.1, 0.1, 0.0, 0.0, 16)
     with pytest.raises(lib.StdError):
         lib.std_rmse(None, 1, np.zeros((1, 3), np.int32), np.zeros(1, np.float32))
+    with pytest.raises(lib.StdError):
+        lib.std_progress(None)
+    with pytest.raises(lib.StdError):
+        lib.std_reserve(None, 16, 1, 0)
+    with pytest.raises(lib.StdError):
+        lib.std_device_bytes(None)
+    with pytest.raises(lib.StdError):
+        lib.std_batch_step(None, 0.1, 0.1, 0.0, 0.0, 16, 1)
     lib.std_destroy(None)

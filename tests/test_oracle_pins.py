@@ -208,7 +208,7 @@ def test_factor_gradient_finite_differences(shape, ranks, R, norm_mode):
 
 
 def test_literal_and_closed_form_steps_agree():
-    """W_r = H O_r (Algorithm 1 lines 2-5, Eq. 7) equals the closed form."""
+    """W_r = H O_r (Algorithm 1, core phase, Eq. 7) equals the closed form."""
     shape, ranks, R = (5, 4, 6), (3, 2, 3), 2
     coords, x = _random_batch(shape, 19, seed=41, distinct=False)
     a = _random_model(shape, ranks, R, seed=42)
@@ -226,7 +226,7 @@ def test_literal_and_closed_form_steps_agree():
 def test_step_probe_matches_gradient_functions():
     """The V recorded for (mode 1, r_core 1) of a step is the Eq. 15 bracket at
     the start of the step; the factor F of mode 1 uses the core after the core
-    phase (Algorithm 1 line 16)."""
+    phase (Algorithm 1, Eq. 4)."""
     shape, ranks, R = (6, 5, 4), (3, 2, 4), 3
     coords, x = _random_batch(shape, 21, seed=43, distinct=False)
     md = _random_model(shape, ranks, R, seed=44)
