@@ -131,6 +131,15 @@ __host__ __device__ inline int bf16_row_stride(int Pn) {
   return kp;
 }
 
+// Row stride (in floats) of the FP32 Kronecker-row and unfolded-core tiles:
+// P_n padded to 4 and then to an odd number of 16-byte units, so that the
+// eight 16-byte loads of a quarter warp from eight consecutive rows fall on
+// distinct shared-memory banks.
+__host__ __device__ inline int fp32_row_stride(int Pn) {
+  const int p4 = pad4(Pn);
+  return (p4 & 7) == 4 ? p4 : p4 + 4;
+}
+
 struct SmemLayout {
   int B, VB, G, GT, GTh, Sh, S, ldig, cdig, rowtab, trij, sc[2], rows, master, p, left, right, red, D, q, head, fown,
       pbuf, total_words;
@@ -164,12 +173,13 @@ __host__ __device__ inline SmemLayout smem_layout_v(const Geometry& g, int chunk
   L.lw = left_width(g);
   L.rpre = (v == 0 && chunk * rwall <= kRightBudget) ? 1 : 0;
   L.rw = L.rpre ? rwall : rwmax;
-  L.sfloats = (bf || v == 2) ? 0 : (chunk * pad4(Pmax) < kSBudget ? chunk * pad4(Pmax) : kSBudget);
+  const int spmax = fp32_row_stride(Pmax);
+  L.sfloats = (bf || v == 2) ? 0 : (chunk * spmax < kSBudget ? chunk * spmax : kSBudget);
   const int kpmax = bf16_row_stride(Pmax);
   L.B = take(sumJR);
   L.VB = take(sumJR);
   L.G = take(g.prodJ);
-  L.GT = take(bf ? 0 : g.Jmax * pad4(Pmax));
+  L.GT = take(bf ? 0 : g.Jmax * spmax);
   L.GTh = take(bf ? round_up(g.Jmax, 16) * kpmax / 2 : 0);
   L.Sh = take(bf ? round_up(chunk, 16) * kpmax / 2 : 0);
   L.S = take(L.sfloats);
@@ -476,6 +486,74 @@ __device__ __forceinline__ float kron_entry(const float* rs, unsigned long long 
   return v;
 }
 
+// FP32 factor-phase contraction E_s = G_(n) S_s^T with the residual and the
+// contributions: thread per (group of SG consecutive samples, j), JL lanes
+// per group (J_n rounded up to a power of two), so that each unfolded-core
+// load serves SG samples; e_s = a_n . E_s - x_s is a shuffle sum over the
+// group's lanes, and qbuf[s][j] = e_s E_s[j].  Without materialised
+// Kronecker rows (full_s false) the entries are formed on the fly.
+template <int SG>
+__device__ __forceinline__ void contract_fp32(int cnt, int Jn, int Pn, int Pp, bool full_s, const float* GT,
+                                              const float* Sbuf, const float* rows, int sumJ, int an_off,
+                                              const unsigned long long* cdn, int nm1, const float* fx, float* qbuf,
+                                              int Jmax, int tid, int T) {
+  const int JL = pow2_at_least(Jn);
+  const int lg = 31 - __clz(JL);
+  const int ngrp = (cnt + SG - 1) / SG;
+  const int nitems = ngrp << lg;
+#pragma unroll 1
+  for (int o0 = 0; o0 < nitems; o0 += T) {
+    const int o = o0 + tid;
+    const int s0 = (o >> lg) * SG, j = o & (JL - 1);
+    const bool livej = (o < nitems) && (j < Jn);
+    float e[SG];
+#pragma unroll
+    for (int q = 0; q < SG; ++q) e[q] = 0.f;
+    if (livej) {
+      const float* gv = GT + j * Pp;
+      if (full_s) {
+        const float4* g4 = reinterpret_cast<const float4*>(gv);
+        const float4* sv[SG];
+#pragma unroll
+        for (int q = 0; q < SG; ++q)
+          sv[q] = reinterpret_cast<const float4*>(Sbuf + (s0 + q < cnt ? s0 + q : cnt - 1) * Pp);
+        const int nv = Pp >> 2;
+#pragma unroll 1
+        for (int v = 0; v < nv; ++v) {
+          const float4 y = g4[v];
+#pragma unroll
+          for (int q = 0; q < SG; ++q) {
+            const float4 x = sv[q][v];
+            e[q] = fmaf(x.x, y.x, e[q]);
+            e[q] = fmaf(x.y, y.y, e[q]);
+            e[q] = fmaf(x.z, y.z, e[q]);
+            e[q] = fmaf(x.w, y.w, e[q]);
+          }
+        }
+      } else {
+#pragma unroll
+        for (int q = 0; q < SG; ++q)
+          if (s0 + q < cnt) {
+            const float* rs = rows + (s0 + q) * sumJ;
+            float acc = 0.f;
+#pragma unroll 1
+            for (int cc = 0; cc < Pn; ++cc) acc = fmaf(kron_entry(rs, cdn[cc], nm1), gv[cc], acc);
+            e[q] = acc;
+          }
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < SG; ++q) {
+      const int s = s0 + q;
+      const bool live = livej && s < cnt;
+      float part = live ? rows[s * sumJ + an_off + j] * e[q] : 0.f;
+#pragma unroll 1
+      for (int off = JL >> 1; off > 0; off >>= 1) part += __shfl_xor_sync(0xffffffffu, part, off);
+      if (live) qbuf[s * Jmax + j] = (part - fx[s]) * e[q];
+    }
+  }
+}
+
 // Right Gram operand row of one sample for mode n (a_j a_j' packed, then a_j),
 // written by the lanes of one warp.
 __device__ __forceinline__ void right_row(float* dst, const float* an, int Jn, int tJ, int tJp, int rwn,
@@ -574,6 +652,7 @@ __device__ __forceinline__ void epoch_body(const EpochArgs& a, const int G, cons
   __syncthreads();
   const FastDiv f_sumJ = make_fastdiv((uint32_t)sumJ);
   const FastDiv f_R = make_fastdiv((uint32_t)R);
+  const FastDiv f_NR = make_fastdiv((uint32_t)(N * R));
   int sumJR = 0;
   for (int n = 0; n < N; ++n) sumJR += mJ[n] * R;
 #pragma unroll 1
@@ -676,31 +755,32 @@ __device__ __forceinline__ void epoch_body(const EpochArgs& a, const int G, cons
       // p[s][k][r] (warp per sample, lane per (k, r)) and, when they fit, the
       // right Gram operand rows of every mode (they depend on A only)
   #pragma unroll 1
-      for (int s = warp; s < cnt; s += nwarps) {
-        const float* rs = rows + s * sumJ;
+      for (int i = tid; i < cnt * NR; i += T) {
+        const int s = fdiv(i, f_NR), kr = i - s * NR;
+        const int k = fdiv(kr, f_R), r = kr - k * R;
+        const float* ar = rows + s * sumJ + mJoff[k];
+        const float* br = Bsm + mBoff[k] + r;
+        float acc0 = 0.f, acc1 = 0.f;
+        int j = 0;
   #pragma unroll 1
-        for (int kr = lane; kr < NR; kr += 32) {
-          const int k = fdiv(kr, f_R), r = kr - k * R;
-          const float* ar = rs + mJoff[k];
-          const float* br = Bsm + mBoff[k] + r;
-          float acc0 = 0.f, acc1 = 0.f;
-          int j = 0;
-  #pragma unroll 1
-          for (; j + 1 < mJ[k]; j += 2) {
-            acc0 = fmaf(ar[j], br[j * R], acc0);
-            acc1 = fmaf(ar[j + 1], br[(j + 1) * R], acc1);
-          }
-          if (j < mJ[k]) acc0 = fmaf(ar[j], br[j * R], acc0);
-          pbuf[s * NR + kr] = acc0 + acc1;
+        for (; j + 1 < mJ[k]; j += 2) {
+          acc0 = fmaf(ar[j], br[j * R], acc0);
+          acc1 = fmaf(ar[j + 1], br[(j + 1) * R], acc1);
         }
-        if (L.rpre)
+        if (j < mJ[k]) acc0 = fmaf(ar[j], br[j * R], acc0);
+        pbuf[i] = acc0 + acc1;
+      }
+      if (L.rpre)
+  #pragma unroll 1
+        for (int s = warp; s < cnt; s += nwarps) {
+          const float* rs = rows + s * sumJ;
   #pragma unroll 1
           for (int n = 0; n < N; ++n) {
             const int Jn = mJ[n];
             right_row(right + s * rw + mRoff[n], rs + mJoff[n], Jn, tri(Jn), pad4(tri(Jn)), right_width(Jn), trij,
                       lane);
           }
-      }
+        }
       __syncthreads();
 
   #pragma unroll 1
@@ -799,21 +879,27 @@ __device__ __forceinline__ void epoch_body(const EpochArgs& a, const int G, cons
           }
         }
         // hop 1: CTA c sums its slice of the payload (word pairs) over all CTAs
-        // (in CTA order within each lane, then a fixed butterfly across lanes)
-        // and pushes each sum into every CTA's copy of the payload
+        // (in CTA order within each lane, then a fixed butterfly across the
+        // GL lanes of the pair) and pushes each sum into every CTA's copy of
+        // the payload; with fewer than 32 CTAs a warp takes 32 / GL pairs at once
         bool ok = true;
         {
           const int P2 = P >> 1;
           const int per = (P2 + G - 1) / G;
           const int o_lo = c * per, o_hi = min(o_lo + per, P2);
+          const int GL = G >= 32 ? 32 : pow2_at_least(G);
+          const int lgl = 31 - __clz(GL);
+          const int sub = lane >> lgl, gl = lane & (GL - 1);
   #pragma unroll 1
-          for (int o = o_lo + warp; o < o_hi; o += nwarps) {
+          for (int ob = o_lo + (warp << (5 - lgl)); ob < o_hi; ob += nwarps << (5 - lgl)) {
+            const int o = ob + sub;
+            const bool live = o < o_hi;
             ulonglong2 w8[8];
             const unsigned long long* p8[8];
   #pragma unroll
             for (int u = 0; u < 8; ++u) {
-              const int cc = lane + 32 * u;
-              p8[u] = cc < G ? a.part + (unsigned)cc * (unsigned)a.pstride + 2 * o : nullptr;
+              const int cc = gl + GL * u;
+              p8[u] = (live && cc < G) ? a.part + (unsigned)cc * (unsigned)a.pstride + 2 * o : nullptr;
               w8[u] = p8[u] ? get_pair(p8[u]) : make_ulonglong2(0ULL, 0ULL);
             }
             if (ok) ok = wait_pairs<8>(p8, w8, tag, a);
@@ -824,14 +910,14 @@ __device__ __forceinline__ void epoch_body(const EpochArgs& a, const int G, cons
                 s0 += val_of(w8[u].x);
                 s1 += val_of(w8[u].y);
               }
-  #pragma unroll
-            for (int off = 16; off > 0; off >>= 1) {
+  #pragma unroll 1
+            for (int off = GL >> 1; off > 0; off >>= 1) {
               s0 += __shfl_xor_sync(0xffffffffu, s0, off);
               s1 += __shfl_xor_sync(0xffffffffu, s1, off);
             }
-            if (ok)
+            if (ok && live)
   #pragma unroll 1
-              for (int cc = lane; cc < G; cc += 32) put_pair(a.inbox + (unsigned)cc * (unsigned)a.pstride + 2 * o, tag, s0, s1);
+              for (int cc = gl; cc < G; cc += GL) put_pair(a.inbox + (unsigned)cc * (unsigned)a.pstride + 2 * o, tag, s0, s1);
           }
         }
         // hop 2: this CTA's copy of the reduced payload, into shared memory: g
@@ -840,15 +926,24 @@ __device__ __forceinline__ void epoch_body(const EpochArgs& a, const int G, cons
         {
           const unsigned long long* mine = a.inbox + (unsigned)c * (unsigned)a.pstride;
   #pragma unroll 1
-          for (int o2 = tid; o2 < (P >> 1); o2 += T) {
-            ulonglong2 w1[1];
-            const unsigned long long* p1[1] = {mine + 2 * o2};
-            w1[0] = get_pair(p1[0]);
-            if (ok) ok = wait_pairs<1>(p1, w1, tag, a);
+          for (int ob2 = tid; ob2 < (P >> 1); ob2 += 4 * T) {
+            ulonglong2 w4[4];
+            const unsigned long long* p4[4];
   #pragma unroll
-            for (int u = 0; u < 2; ++u) {
-              const int o = 2 * o2 + u;
-              const float v = val_of(u == 0 ? w1[0].x : w1[0].y);
+            for (int u = 0; u < 4; ++u) {
+              const int o2 = ob2 + u * T;
+              p4[u] = o2 < (P >> 1) ? mine + 2 * o2 : nullptr;
+              w4[u] = p4[u] ? get_pair(p4[u]) : make_ulonglong2(0ULL, 0ULL);
+            }
+            if (ok) ok = wait_pairs<4>(p4, w4, tag, a);
+  #pragma unroll 1
+            for (int uw = 0; uw < 8; ++uw) {
+              const int u = uw >> 1;
+              const int o2 = ob2 + u * T;
+              if (o2 >= (P >> 1)) break;
+              const ulonglong2 wv = u == 0 ? w4[0] : (u == 1 ? w4[1] : (u == 2 ? w4[2] : w4[3]));
+              const int o = 2 * o2 + (uw & 1);
+              const float v = val_of((uw & 1) == 0 ? wv.x : wv.y);
               if (o < Kx) {
                 const int r = fdiv(o >> 2, f_na4), j = o - r * Jq;
                 if (j < Jn) redsm[r * Jn + j] = v;
@@ -937,22 +1032,22 @@ __device__ __forceinline__ void epoch_body(const EpochArgs& a, const int G, cons
           }
         }
         __syncthreads();
-        // p[s][n][r] with the new B(n): warp per sample, lane r
+        // p[s][n][r] with the new B(n): thread per (sample, r)
   #pragma unroll 1
-        for (int s = warp; s < cnt; s += nwarps)
-          if (lane < R) {
-            const float* ar = rows + s * sumJ + mJoff[n];
-            const float* br = Bsm + mBoff[n] + lane;
-            float acc0 = 0.f, acc1 = 0.f;
-            int j = 0;
+        for (int i = tid; i < cnt * R; i += T) {
+          const int s = fdiv(i, f_R), r = i - s * R;
+          const float* ar = rows + s * sumJ + mJoff[n];
+          const float* br = Bsm + mBoff[n] + r;
+          float acc0 = 0.f, acc1 = 0.f;
+          int j = 0;
   #pragma unroll 1
-            for (; j + 1 < Jn; j += 2) {
-              acc0 = fmaf(ar[j], br[j * R], acc0);
-              acc1 = fmaf(ar[j + 1], br[(j + 1) * R], acc1);
-            }
-            if (j < Jn) acc0 = fmaf(ar[j], br[j * R], acc0);
-            pbuf[s * NR + n * R + lane] = acc0 + acc1;
+          for (; j + 1 < Jn; j += 2) {
+            acc0 = fmaf(ar[j], br[j * R], acc0);
+            acc1 = fmaf(ar[j + 1], br[(j + 1) * R], acc1);
           }
+          if (j < Jn) acc0 = fmaf(ar[j], br[j * R], acc0);
+          pbuf[s * NR + n * R + r] = acc0 + acc1;
+        }
         __syncthreads();
       }
     }
@@ -982,7 +1077,7 @@ __device__ __forceinline__ void epoch_body(const EpochArgs& a, const int G, cons
     for (int n = 0; n < N; ++n) {
       const int Jn = mJ[n];
       const int Pn = mPn[n];
-      const int Pp = pad4(Pn);
+      const int Pp = fp32_row_stride(Pn);
       const uint32_t tag = tag0 + (uint32_t)n;
       const unsigned long long* cdn = cdig + mToff[n];
       bool ok = true;
@@ -1199,49 +1294,12 @@ __device__ __forceinline__ void epoch_body(const EpochArgs& a, const int G, cons
           }
         }
       } else {
-        // E_s = G_(n) S_s^T: thread per (sample, j), JL lanes per sample (J_n
-        // rounded up to a power of two); the residual e_s = a_n . E_s - x_s is
-        // a shuffle sum over the sample's lanes
+        // four samples per thread when that still fills half the block
         const int JL = pow2_at_least(Jn);
-        const int lg = 31 - __clz(JL);
-        const int nitems = cnt << lg;
-#pragma unroll 1
-        for (int o0 = 0; o0 < nitems; o0 += T) {
-          const int o = o0 + tid;
-          const int s = o >> lg, j = o & (JL - 1);
-          const bool live = (o < nitems) && (j < Jn);
-          float e0 = 0.f;
-          if (live) {
-            const float* gv = GT + j * Pp;
-            float a0 = 0.f, a1 = 0.f;
-            if (full_s) {
-              const float4* sv = reinterpret_cast<const float4*>(Sbuf + s * Pp);
-              const float4* g4 = reinterpret_cast<const float4*>(gv);
-              const int nv = Pp >> 2;
-              int v = 0;
-#pragma unroll 1
-              for (; v + 1 < nv; v += 2) {
-                const float4 x = sv[v], y = g4[v];
-                const float4 x2 = sv[v + 1], y2 = g4[v + 1];
-                a0 = fmaf(x.x, y.x, a0); a0 = fmaf(x.y, y.y, a0); a0 = fmaf(x.z, y.z, a0); a0 = fmaf(x.w, y.w, a0);
-                a1 = fmaf(x2.x, y2.x, a1); a1 = fmaf(x2.y, y2.y, a1); a1 = fmaf(x2.z, y2.z, a1); a1 = fmaf(x2.w, y2.w, a1);
-              }
-              if (v < nv) {
-                const float4 x = sv[v], y = g4[v];
-                a0 = fmaf(x.x, y.x, a0); a0 = fmaf(x.y, y.y, a0); a0 = fmaf(x.z, y.z, a0); a0 = fmaf(x.w, y.w, a0);
-              }
-            } else {
-              const float* rs = rows + s * sumJ;
-#pragma unroll 1
-              for (int cc = 0; cc < Pn; ++cc) a0 = fmaf(kron_entry(rs, cdn[cc], nm1), gv[cc], a0);
-            }
-            e0 = a0 + a1;
-          }
-          float part = live ? rows[s * sumJ + mJoff[n] + j] * e0 : 0.f;
-#pragma unroll 1
-          for (int off = JL >> 1; off > 0; off >>= 1) part += __shfl_xor_sync(0xffffffffu, part, off);
-          if (live) qbuf[s * Jmax + j] = (part - fx[s]) * e0;
-        }
+        if (((cnt + 3) >> 2) * JL >= (T >> 1))
+          contract_fp32<4>(cnt, Jn, Pn, Pp, full_s, GT, Sbuf, rows, sumJ, mJoff[n], cdn, nm1, fx, qbuf, Jmax, tid, T);
+        else
+          contract_fp32<1>(cnt, Jn, Pn, Pp, full_s, GT, Sbuf, rows, sumJ, mJoff[n], cdn, nm1, fx, qbuf, Jmax, tid, T);
       }
       __syncthreads();
       // run sums in sorted order (warp per run piece, lane j), kept in the
