@@ -1135,26 +1135,40 @@ __device__ __forceinline__ void epoch_body(const EpochArgs& a, const int G, cons
                 master[s * Jmax + lane] = __ldcg(mA[n] + (unsigned)fcrd[s * N + n] * (unsigned)mJp[n] + lane);
           // G_(n) for the contraction, [j][c]: warp per j, lanes over c;
           // column c sits at the offset of its other-mode digits in G-hat
+          // (BF16: the rows and columns the tensor-core tiles read, J_n
+          // rounded up to 8 and P_n to 16)
           const int KP = BF ? bf16_row_stride(Pn) : Pp;
-          const int Jrows = a.contraction == 1 ? 0 : (BF ? round_up(Jn, 16) : Jn);
+          const int Kext = BF ? round_up(Pn, 16) : Pp;
+          const int Jrows = a.contraction == 1 ? 0 : (BF ? round_up(Jn, 8) : Jn);
 #pragma unroll 1
           for (int j = warp; j < Jrows; j += nwarps)
 #pragma unroll 1
-            for (int cc = lane; cc < KP; cc += 32) {
-              float gv = 0.f;
-              if (j < Jn && cc < Pn) {
-                const unsigned long long packed = cdn[cc];
-                int off = j * mGs[n], sh = 0;
+            for (int cc0 = lane; cc0 < Kext; cc0 += 64) {
+              float gv[2];
+#pragma unroll
+              for (int h = 0; h < 2; ++h) {
+                const int cc = cc0 + 32 * h;
+                gv[h] = 0.f;
+                if (j < Jn && cc < Pn) {
+                  const unsigned long long packed = cdn[cc];
+                  int off = j * mGs[n], sh = 0;
 #pragma unroll 1
-                for (int k = 0; k < N; ++k) {
-                  if (k == n) continue;
-                  off += ((int)((packed >> sh) & 0xffu) - mJoff[k]) * mGs[k];
-                  sh += 8;
+                  for (int k = 0; k < N; ++k) {
+                    if (k == n) continue;
+                    off += ((int)((packed >> sh) & 0xffu) - mJoff[k]) * mGs[k];
+                    sh += 8;
+                  }
+                  gv[h] = Gsm[off];
                 }
-                gv = Gsm[off];
               }
-              if (BF) GTh[j * KP + cc] = __float2bfloat16_rn(gv);
-              else GT[j * KP + cc] = gv;
+#pragma unroll
+              for (int h = 0; h < 2; ++h) {
+                const int cc = cc0 + 32 * h;
+                if (cc < Kext) {
+                  if (BF) GTh[j * KP + cc] = __float2bfloat16_rn(gv[h]);
+                  else GT[j * KP + cc] = gv[h];
+                }
+              }
             }
           // run heads of this chunk, compacted in order (last warp)
           if (warp == nwarps - 1) {
@@ -1223,20 +1237,33 @@ __device__ __forceinline__ void epoch_body(const EpochArgs& a, const int G, cons
           if (lane < Jn) qbuf[s * Jmax + lane] = (part - fx[s]) * E;
         }
       } else if (BF) {
+        // (the K extent P_n rounded up to 16 is all the tiles read)
         const int KP = bf16_row_stride(Pn);
+        const int Kext = round_up(Pn, 16);
 #pragma unroll 1
         for (int s = warp; s < round_up(cnt, 16); s += nwarps) {
           const float* rs = rows + s * sumJ;
 #pragma unroll 1
-          for (int cc = lane; cc < KP; cc += 32)
-            Sh[s * KP + cc] = __float2bfloat16_rn((s < cnt && cc < Pn) ? kron_entry(rs, cdn[cc], nm1) : 0.f);
+          for (int cc = lane; cc < Kext; cc += 64) {
+            const int c2 = cc + 32;
+            const float v0 = (s < cnt && cc < Pn) ? kron_entry(rs, cdn[cc], nm1) : 0.f;
+            const float v1 = (s < cnt && c2 < Pn) ? kron_entry(rs, cdn[c2], nm1) : 0.f;
+            Sh[s * KP + cc] = __float2bfloat16_rn(v0);
+            if (c2 < Kext) Sh[s * KP + c2] = __float2bfloat16_rn(v1);
+          }
         }
       } else if (full_s) {
 #pragma unroll 1
         for (int s = warp; s < cnt; s += nwarps) {
           const float* rs = rows + s * sumJ;
 #pragma unroll 1
-          for (int cc = lane; cc < Pp; cc += 32) Sbuf[s * Pp + cc] = cc < Pn ? kron_entry(rs, cdn[cc], nm1) : 0.f;
+          for (int cc = lane; cc < Pp; cc += 64) {
+            const int c2 = cc + 32;
+            const float v0 = cc < Pn ? kron_entry(rs, cdn[cc], nm1) : 0.f;
+            const float v1 = c2 < Pn ? kron_entry(rs, cdn[c2], nm1) : 0.f;
+            Sbuf[s * Pp + cc] = v0;
+            if (c2 < Pp) Sbuf[s * Pp + c2] = v1;
+          }
         }
       }
       __syncthreads();
