@@ -209,12 +209,17 @@ const char* std_last_error(void);
  * the other (longest first onto the least-loaded group), so small tensors no
  * longer leave the GPU idle behind one tensor's chain of dependent phases
  * (Algorithm 1).  Each tensor's epoch is exactly the one std_sgd_epoch would
- * run with that many CTAs.
+ * run with that many CTAs.  The launch sequence (barrier resets, argument
+ * uploads from pinned staging, the cooperative kernel) is captured once as a
+ * CUDA graph and replayed while the tensors, the group size and the group
+ * count stay the same; samplers run before it only when a tensor starts an
+ * epoch.
  *   count, ctxs       the contexts (same precision, same stream; each at most
  *                     once); they must outlive the batch, which does not own them
- *   ctas_per_tensor   CTAs per tensor; 0 = chosen on the first std_batch_epoch
- *                     by timing each power of two that fits on a run of the
- *                     first minibatches that writes no parameter
+ *   ctas_per_tensor   CTAs per tensor; 0 = chosen on the first step by
+ *                     timing each power of two up to 32 that fits on a run
+ *                     of 3% of every tensor's minibatches that writes no
+ *                     parameter (the autotuner)
  * Errors: STD_EINVAL, STD_ECUDA.
  */
 typedef struct std_batch std_batch;
@@ -227,6 +232,8 @@ typedef struct {
     int64_t nnz;              /* total training nonzeros visited */
     int32_t tensors;
     int32_t ctas_per_tensor;  /* the group size used */
+    int32_t graph_replayed;   /* 1: the launch replayed the captured graph; 0: it was (re)captured */
+    int32_t reserved;
 } std_batch_stats;
 
 /* Up to max_batches minibatches of every tensor of the batch, each tensor

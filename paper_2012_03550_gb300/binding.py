@@ -78,6 +78,8 @@ class std_batch_stats(ctypes.Structure):
         ("nnz", ctypes.c_int64),
         ("tensors", ctypes.c_int32),
         ("ctas_per_tensor", ctypes.c_int32),
+        ("graph_replayed", ctypes.c_int32),
+        ("reserved", ctypes.c_int32),
     ]
 
 

@@ -773,9 +773,21 @@ struct std_batch {
   int* d_order = nullptr;
   int* d_first = nullptr;
   size_t cap_items = 0, cap_groups = 0;
-  std::vector<EpochArgs> h_items;
-  std::vector<int> h_order, h_first;
+  // pinned host staging of the launch arguments (fixed addresses, so that a
+  // captured graph copies their current contents at every replay)
+  EpochArgs* h_items = nullptr;
+  int* h_order = nullptr;
+  int* h_first = nullptr;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr, evm = nullptr;
+  // the launch sequence (barrier resets, argument uploads, the cooperative
+  // kernel) captured as a CUDA graph and replayed while its shape holds
+  cudaStream_t cap_stream = nullptr;
+  cudaGraphExec_t gexec = nullptr;
+  std::vector<std_ctx*> gkey_ctxs;
+  int gkey_G = 0, gkey_groups = 0;
+  size_t gkey_smem = 0;
+  const void* gkey_items = nullptr;
+  bool replayed = false;   // the last launch replayed the graph
 };
 
 namespace {
@@ -795,7 +807,33 @@ int batch_launch(std_batch* bt, float lr_a, float lr_b, float lam_a, float lam_b
                  const std::vector<std::pair<int64_t, int64_t>>& range, int G, bool dry) {
   const int T = (int)bt->ctxs.size();
   size_t smem = 0;
-  bt->h_items.resize(T);
+  if ((size_t)T > bt->cap_items) {
+    // grow every argument buffer (device and pinned host) to T tensors
+    if (bt->gexec) cudaGraphExecDestroy(bt->gexec);
+    bt->gexec = nullptr;
+    cudaFree(bt->d_items);
+    cudaFree(bt->d_order);
+    cudaFree(bt->d_first);
+    cudaFreeHost(bt->h_items);
+    cudaFreeHost(bt->h_order);
+    cudaFreeHost(bt->h_first);
+    bt->d_items = nullptr;
+    bt->d_order = nullptr;
+    bt->d_first = nullptr;
+    bt->h_items = nullptr;
+    bt->h_order = nullptr;
+    bt->h_first = nullptr;
+    bt->cap_items = 0;
+    const size_t ci = (size_t)T, cg = (size_t)(T + 1);
+    STD_CUDA(cudaMalloc((void**)&bt->d_items, ci * sizeof(EpochArgs)), "batch arguments");
+    STD_CUDA(cudaMalloc((void**)&bt->d_order, ci * sizeof(int)), "batch order");
+    STD_CUDA(cudaMalloc((void**)&bt->d_first, cg * sizeof(int)), "batch groups");
+    STD_CUDA(cudaMallocHost((void**)&bt->h_items, ci * sizeof(EpochArgs)), "batch arguments (host)");
+    STD_CUDA(cudaMallocHost((void**)&bt->h_order, ci * sizeof(int)), "batch order (host)");
+    STD_CUDA(cudaMallocHost((void**)&bt->h_first, cg * sizeof(int)), "batch groups (host)");
+    bt->cap_items = ci;
+    bt->cap_groups = cg;
+  }
   std::vector<std::pair<int64_t, int>> work;
   for (int t = 0; t < T; ++t) {
     std_ctx* c = bt->ctxs[t];
@@ -817,7 +855,6 @@ int batch_launch(std_batch* bt, float lr_a, float lr_b, float lam_a, float lam_b
     a.dry = dry ? 1 : 0;
     if (dry) a.momentum = 0.f;
     bt->h_items[t] = a;
-    STD_CUDA(cudaMemsetAsync(c->bar, 0, sizeof(unsigned long long), bt->stream), "barrier clear");
     work.push_back({(e1 - e0) * (int64_t)M * (c->g.sumJ + c->g.prodJ / c->g.Jmax), t});
   }
   STD_CUDA(epoch_multi_setup(bt->precision, smem), "batched kernel attributes");
@@ -838,39 +875,59 @@ int batch_launch(std_batch* bt, float lr_a, float lr_b, float lam_a, float lam_b
     load[q] += w.first;
     lists[q].push_back(w.second);
   }
-  bt->h_order.clear();
-  bt->h_first.assign(1, 0);
+  int no = 0;
+  bt->h_first[0] = 0;
   for (int q = 0; q < groups; ++q) {
-    for (int t : lists[q]) bt->h_order.push_back(t);
-    bt->h_first.push_back((int)bt->h_order.size());
+    for (int t : lists[q]) bt->h_order[no++] = t;
+    bt->h_first[q + 1] = no;
   }
-  if ((size_t)T > bt->cap_items || (size_t)groups + 1 > bt->cap_groups) {
-    cudaFree(bt->d_items);
-    cudaFree(bt->d_order);
-    cudaFree(bt->d_first);
-    bt->d_items = nullptr;
-    bt->d_order = nullptr;
-    bt->d_first = nullptr;
-    const size_t ci = (size_t)T, cg = (size_t)(T + 1);
-    STD_CUDA(cudaMalloc((void**)&bt->d_items, ci * sizeof(EpochArgs)), "batch arguments");
-    STD_CUDA(cudaMalloc((void**)&bt->d_order, ci * sizeof(int)), "batch order");
-    STD_CUDA(cudaMalloc((void**)&bt->d_first, cg * sizeof(int)), "batch groups");
-    bt->cap_items = ci;
-    bt->cap_groups = cg;
+  // (re)capture the launch sequence when its shape changed: the tensors (their
+  // barrier words), the group size, the group count, the shared memory and
+  // the argument buffers; otherwise replay it (the copies read the pinned
+  // staging, so the new ranges, order and flags reach the device)
+  const bool same = bt->gexec && bt->gkey_ctxs == bt->ctxs && bt->gkey_G == G && bt->gkey_groups == groups &&
+                    bt->gkey_smem == smem && bt->gkey_items == (const void*)bt->d_items;
+  bt->replayed = same;
+  if (!same) {
+    if (bt->gexec) cudaGraphExecDestroy(bt->gexec);
+    bt->gexec = nullptr;
+    if (!bt->cap_stream) STD_CUDA(cudaStreamCreateWithFlags(&bt->cap_stream, cudaStreamNonBlocking), "capture stream");
+    cudaStream_t cs = bt->cap_stream;
+    STD_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal), "graph capture");
+    cudaError_t e = cudaSuccess;
+    for (int t = 0; t < T && e == cudaSuccess; ++t)
+      e = cudaMemsetAsync(bt->ctxs[t]->bar, 0, sizeof(unsigned long long), cs);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(bt->d_items, bt->h_items, (size_t)T * sizeof(EpochArgs), cudaMemcpyHostToDevice, cs);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(bt->d_order, bt->h_order, (size_t)T * sizeof(int), cudaMemcpyHostToDevice, cs);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(bt->d_first, bt->h_first, (size_t)(groups + 1) * sizeof(int), cudaMemcpyHostToDevice, cs);
+    if (e == cudaSuccess) {
+      MultiArgs m{};
+      m.items = bt->d_items;
+      m.order = bt->d_order;
+      m.first = bt->d_first;
+      m.group = G;
+      e = launch_epoch_multi(m, bt->precision, groups * G, smem, cs);
+    }
+    cudaGraph_t graph = nullptr;
+    const cudaError_t e2 = cudaStreamEndCapture(cs, &graph);
+    if (e == cudaSuccess) e = e2;
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&bt->gexec, graph, 0);
+    if (graph) cudaGraphDestroy(graph);
+    if (e != cudaSuccess) {
+      bt->gexec = nullptr;
+      return cuda_error(e, "batched launch graph");
+    }
+    bt->gkey_ctxs = bt->ctxs;
+    bt->gkey_G = G;
+    bt->gkey_groups = groups;
+    bt->gkey_smem = smem;
+    bt->gkey_items = bt->d_items;
   }
-  STD_CUDA(cudaMemcpyAsync(bt->d_items, bt->h_items.data(), (size_t)T * sizeof(EpochArgs), cudaMemcpyHostToDevice,
-                           bt->stream), "batch arguments upload");
-  STD_CUDA(cudaMemcpyAsync(bt->d_order, bt->h_order.data(), (size_t)T * sizeof(int), cudaMemcpyHostToDevice,
-                           bt->stream), "batch order upload");
-  STD_CUDA(cudaMemcpyAsync(bt->d_first, bt->h_first.data(), (size_t)(groups + 1) * sizeof(int),
-                           cudaMemcpyHostToDevice, bt->stream), "batch groups upload");
-  MultiArgs m{};
-  m.items = bt->d_items;
-  m.order = bt->d_order;
-  m.first = bt->d_first;
-  m.group = G;
   STD_CUDA(cudaEventRecord(bt->evm, bt->stream), "event");
-  STD_CUDA(launch_epoch_multi(m, bt->precision, groups * G, smem, bt->stream), "batched kernel launch");
+  STD_CUDA(cudaGraphLaunch(bt->gexec, bt->stream), "batched graph launch");
   STD_CUDA(cudaEventRecord(bt->ev1, bt->stream), "event");
   int h = 0;
   STD_CUDA(cudaMemcpyAsync(&h, bt->err, sizeof(int), cudaMemcpyDeviceToHost, bt->stream), "batch error read");
@@ -923,10 +980,15 @@ int std_batch_create(std_batch** out, int32_t count, std_ctx* const* ctxs, int32
 int std_batch_destroy(std_batch* bt) {
   if (!bt) return STD_OK;
   cudaStreamSynchronize(bt->stream);
+  if (bt->gexec) cudaGraphExecDestroy(bt->gexec);
+  if (bt->cap_stream) cudaStreamDestroy(bt->cap_stream);
   cudaFree(bt->err);
   cudaFree(bt->d_items);
   cudaFree(bt->d_order);
   cudaFree(bt->d_first);
+  cudaFreeHost(bt->h_items);
+  cudaFreeHost(bt->h_order);
+  cudaFreeHost(bt->h_first);
   if (bt->ev0) cudaEventDestroy(bt->ev0);
   if (bt->ev1) cudaEventDestroy(bt->ev1);
   if (bt->evm) cudaEventDestroy(bt->evm);
@@ -1006,6 +1068,8 @@ int std_batch_step(std_batch* bt, float lr_a, float lr_b, float lambda_a, float 
     out->nnz_per_s = ms > 0.f ? (double)nnz / (ms * 1e-3) : 0.0;
     out->tensors = (int32_t)bt->ctxs.size();
     out->ctas_per_tensor = bt->group;
+    out->graph_replayed = bt->replayed ? 1 : 0;
+    out->reserved = 0;
   }
   return STD_OK;
 }

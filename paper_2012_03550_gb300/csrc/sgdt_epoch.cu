@@ -1498,10 +1498,21 @@ int epoch_multi_max_ctas(int precision, size_t smem) {
   return per * sms;
 }
 
+// Cooperative launch through the launch-attribute form, which stream capture
+// records as a cooperative kernel node.
 cudaError_t launch_epoch_multi(const MultiArgs& m, int precision, int ctas, size_t smem, cudaStream_t st) {
-  MultiArgs copy = m;
-  void* args[] = {&copy};
-  return cudaLaunchCooperativeKernel(multi_kernel_for(precision), dim3(ctas), dim3(kEpochThreads), args, smem, st);
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(ctas);
+  cfg.blockDim = dim3(kEpochThreads);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  if (precision == 1) return cudaLaunchKernelEx(&cfg, k_epoch_multi<true>, m);
+  return cudaLaunchKernelEx(&cfg, k_epoch_multi<false>, m);
 }
 
 }  // namespace sgdt

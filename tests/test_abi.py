@@ -53,6 +53,8 @@ def test_struct_layouts_match_c(lib, tmp_path):
         'printf("%zu %zu %zu %zu %zu %zu\\n", sizeof(std_options), offsetof(std_options, stream),'
         " offsetof(std_options, watchdog_ns), offsetof(std_options, hbm_budget_bytes),"
         " sizeof(std_epoch_stats), sizeof(std_probe));\n"
+        'printf("%zu %zu %zu %zu\\n", sizeof(std_batch_stats), offsetof(std_batch_stats, graph_replayed),'
+        " offsetof(std_options, contraction), offsetof(std_options, momentum));\n"
         'printf("%d %d %d %d\\n", STD_MAX_ORDER, STD_MAX_RANK, STD_MAX_CORE, STD_MAX_MINIBATCH);\n'
         "return 0;}\n")
     exe = tmp_path / "layout"
@@ -62,7 +64,10 @@ def test_struct_layouts_match_c(lib, tmp_path):
     py = [ctypes.sizeof(lib.std_options), lib.std_options.stream.offset, lib.std_options.watchdog_ns.offset,
           lib.std_options.hbm_budget_bytes.offset, ctypes.sizeof(lib.std_epoch_stats), ctypes.sizeof(lib.std_probe)]
     assert c_sizes == py
-    lims = [int(v) for v in out[1].split()]
+    b_sizes = [int(v) for v in out[1].split()]
+    assert b_sizes == [ctypes.sizeof(lib.std_batch_stats), lib.std_batch_stats.graph_replayed.offset,
+                       lib.std_options.contraction.offset, lib.std_options.momentum.offset]
+    lims = [int(v) for v in out[2].split()]
     assert lims == [lib.STD_MAX_ORDER, lib.STD_MAX_RANK, lib.STD_MAX_CORE, lib.STD_MAX_MINIBATCH]
 
 

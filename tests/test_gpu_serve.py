@@ -162,7 +162,7 @@ def test_epoch_in_progress_is_protected(B, tensors):
     try:
         with B.Batch([g], ctas_per_tensor=2) as bt:
             st = bt.step(LR, LR, LAM, LAM, M, 3)
-            assert st["nnz"] == 3 * M
+            assert st["nnz"] == 3 * M and st["graph_replayed"] == 0
             assert g.progress() == (0, 3)
             with pytest.raises(B.StdError):
                 g.epoch(LR, LR, LAM, LAM, M)           # std_sgd_epoch refuses a context mid-epoch
@@ -170,6 +170,7 @@ def test_epoch_in_progress_is_protected(B, tensors):
                 bt.step(LR, LR, LAM, LAM, M // 2, 1)   # and a step with another minibatch size
             st = bt.step(LR, LR, LAM, LAM, M, 10 ** 6)
             assert st["nnz"] == c.shape[0] - 3 * M
+            assert st["graph_replayed"] == 1        # same tensors and group size: the captured graph
             assert g.progress() == (1, 0)
         g.epoch(LR, LR, LAM, LAM, M)
         assert g.progress() == (2, 0)
