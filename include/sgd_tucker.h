@@ -269,6 +269,14 @@ int std_reserve(std_ctx* ctx, int32_t minibatch, int32_t ctas_per_tensor, int64_
  * scratch). */
 int std_device_bytes(const std_ctx* ctx, uint64_t* bytes);
 
+/* Failure-detection check of the epoch kernels' bounded waits: one thread
+ * waits, through the same wait routine, for a tagged exchange word that
+ * nothing writes, with a watchdog of watchdog_ns (1e3..1e10).  *status gets
+ * the error the device recorded: STD_ETIMEOUT when the watchdog expired as it
+ * must.  Nothing faults and the device stays usable.  Errors: STD_EINVAL,
+ * STD_ECUDA. */
+int std_watchdog_probe(uint64_t watchdog_ns, int32_t* status);
+
 /* Release the batch (not its contexts; NULL is a no-op). */
 int std_batch_destroy(std_batch* batch);
 

@@ -120,6 +120,7 @@ SIGNATURES = {
     "std_progress": (ctypes.c_int, [_P, _P, _P]),
     "std_reserve": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int64]),
     "std_device_bytes": (ctypes.c_int, [_P, _P]),
+    "std_watchdog_probe": (ctypes.c_int, [ctypes.c_uint64, _P]),
 }
 
 
@@ -382,6 +383,12 @@ def std_device_bytes(ctx):
     b = ctypes.c_uint64()
     _check(lib().std_device_bytes(ctx, ctypes.byref(b)))
     return b.value
+
+
+def std_watchdog_probe(watchdog_ns):
+    st = ctypes.c_int32()
+    _check(lib().std_watchdog_probe(int(watchdog_ns), ctypes.byref(st)))
+    return st.value
 
 
 def std_batch_destroy(batch):

@@ -1103,6 +1103,27 @@ int std_device_bytes(const std_ctx* c, uint64_t* bytes) {
   return STD_OK;
 }
 
+int std_watchdog_probe(uint64_t watchdog_ns, int32_t* status) {
+  if (!status) return set_error(STD_EINVAL, "status is NULL");
+  if (watchdog_ns < 1000ULL || watchdog_ns > 10000000000ULL)
+    return set_error(STD_EINVAL, "watchdog_ns must be in [1e3, 1e10]");
+  int* err = nullptr;
+  unsigned long long* word = nullptr;
+  cudaError_t e = cudaMalloc((void**)&err, sizeof(int));
+  if (e == cudaSuccess) e = cudaMalloc((void**)&word, sizeof(unsigned long long));
+  if (e == cudaSuccess) e = cudaMemset(err, 0, sizeof(int));
+  if (e == cudaSuccess) e = cudaMemset(word, 0, sizeof(unsigned long long));
+  if (e == cudaSuccess) e = launch_wait_probe(watchdog_ns, err, word, nullptr);
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  int h = 0;
+  if (e == cudaSuccess) e = cudaMemcpy(&h, err, sizeof(int), cudaMemcpyDeviceToHost);
+  cudaFree(err);
+  cudaFree(word);
+  if (e != cudaSuccess) return cuda_error(e, "watchdog probe");
+  *status = h;
+  return STD_OK;
+}
+
 int std_progress(const std_ctx* c, int64_t* epoch, int64_t* next_batch) {
   if (!c) return set_error(STD_EINVAL, "context is NULL");
   if (epoch) *epoch = c->epoch;

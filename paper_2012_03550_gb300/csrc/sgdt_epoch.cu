@@ -512,24 +512,47 @@ __device__ __forceinline__ void contract_fp32(int cnt, int Jn, int Pn, int Pp, b
     if (livej) {
       const float* gv = GT + j * Pp;
       if (full_s) {
+        // two partial sums per sample (even and odd 4-column groups)
         const float4* g4 = reinterpret_cast<const float4*>(gv);
-        const float4* sv[SG];
-#pragma unroll
-        for (int q = 0; q < SG; ++q)
-          sv[q] = reinterpret_cast<const float4*>(Sbuf + (s0 + q < cnt ? s0 + q : cnt - 1) * Pp);
+        const float4* s4 = reinterpret_cast<const float4*>(Sbuf);
         const int nv = Pp >> 2;
+        int sr[SG];   // 4-column row offsets of the group's samples (the last sample repeated past cnt)
+        float f[SG];
+#pragma unroll
+        for (int q = 0; q < SG; ++q) {
+          sr[q] = (s0 + q < cnt ? s0 + q : cnt - 1) * nv;
+          f[q] = 0.f;
+        }
+        int v = 0;
 #pragma unroll 1
-        for (int v = 0; v < nv; ++v) {
+        for (; v + 1 < nv; v += 2) {
+          const float4 y = g4[v], y2 = g4[v + 1];
+#pragma unroll
+          for (int q = 0; q < SG; ++q) {
+            const float4 x = s4[sr[q] + v], x2 = s4[sr[q] + v + 1];
+            e[q] = fmaf(x.x, y.x, e[q]);
+            e[q] = fmaf(x.y, y.y, e[q]);
+            e[q] = fmaf(x.z, y.z, e[q]);
+            e[q] = fmaf(x.w, y.w, e[q]);
+            f[q] = fmaf(x2.x, y2.x, f[q]);
+            f[q] = fmaf(x2.y, y2.y, f[q]);
+            f[q] = fmaf(x2.z, y2.z, f[q]);
+            f[q] = fmaf(x2.w, y2.w, f[q]);
+          }
+        }
+        if (v < nv) {
           const float4 y = g4[v];
 #pragma unroll
           for (int q = 0; q < SG; ++q) {
-            const float4 x = sv[q][v];
+            const float4 x = s4[sr[q] + v];
             e[q] = fmaf(x.x, y.x, e[q]);
             e[q] = fmaf(x.y, y.y, e[q]);
             e[q] = fmaf(x.z, y.z, e[q]);
             e[q] = fmaf(x.w, y.w, e[q]);
           }
         }
+#pragma unroll
+        for (int q = 0; q < SG; ++q) e[q] += f[q];
       } else {
 #pragma unroll
         for (int q = 0; q < SG; ++q)
@@ -752,8 +775,8 @@ __device__ __forceinline__ void epoch_body(const EpochArgs& a, const int G, cons
     __syncthreads();
     // lr_b = 0 leaves B unchanged: the core phase is skipped
     if (a.lr_b != 0.f) {
-      // p[s][k][r] (warp per sample, lane per (k, r)) and, when they fit, the
-      // right Gram operand rows of every mode (they depend on A only)
+      // p[s][k][r] (thread per (sample, k, r)) and, when they fit, the right
+      // Gram operand rows of every mode (they depend on A only)
   #pragma unroll 1
       for (int i = tid; i < cnt * NR; i += T) {
         const int s = fdiv(i, f_NR), kr = i - s * NR;
@@ -882,42 +905,63 @@ __device__ __forceinline__ void epoch_body(const EpochArgs& a, const int G, cons
         // (in CTA order within each lane, then a fixed butterfly across the
         // GL lanes of the pair) and pushes each sum into every CTA's copy of
         // the payload; with fewer than 32 CTAs a warp takes 32 / GL pairs at once
+        // (a separate loop: the full-warp form is faster when every lane has a CTA)
         bool ok = true;
         {
           const int P2 = P >> 1;
           const int per = (P2 + G - 1) / G;
           const int o_lo = c * per, o_hi = min(o_lo + per, P2);
-          const int GL = G >= 32 ? 32 : pow2_at_least(G);
-          const int lgl = 31 - __clz(GL);
-          const int sub = lane >> lgl, gl = lane & (GL - 1);
-  #pragma unroll 1
-          for (int ob = o_lo + (warp << (5 - lgl)); ob < o_hi; ob += nwarps << (5 - lgl)) {
-            const int o = ob + sub;
-            const bool live = o < o_hi;
-            ulonglong2 w8[8];
-            const unsigned long long* p8[8];
-  #pragma unroll
-            for (int u = 0; u < 8; ++u) {
-              const int cc = gl + GL * u;
-              p8[u] = (live && cc < G) ? a.part + (unsigned)cc * (unsigned)a.pstride + 2 * o : nullptr;
-              w8[u] = p8[u] ? get_pair(p8[u]) : make_ulonglong2(0ULL, 0ULL);
-            }
-            if (ok) ok = wait_pairs<8>(p8, w8, tag, a);
-            float s0 = 0.f, s1 = 0.f;
-  #pragma unroll
-            for (int u = 0; u < 8; ++u)
-              if (p8[u]) {
-                s0 += val_of(w8[u].x);
-                s1 += val_of(w8[u].y);
+          if (G >= 32) {
+    #pragma unroll 1
+            for (int o = o_lo + warp; o < o_hi; o += nwarps) {
+              ulonglong2 w8[8];
+              const unsigned long long* p8[8];
+    #pragma unroll
+              for (int u = 0; u < 8; ++u) {
+                const int cc = lane + 32 * u;
+                p8[u] = cc < G ? a.part + (unsigned)cc * (unsigned)a.pstride + 2 * o : nullptr;
+                w8[u] = p8[u] ? get_pair(p8[u]) : make_ulonglong2(0ULL, 0ULL);
               }
-  #pragma unroll 1
-            for (int off = GL >> 1; off > 0; off >>= 1) {
-              s0 += __shfl_xor_sync(0xffffffffu, s0, off);
-              s1 += __shfl_xor_sync(0xffffffffu, s1, off);
+              if (ok) ok = wait_pairs<8>(p8, w8, tag, a);
+              float s0 = 0.f, s1 = 0.f;
+    #pragma unroll
+              for (int u = 0; u < 8; ++u)
+                if (p8[u]) {
+                  s0 += val_of(w8[u].x);
+                  s1 += val_of(w8[u].y);
+                }
+    #pragma unroll
+              for (int off = 16; off > 0; off >>= 1) {
+                s0 += __shfl_xor_sync(0xffffffffu, s0, off);
+                s1 += __shfl_xor_sync(0xffffffffu, s1, off);
+              }
+              if (ok)
+    #pragma unroll 1
+                for (int cc = lane; cc < G; cc += 32) put_pair(a.inbox + (unsigned)cc * (unsigned)a.pstride + 2 * o, tag, s0, s1);
             }
-            if (ok && live)
-  #pragma unroll 1
-              for (int cc = gl; cc < G; cc += GL) put_pair(a.inbox + (unsigned)cc * (unsigned)a.pstride + 2 * o, tag, s0, s1);
+          } else {
+            // GL = G rounded up to a power of two lanes per pair, one CTA per lane
+            const int GL = pow2_at_least(G);
+            const int lgl = 31 - __clz(GL);
+            const int sub = lane >> lgl, gl = lane & (GL - 1);
+    #pragma unroll 1
+            for (int ob = o_lo + (warp << (5 - lgl)); ob < o_hi; ob += nwarps << (5 - lgl)) {
+              const int o = ob + sub;
+              ulonglong2 w1[1];
+              const unsigned long long* p1[1];
+              p1[0] = (o < o_hi && gl < G) ? a.part + (unsigned)gl * (unsigned)a.pstride + 2 * o : nullptr;
+              w1[0] = p1[0] ? get_pair(p1[0]) : make_ulonglong2(0ULL, 0ULL);
+              if (ok) ok = wait_pairs<1>(p1, w1, tag, a);
+              float s0 = p1[0] ? val_of(w1[0].x) : 0.f, s1 = p1[0] ? val_of(w1[0].y) : 0.f;
+    #pragma unroll
+              for (int off = 16; off > 0; off >>= 1)
+                if (off < GL) {
+                  s0 += __shfl_xor_sync(0xffffffffu, s0, off);
+                  s1 += __shfl_xor_sync(0xffffffffu, s1, off);
+                }
+              if (ok && o < o_hi && gl < G)
+                put_pair(a.inbox + (unsigned)gl * (unsigned)a.pstride + 2 * o, tag, s0, s1);
+            }
           }
         }
         // hop 2: this CTA's copy of the reduced payload, into shared memory: g
@@ -926,24 +970,15 @@ __device__ __forceinline__ void epoch_body(const EpochArgs& a, const int G, cons
         {
           const unsigned long long* mine = a.inbox + (unsigned)c * (unsigned)a.pstride;
   #pragma unroll 1
-          for (int ob2 = tid; ob2 < (P >> 1); ob2 += 4 * T) {
-            ulonglong2 w4[4];
-            const unsigned long long* p4[4];
+          for (int o2 = tid; o2 < (P >> 1); o2 += T) {
+            ulonglong2 w1[1];
+            const unsigned long long* p1[1] = {mine + 2 * o2};
+            w1[0] = get_pair(p1[0]);
+            if (ok) ok = wait_pairs<1>(p1, w1, tag, a);
   #pragma unroll
-            for (int u = 0; u < 4; ++u) {
-              const int o2 = ob2 + u * T;
-              p4[u] = o2 < (P >> 1) ? mine + 2 * o2 : nullptr;
-              w4[u] = p4[u] ? get_pair(p4[u]) : make_ulonglong2(0ULL, 0ULL);
-            }
-            if (ok) ok = wait_pairs<4>(p4, w4, tag, a);
-  #pragma unroll 1
-            for (int uw = 0; uw < 8; ++uw) {
-              const int u = uw >> 1;
-              const int o2 = ob2 + u * T;
-              if (o2 >= (P >> 1)) break;
-              const ulonglong2 wv = u == 0 ? w4[0] : (u == 1 ? w4[1] : (u == 2 ? w4[2] : w4[3]));
-              const int o = 2 * o2 + (uw & 1);
-              const float v = val_of((uw & 1) == 0 ? wv.x : wv.y);
+            for (int u = 0; u < 2; ++u) {
+              const int o = 2 * o2 + u;
+              const float v = val_of(u == 0 ? w1[0].x : w1[0].y);
               if (o < Kx) {
                 const int r = fdiv(o >> 2, f_na4), j = o - r * Jq;
                 if (j < Jn) redsm[r * Jn + j] = v;
@@ -1439,6 +1474,16 @@ k_epoch_multi(MultiArgs m) {
   }
 }
 
+// One thread waits, through the epoch kernel's bounded wait, for a tag that
+// nothing writes: the watchdog must expire and record STD_ETIMEOUT in *err.
+__global__ void k_wait_probe(EpochArgs a, const unsigned long long* word) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  const unsigned long long* p[1] = {word};
+  unsigned long long w[1] = {get_word(word)};
+  const uint32_t tg[1] = {1u};
+  (void)wait_all<1>(p, w, tg, a);
+}
+
 namespace {
 
 const void* kernel_for(int precision) {
@@ -1483,6 +1528,15 @@ cudaError_t launch_epoch(const EpochArgs& a, int ctas, size_t smem, cudaStream_t
   EpochArgs copy = a;
   void* args[] = {&copy};
   return cudaLaunchCooperativeKernel(kernel_for(a.precision), dim3(ctas), dim3(kEpochThreads), args, smem, st);
+}
+
+cudaError_t launch_wait_probe(unsigned long long watchdog_ns, int* err, const unsigned long long* word,
+                              cudaStream_t st) {
+  EpochArgs a{};
+  a.err = err;
+  a.watchdog_ns = watchdog_ns;
+  k_wait_probe<<<1, 32, 0, st>>>(a, word);
+  return cudaGetLastError();
 }
 
 cudaError_t epoch_multi_setup(int precision, size_t smem) {

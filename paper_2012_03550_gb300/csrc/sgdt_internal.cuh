@@ -176,6 +176,8 @@ size_t epoch_smem_bytes(const Geometry& g, int chunk_max, int ctas, int precisio
 cudaError_t epoch_kernel_setup(int precision, size_t smem);
 int epoch_max_ctas(int precision, size_t smem);
 cudaError_t launch_epoch(const EpochArgs& a, int ctas, size_t smem, cudaStream_t st);
+cudaError_t launch_wait_probe(unsigned long long watchdog_ns, int* err, const unsigned long long* word,
+                              cudaStream_t st);
 cudaError_t epoch_multi_setup(int precision, size_t smem);
 int epoch_multi_max_ctas(int precision, size_t smem);
 cudaError_t launch_epoch_multi(const MultiArgs& m, int precision, int ctas, size_t smem, cudaStream_t st);

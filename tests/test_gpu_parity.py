@@ -460,3 +460,22 @@ def test_bf16_step_gradients_close_to_oracle(B, synth, cfg1):
         U = int(nseg[n])
         assert pr["nseg"][n] == U
         assert _rel(pr["factor_F"][n, :U, :5], F[n, :U, :5]) <= 2e-2
+
+
+def test_watchdog_expires_without_fault_and_device_stays_usable(B, cfg1):
+    """A bounded wait on a word nothing writes ends with STD_ETIMEOUT after
+    its budget (no trap, no hang); a normal epoch runs afterwards."""
+    import time
+    t0 = time.time()
+    assert B.std_watchdog_probe(2_000_000) == B.STD_ETIMEOUT      # 2 ms budget
+    assert time.time() - t0 < 5.0
+    with pytest.raises(B.StdError):
+        B.std_watchdog_probe(10)                                   # budget outside [1e3, 1e10]
+    t = cfg1.tensor
+    c, v = t.split("train")
+    g = B.Tucker(t.shape, cfg1.ranks, c, v, r_core=cfg1.r_core)
+    try:
+        st = g.epoch(cfg1.lr, cfg1.lr, cfg1.lam, cfg1.lam, cfg1.minibatch)
+        assert st["nnz"] == c.shape[0]
+    finally:
+        g.close()
