@@ -57,6 +57,8 @@ def _args():
     p.add_argument("--batched", action="store_true",
                    help="batched workload instead of the default line: 256 independent 3-order tensors "
                         "(lognormal sizes, J in {4, 8, 16}) in one persistent launch per epoch")
+    p.add_argument("--msweep", action="store_true",
+                   help="throughput against the minibatch size on the rating tensor (--scale, default 0.25)")
     p.add_argument("--serve", action="store_true",
                    help="open-loop serving run (job arrivals + query batches) instead of the epoch bench")
     p.add_argument("--serve-seconds", type=float, default=60.0)
@@ -501,6 +503,59 @@ def run_sweep(a):
     return 0
 
 
+def run_msweep(a):
+    """Throughput against the minibatch size M on the rating tensor (strict
+    Algorithm 1 at every M): the per-minibatch chain of dependent steps is
+    amortised over more samples as M grows.  The learning rate scales with
+    M / 4096 so that the step per epoch stays comparable."""
+    import numpy as np
+    import torch
+
+    import __graft_entry__ as ge
+    ge.build()
+    from paper_2012_03550_gb300 import binding as B
+    from paper_2012_03550_gb300 import synth
+
+    scale = a.scale if a.scale != 1.0 else 0.25
+    w = synth.config2(scale=scale)
+    t = w.tensor
+    c, v = t.split("train")
+    tc, tv = t.split("test")
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.Stream(device=dev)
+    dc, dv = torch.from_numpy(c).to(dev), torch.from_numpy(v).to(dev)
+    dtc, dtv = torch.from_numpy(tc).to(dev), torch.from_numpy(tv).to(dev)
+    A0, B0 = synth.init_params(t.shape, w.ranks, w.r_core, mode="rating", seed=1, mean_value=float(np.mean(v)))
+    for M in (1024, 2048, 4096, 8192, 16384):
+        lr = w.lr * M / 4096.0
+        opt = B.std_default_options()
+        opt.r_core = w.r_core
+        opt.ptr_kind = 1
+        opt.stream = stream.cuda_stream
+        ctx = B.std_create(t.order, t.shape, w.ranks, c.shape[0], dc, dv, opt)
+        B.std_set_params(ctx, [np.ascontiguousarray(x) for x in A0], [np.ascontiguousarray(x) for x in B0], 0)
+        for _ in range(a.warmup):
+            B.std_sgd_epoch(ctx, lr, lr, w.lam, w.lam, M)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(a.steps):
+            st = B.std_sgd_epoch(ctx, lr, lr, w.lam, w.lam, M)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / a.steps
+        rm = B.std_rmse(ctx, tc.shape[0], dtc, dtv)
+        B.std_destroy(ctx)
+        nb = (c.shape[0] + M - 1) // M
+        line = {"metric": "minibatch sweep: epoch throughput and test RMSE", "workload": w.name, "minibatch": M,
+                "lr": lr, "epochs": a.warmup + a.steps, "ms_per_epoch": ms, "value": c.shape[0] / (ms * 1e-3),
+                "unit": "nnz/s", "us_per_minibatch": 1e6 * st["update_seconds"] / nb, "test_rmse": rm[0],
+                "data": "synthetic"}
+        print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_batched(a):
     """Epochs of 256 independent decompositions in one launch per epoch, FP32 and
     BF16, against the same tensors run one after another on the whole GPU."""
@@ -696,6 +751,8 @@ def main():
         return run_reference(a)
     if a.sweep:
         return run_sweep(a)
+    if a.msweep:
+        return run_msweep(a)
     if a.batched:
         return run_batched(a)
     if a.serve:
