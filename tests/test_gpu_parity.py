@@ -479,3 +479,30 @@ def test_watchdog_expires_without_fault_and_device_stays_usable(B, cfg1):
         assert st["nnz"] == c.shape[0]
     finally:
         g.close()
+
+
+# ---------------------------------------------------------------------------
+# Full size: the Netflix-shaped 100M-nonzero workload in the bench's launch
+# configuration (152 CTAs, M = 4096), checked on sampled minibatches the
+# oracle computes one by one
+# ---------------------------------------------------------------------------
+
+@pytest.fixture(scope="module")
+def full2(synth):
+    return synth.config2(scale=1.0)
+
+
+def test_fullsize_schedule_bitexact_sampled_minibatches(B, full2):
+    t = full2.tensor
+    c, v = t.split("train")
+    M = full2.minibatch
+    nb = (c.shape[0] + M - 1) // M
+    assert c.shape[0] % M != 0          # the last minibatch is ragged
+    with B.Tucker(t.shape, full2.ranks, c, v, r_core=full2.r_core) as g:
+        for b in (0, nb // 2, nb - 1):
+            _check_schedule(B, g, c, M, (b, b + 1))
+
+
+def test_fullsize_step_gradients_first_minibatch(B, synth, full2):
+    _step_case(B, synth, full2.tensor, full2.ranks, full2.r_core, full2.minibatch, batch=0, init="rating",
+               lr=(0.05, 0.05))
