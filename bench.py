@@ -602,6 +602,7 @@ def run_batched(a):
         for _ in range(a.steps):
             st = B.std_batch_epoch(bt, lr, lr, lam, lam, M)
             secs.append(st["seconds"])
+        sizes = B.std_batch_groups(bt, len(ctxs))
         B.std_batch_destroy(bt)
         # test RMSE over all members (weighted by test entries)
         se, cnt = 0.0, 0
@@ -627,14 +628,20 @@ def run_batched(a):
         for ctx in ctxs:
             B.std_destroy(ctx)
         ms = 1e3 * sum(secs) / len(secs)
+        hist = {}
+        for g in sizes:
+            hist[str(g)] = hist.get(str(g), 0) + 1
         lines[precision] = {"value": n_train / (ms * 1e-3), "ms_per_epoch": ms, "ctas_per_tensor": st["ctas_per_tensor"],
+                            "tensors_by_group_size": hist, "graph_replayed": st["graph_replayed"],
                             "test_rmse": (se / cnt) ** 0.5 if cnt else None, "sequential_value": seq}
     line = {"metric": "batched SGD_Tucker: sampled nonzeros/s per epoch over all tensors", "value": lines[0]["value"],
             "unit": "nnz/s", "n_gpus": 1, "steps": a.steps, "warmup": a.warmup,
             "ms_per_step": lines[0]["ms_per_epoch"], "higher_is_better": True, "dtype": "f32", "data": "synthetic",
             "config": {"workload": f"batched-{len(specs)}-tensors-{n_train}", "tensors": len(specs),
                        "nnz_train": n_train, "minibatch": M, "ranks": "J in {4, 8, 16}, R = min(5, J)",
-                       "ctas_per_tensor": lines[0]["ctas_per_tensor"], "datagen_s": round(gen_s, 1),
+                       "ctas_per_tensor": lines[0]["ctas_per_tensor"],
+                       "tensors_by_group_size": lines[0]["tensors_by_group_size"],
+                       "graph_replayed": lines[0]["graph_replayed"], "datagen_s": round(gen_s, 1),
                        "step": "one epoch of every tensor in one persistent launch (samplers and tilers before it)"},
             "test_rmse": lines[0]["test_rmse"],
             "one_after_another_value": lines[0]["sequential_value"],

@@ -216,10 +216,14 @@ const char* std_last_error(void);
  * epoch.
  *   count, ctxs       the contexts (same precision, same stream; each at most
  *                     once); they must outlive the batch, which does not own them
- *   ctas_per_tensor   CTAs per tensor; 0 = chosen on the first step by
- *                     timing each power of two up to 32 that fits on a run
- *                     of 3% of every tensor's minibatches that writes no
- *                     parameter (the autotuner)
+ *   ctas_per_tensor   CTAs per tensor, the same for every tensor; 0 = a base
+ *                     size chosen on the first step by timing each power of
+ *                     two up to 32 that fits on a run of 3% of every tensor's
+ *                     minibatches that writes no parameter (the autotuner),
+ *                     and, at every launch, a group of 2^k times the base
+ *                     size (up to 32 CTAs, chunks of at least 8 samples) for
+ *                     each tensor whose work alone exceeds the average load
+ *                     of a base group (std_batch_groups reports the sizes)
  * Errors: STD_EINVAL, STD_ECUDA.
  */
 typedef struct std_batch std_batch;
@@ -246,6 +250,11 @@ typedef struct {
  * STD_ENOMEM, STD_ECUDA, STD_ETIMEOUT. */
 int std_batch_step(std_batch* batch, float lr_a, float lr_b, float lambda_a, float lambda_b,
                    int32_t minibatch, int64_t max_batches, std_batch_stats* out);
+
+/* CTAs each tensor of the batch had in the last launch (count entries, in
+ * the order of std_batch_create; 0 before the first launch).  A tensor's
+ * result equals std_sgd_epoch's with that many CTAs. */
+int std_batch_groups(const std_batch* batch, int32_t* ctas_per_tensor);
 
 /* std_batch_step without a limit: every tensor finishes its current epoch. */
 int std_batch_epoch(std_batch* batch, float lr_a, float lr_b, float lambda_a, float lambda_b,

@@ -121,6 +121,7 @@ SIGNATURES = {
     "std_reserve": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int64]),
     "std_device_bytes": (ctypes.c_int, [_P, _P]),
     "std_watchdog_probe": (ctypes.c_int, [ctypes.c_uint64, _P]),
+    "std_batch_groups": (ctypes.c_int, [_P, _P]),
 }
 
 
@@ -385,6 +386,12 @@ def std_device_bytes(ctx):
     return b.value
 
 
+def std_batch_groups(batch, count):
+    out = (ctypes.c_int32 * int(count))()
+    _check(lib().std_batch_groups(batch, ctypes.cast(out, ctypes.c_void_p)))
+    return [int(x) for x in out]
+
+
 def std_watchdog_probe(watchdog_ns):
     st = ctypes.c_int32()
     _check(lib().std_watchdog_probe(int(watchdog_ns), ctypes.byref(st)))
@@ -407,6 +414,9 @@ class Batch:
 
     def step(self, lr_a, lr_b, lam_a, lam_b, minibatch, max_batches):
         return std_batch_step(self.ptr, lr_a, lr_b, lam_a, lam_b, minibatch, max_batches)
+
+    def groups(self):
+        return std_batch_groups(self.ptr, len(self.members))
 
     def close(self):
         if self.ptr is not None:

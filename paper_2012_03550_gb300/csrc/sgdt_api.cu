@@ -766,25 +766,29 @@ struct std_batch {
   std::vector<std_ctx*> ctxs;
   cudaStream_t stream = nullptr;
   int precision = 0;
-  int group = 0;          // CTAs per tensor; 0 until tuned
+  int group = 0;          // CTAs per tensor (the base size); 0 until tuned
   bool tuned = false;
+  bool promote = false;   // long tensors may get groups of 2^k x group CTAs
+  std::vector<int> last_g; // CTAs each tensor had in the last launch
   int* err = nullptr;     // one error word shared by every tensor of a launch
   EpochArgs* d_items = nullptr;
   int* d_order = nullptr;
   int* d_first = nullptr;
+  int* d_gstart = nullptr;
   size_t cap_items = 0, cap_groups = 0;
   // pinned host staging of the launch arguments (fixed addresses, so that a
   // captured graph copies their current contents at every replay)
   EpochArgs* h_items = nullptr;
   int* h_order = nullptr;
   int* h_first = nullptr;
+  int* h_gstart = nullptr;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr, evm = nullptr;
   // the launch sequence (barrier resets, argument uploads, the cooperative
   // kernel) captured as a CUDA graph and replayed while its shape holds
   cudaStream_t cap_stream = nullptr;
   cudaGraphExec_t gexec = nullptr;
   std::vector<std_ctx*> gkey_ctxs;
-  int gkey_G = 0, gkey_groups = 0;
+  int gkey_ctas = 0, gkey_groups = 0;
   size_t gkey_smem = 0;
   const void* gkey_items = nullptr;
   bool replayed = false;   // the last launch replayed the graph
@@ -801,10 +805,15 @@ size_t batch_smem(std_ctx* c, int M, int G) {
   return sm > 227 * 1024 ? 0 : sm;
 }
 
-// One launch of minibatches range[t] = [b0, b1) of every tensor t at group
-// size G; dry = no parameter writes (timing runs of the tuner).
+// One launch of minibatches range[t] = [b0, b1) of every tensor t; dry = no
+// parameter writes (timing runs of the tuner).  Every tensor runs on a group
+// of G CTAs, except, when promote is set, the tensors that would set the
+// makespan: those get a group of their own of G * 2^k CTAs (up to 32 CTAs
+// and chunks of at least 8 samples), doubled one at a time while the
+// estimated makespan falls.  The other tensors go longest-first to the
+// least-loaded base group.
 int batch_launch(std_batch* bt, float lr_a, float lr_b, float lam_a, float lam_b, int32_t M,
-                 const std::vector<std::pair<int64_t, int64_t>>& range, int G, bool dry) {
+                 const std::vector<std::pair<int64_t, int64_t>>& range, int G, bool dry, bool promote) {
   const int T = (int)bt->ctxs.size();
   size_t smem = 0;
   if ((size_t)T > bt->cap_items) {
@@ -814,27 +823,35 @@ int batch_launch(std_batch* bt, float lr_a, float lr_b, float lam_a, float lam_b
     cudaFree(bt->d_items);
     cudaFree(bt->d_order);
     cudaFree(bt->d_first);
+    cudaFree(bt->d_gstart);
     cudaFreeHost(bt->h_items);
     cudaFreeHost(bt->h_order);
     cudaFreeHost(bt->h_first);
+    cudaFreeHost(bt->h_gstart);
     bt->d_items = nullptr;
     bt->d_order = nullptr;
     bt->d_first = nullptr;
+    bt->d_gstart = nullptr;
     bt->h_items = nullptr;
     bt->h_order = nullptr;
     bt->h_first = nullptr;
+    bt->h_gstart = nullptr;
     bt->cap_items = 0;
     const size_t ci = (size_t)T, cg = (size_t)(T + 1);
     STD_CUDA(cudaMalloc((void**)&bt->d_items, ci * sizeof(EpochArgs)), "batch arguments");
     STD_CUDA(cudaMalloc((void**)&bt->d_order, ci * sizeof(int)), "batch order");
     STD_CUDA(cudaMalloc((void**)&bt->d_first, cg * sizeof(int)), "batch groups");
+    STD_CUDA(cudaMalloc((void**)&bt->d_gstart, cg * sizeof(int)), "batch group starts");
     STD_CUDA(cudaMallocHost((void**)&bt->h_items, ci * sizeof(EpochArgs)), "batch arguments (host)");
     STD_CUDA(cudaMallocHost((void**)&bt->h_order, ci * sizeof(int)), "batch order (host)");
     STD_CUDA(cudaMallocHost((void**)&bt->h_first, cg * sizeof(int)), "batch groups (host)");
+    STD_CUDA(cudaMallocHost((void**)&bt->h_gstart, cg * sizeof(int)), "batch group starts (host)");
     bt->cap_items = ci;
     bt->cap_groups = cg;
   }
-  std::vector<std::pair<int64_t, int>> work;
+  // work estimates and the base-size shared memory (a larger group has
+  // smaller chunks, so the base size bounds every tensor's need)
+  std::vector<int64_t> w(T), e0v(T), e1v(T);
   for (int t = 0; t < T; ++t) {
     std_ctx* c = bt->ctxs[t];
     int rc = ensure_schedule(c, M);
@@ -842,50 +859,134 @@ int batch_launch(std_batch* bt, float lr_a, float lr_b, float lam_a, float lam_b
     const size_t sm = batch_smem(c, M, G);
     if (sm == 0) return set_error(STD_EUNSUPPORTED, "a tensor of the batch does not fit a CTA at this group size");
     smem = sm > smem ? sm : smem;
-    rc = ensure_scratch(c, G, payload_floats(c->g), M);
-    if (rc) return rc;
     const int64_t nb = (c->nnz + M - 1) / M;
-    const int64_t e0 = range[t].first < nb ? range[t].first : nb;
-    const int64_t e1 = range[t].second < nb ? range[t].second : nb;
-    uint32_t tag_base = 0;
-    rc = reserve_tags(c, e1 - e0, &tag_base);
+    e0v[t] = range[t].first < nb ? range[t].first : nb;
+    e1v[t] = range[t].second < nb ? range[t].second : nb;
+    // time per minibatch ~ a fixed chain of dependent steps plus a part that
+    // grows with the per-sample work (fit of measured times at M = 256:
+    // 34 us + 0.17 us x (sum J + prod J / max J))
+    w[t] = (e1v[t] - e0v[t]) * (int64_t)(192 + c->g.sumJ + c->g.prodJ / c->g.Jmax);
+  }
+  STD_CUDA(epoch_multi_setup(bt->precision, smem), "batched kernel attributes");
+  const int maxc = epoch_multi_max_ctas(bt->precision, smem);
+  if (maxc / G < 1) return set_error(STD_EUNSUPPORTED, "batched kernel cannot be resident at this group size");
+  // longest processing time first
+  std::vector<int> byw(T);
+  for (int t = 0; t < T; ++t) byw[t] = t;
+  std::sort(byw.begin(), byw.end(), [&](int x, int y) { return w[x] != w[y] ? w[x] > w[y] : x < y; });
+  std::vector<int> gt(T, G);
+  int promoted_ctas = 0, promoted = 0;
+  if (promote) {
+    // greedy on the estimated makespan: a tensor's time at 2^k x G CTAs is
+    // its work times kSpeed[k] (measured per-minibatch times at M = 256,
+    // J in {4, 8, 16}: about 0.77 for the first doubling, 0.86 for the next);
+    // the base groups finish after max(their mean load, their longest tensor)
+    static const double kSpeed[6] = {1.0, 0.77, 0.66, 0.63, 0.62, 0.62};
+    std::vector<int> lv(T, 0);
+    auto makespan = [&](const std::vector<int>& lvl, int pctas) {
+      const int nb0 = (maxc - pctas) / G;
+      if (nb0 < 1) return 1e300;
+      double base_sum = 0.0, base_max = 0.0, prom_max = 0.0;
+      int nbase_t = 0;
+      for (int t = 0; t < T; ++t) {
+        if (lvl[t] == 0) {
+          base_sum += (double)w[t];
+          base_max = (double)w[t] > base_max ? (double)w[t] : base_max;
+          ++nbase_t;
+        } else {
+          const double e = (double)w[t] * kSpeed[lvl[t]];
+          prom_max = e > prom_max ? e : prom_max;
+        }
+      }
+      const int ng = nb0 < nbase_t ? nb0 : nbase_t;
+      const double base_span = nbase_t == 0 ? 0.0 : (base_sum / (ng > 0 ? ng : 1) > base_max ? base_sum / ng : base_max);
+      return base_span > prom_max ? base_span : prom_max;
+    };
+    double cur = makespan(lv, 0);
+    int pctas = 0;
+#pragma unroll 1
+    for (int it = 0; it < 4 * T; ++it) {
+      // the tensor that sets the makespan: the longest at its current size
+      int bt_t = -1;
+      double bt_e = -1.0;
+      for (int t = 0; t < T; ++t) {
+        const double e = (double)w[t] * kSpeed[lv[t]];
+        if (e > bt_e) {
+          bt_e = e;
+          bt_t = t;
+        }
+      }
+      const int g_now = G << lv[bt_t], g_new = g_now * 2;
+      if (g_new > 32 || M / g_new < 8 || lv[bt_t] >= 5) break;
+      const int extra = lv[bt_t] == 0 ? g_new : g_now;
+      if (pctas + extra > maxc - G) break;
+      std::vector<int> nx = lv;
+      nx[bt_t] += 1;
+      const double e = makespan(nx, pctas + extra);
+      if (!(e < cur)) break;
+      lv = nx;
+      pctas += extra;
+      cur = e;
+    }
+    for (int t = 0; t < T; ++t)
+      if (lv[t] > 0) {
+        gt[t] = G << lv[t];
+        promoted_ctas += gt[t];
+        ++promoted;
+      }
+  }
+  int nbase = (maxc - promoted_ctas) / G;
+  if (nbase > T - promoted) nbase = T - promoted;
+  const int groups = promoted + nbase;
+  if (groups < 1) return set_error(STD_EUNSUPPORTED, "batched kernel cannot be resident at this group size");
+  std::vector<std::vector<int>> lists(groups);
+  std::vector<int> gsize(groups, G);
+  {
+    int q = 0;
+    for (int t : byw)
+      if (gt[t] > G) {
+        lists[q].push_back(t);
+        gsize[q] = gt[t];
+        ++q;
+      }
+    std::vector<int64_t> load(nbase, 0);
+    for (int t : byw) {
+      if (gt[t] > G) continue;
+      int b = 0;
+      for (int k = 1; k < nbase; ++k)
+        if (load[k] < load[b]) b = k;
+      load[b] += w[t];
+      lists[promoted + b].push_back(t);
+    }
+  }
+  bt->last_g = gt;
+  for (int t = 0; t < T; ++t) {
+    std_ctx* c = bt->ctxs[t];
+    int rc = ensure_scratch(c, gt[t], payload_floats(c->g), M);
     if (rc) return rc;
-    EpochArgs a = epoch_args(c, lr_a, lr_b, lam_a, lam_b, e0, e1, (M + G - 1) / G, tag_base);
+    uint32_t tag_base = 0;
+    rc = reserve_tags(c, e1v[t] - e0v[t], &tag_base);
+    if (rc) return rc;
+    EpochArgs a = epoch_args(c, lr_a, lr_b, lam_a, lam_b, e0v[t], e1v[t], (M + gt[t] - 1) / gt[t], tag_base);
     a.err = bt->err;
     a.dry = dry ? 1 : 0;
     if (dry) a.momentum = 0.f;
     bt->h_items[t] = a;
-    work.push_back({(e1 - e0) * (int64_t)M * (c->g.sumJ + c->g.prodJ / c->g.Jmax), t});
-  }
-  STD_CUDA(epoch_multi_setup(bt->precision, smem), "batched kernel attributes");
-  const int maxc = epoch_multi_max_ctas(bt->precision, smem);
-  int groups = maxc / G;
-  if (groups > T) groups = T;
-  if (groups < 1) return set_error(STD_EUNSUPPORTED, "batched kernel cannot be resident at this group size");
-  // longest processing time first: tensors by decreasing work to the least-loaded group
-  std::sort(work.begin(), work.end(), [](const std::pair<int64_t, int>& x, const std::pair<int64_t, int>& y) {
-    return x.first != y.first ? x.first > y.first : x.second < y.second;
-  });
-  std::vector<int64_t> load(groups, 0);
-  std::vector<std::vector<int>> lists(groups);
-  for (auto& w : work) {
-    int q = 0;
-    for (int k = 1; k < groups; ++k)
-      if (load[k] < load[q]) q = k;
-    load[q] += w.first;
-    lists[q].push_back(w.second);
   }
   int no = 0;
   bt->h_first[0] = 0;
+  bt->h_gstart[0] = 0;
   for (int q = 0; q < groups; ++q) {
     for (int t : lists[q]) bt->h_order[no++] = t;
     bt->h_first[q + 1] = no;
+    bt->h_gstart[q + 1] = bt->h_gstart[q] + gsize[q];
   }
+  const int ctas = bt->h_gstart[groups];
   // (re)capture the launch sequence when its shape changed: the tensors (their
   // barrier words), the group size, the group count, the shared memory and
   // the argument buffers; otherwise replay it (the copies read the pinned
   // staging, so the new ranges, order and flags reach the device)
-  const bool same = bt->gexec && bt->gkey_ctxs == bt->ctxs && bt->gkey_G == G && bt->gkey_groups == groups &&
+  const bool same = bt->gexec && bt->gkey_ctxs == bt->ctxs && bt->gkey_ctas == ctas && bt->gkey_groups == groups &&
                     bt->gkey_smem == smem && bt->gkey_items == (const void*)bt->d_items;
   bt->replayed = same;
   if (!same) {
@@ -903,13 +1004,17 @@ int batch_launch(std_batch* bt, float lr_a, float lr_b, float lam_a, float lam_b
       e = cudaMemcpyAsync(bt->d_order, bt->h_order, (size_t)T * sizeof(int), cudaMemcpyHostToDevice, cs);
     if (e == cudaSuccess)
       e = cudaMemcpyAsync(bt->d_first, bt->h_first, (size_t)(groups + 1) * sizeof(int), cudaMemcpyHostToDevice, cs);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(bt->d_gstart, bt->h_gstart, (size_t)(groups + 1) * sizeof(int), cudaMemcpyHostToDevice,
+                          cs);
     if (e == cudaSuccess) {
       MultiArgs m{};
       m.items = bt->d_items;
       m.order = bt->d_order;
       m.first = bt->d_first;
-      m.group = G;
-      e = launch_epoch_multi(m, bt->precision, groups * G, smem, cs);
+      m.gstart = bt->d_gstart;
+      m.groups = groups;
+      e = launch_epoch_multi(m, bt->precision, ctas, smem, cs);
     }
     cudaGraph_t graph = nullptr;
     const cudaError_t e2 = cudaStreamEndCapture(cs, &graph);
@@ -921,7 +1026,7 @@ int batch_launch(std_batch* bt, float lr_a, float lr_b, float lam_a, float lam_b
       return cuda_error(e, "batched launch graph");
     }
     bt->gkey_ctxs = bt->ctxs;
-    bt->gkey_G = G;
+    bt->gkey_ctas = ctas;
     bt->gkey_groups = groups;
     bt->gkey_smem = smem;
     bt->gkey_items = bt->d_items;
@@ -964,6 +1069,7 @@ int std_batch_create(std_batch** out, int32_t count, std_ctx* const* ctxs, int32
   bt->precision = ctxs[0]->opt.precision;
   bt->group = ctas_per_tensor;
   bt->tuned = ctas_per_tensor > 0;
+  bt->promote = ctas_per_tensor == 0;
   cudaError_t e = cudaMalloc((void**)&bt->err, sizeof(int));
   if (e == cudaSuccess) e = cudaMemset(bt->err, 0, sizeof(int));
   if (e == cudaSuccess) e = cudaEventCreate(&bt->ev0);
@@ -986,9 +1092,11 @@ int std_batch_destroy(std_batch* bt) {
   cudaFree(bt->d_items);
   cudaFree(bt->d_order);
   cudaFree(bt->d_first);
+  cudaFree(bt->d_gstart);
   cudaFreeHost(bt->h_items);
   cudaFreeHost(bt->h_order);
   cudaFreeHost(bt->h_first);
+  cudaFreeHost(bt->h_gstart);
   if (bt->ev0) cudaEventDestroy(bt->ev0);
   if (bt->ev1) cudaEventDestroy(bt->ev1);
   if (bt->evm) cudaEventDestroy(bt->evm);
@@ -1022,7 +1130,7 @@ int std_batch_step(std_batch* bt, float lr_a, float lr_b, float lambda_a, float 
       for (std_ctx* c : bt->ctxs)
         if (batch_smem(c, minibatch, G) == 0) fits = false;
       if (!fits) continue;
-      rc = batch_launch(bt, lr_a, lr_b, lambda_a, lambda_b, minibatch, trial, G, true);
+      rc = batch_launch(bt, lr_a, lr_b, lambda_a, lambda_b, minibatch, trial, G, true, bt->promote);
       if (rc == STD_EUNSUPPORTED) continue;
       if (rc) return rc;
       float ms = 0.f;
@@ -1046,7 +1154,7 @@ int std_batch_step(std_batch* bt, float lr_a, float lr_b, float lambda_a, float 
     const int64_t t1 = e1 * (int64_t)minibatch < c->nnz ? e1 * (int64_t)minibatch : c->nnz;
     nnz += t1 - c->cursor * (int64_t)minibatch;
   }
-  rc = batch_launch(bt, lr_a, lr_b, lambda_a, lambda_b, minibatch, range, bt->group, false);
+  rc = batch_launch(bt, lr_a, lr_b, lambda_a, lambda_b, minibatch, range, bt->group, false, bt->promote);
   if (rc) return rc;
   for (size_t t = 0; t < bt->ctxs.size(); ++t) {
     std_ctx* c = bt->ctxs[t];
@@ -1071,6 +1179,13 @@ int std_batch_step(std_batch* bt, float lr_a, float lr_b, float lambda_a, float 
     out->graph_replayed = bt->replayed ? 1 : 0;
     out->reserved = 0;
   }
+  return STD_OK;
+}
+
+int std_batch_groups(const std_batch* bt, int32_t* ctas_per_tensor) {
+  if (!bt || !ctas_per_tensor) return set_error(STD_EINVAL, "batch or output is NULL");
+  for (size_t t = 0; t < bt->ctxs.size(); ++t)
+    ctas_per_tensor[t] = t < bt->last_g.size() ? bt->last_g[t] : 0;
   return STD_OK;
 }
 

@@ -1454,14 +1454,17 @@ k_epoch(EpochArgs a) {
 }
 
 // Many independent tensors in one persistent launch: the grid is split into
-// groups of m.group CTAs; group q runs the epochs of the tensors
-// m.order[m.first[q] .. m.first[q+1]) one after the other, each on its own
-// arguments (copied into shared memory) and exchange buffers.
+// groups of CTAs [m.gstart[q], m.gstart[q+1]); group q runs the epochs of the
+// tensors m.order[m.first[q] .. m.first[q+1]) one after the other, each on
+// its own arguments (copied into shared memory) and exchange buffers.
 template <bool BF>
 __global__ void __launch_bounds__(kEpochThreads, 1)
 k_epoch_multi(MultiArgs m) {
   __shared__ __align__(16) EpochArgs s_a;
-  const int grp = blockIdx.x / m.group, c = blockIdx.x - grp * m.group;
+  int grp = 0;
+#pragma unroll 1
+  while (grp + 1 < m.groups && m.gstart[grp + 1] <= (int)blockIdx.x) ++grp;
+  const int G = m.gstart[grp + 1] - m.gstart[grp], c = (int)blockIdx.x - m.gstart[grp];
 #pragma unroll 1
   for (int q = m.first[grp]; q < m.first[grp + 1]; ++q) {
     const int* src = reinterpret_cast<const int*>(m.items + m.order[q]);
@@ -1469,7 +1472,7 @@ k_epoch_multi(MultiArgs m) {
 #pragma unroll 1
     for (int i = threadIdx.x; i < (int)(sizeof(EpochArgs) / 4); i += blockDim.x) dst[i] = src[i];
     __syncthreads();
-    epoch_body<BF>(s_a, m.group, c);
+    epoch_body<BF>(s_a, G, c);
     __syncthreads();
   }
 }

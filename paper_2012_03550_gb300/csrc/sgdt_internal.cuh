@@ -156,8 +156,9 @@ struct EpochArgs {
 struct MultiArgs {
   const EpochArgs* items;
   const int* order;
-  const int* first;
-  int group;
+  const int* first;    // group q runs order[first[q] .. first[q+1])
+  const int* gstart;   // group q owns CTAs [gstart[q], gstart[q+1])
+  int groups;
 };
 
 // Factor-matrix pointers passed to kernels by value.

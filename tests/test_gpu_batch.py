@@ -78,19 +78,57 @@ def test_batch_equals_each_tensor_alone(B, synth, group, opts):
 
 
 def test_batch_tuner_writes_nothing_and_matches_alone(B, synth):
+    """Tuned base size plus larger groups for the long tensors: each tensor
+    equals its run alone with the CTAs it was given."""
     M, lr, lam = 256, 0.1, 1e-3
     batched = _members(B, synth)
     with B.Batch([m[1] for m in batched], ctas_per_tensor=0) as bt:
         st = bt.epoch(lr, lr, lam, lam, M)
         group = st["ctas_per_tensor"]
-        assert group >= 1
-    alone = _members(B, synth, ctas=group)
-    for m in alone:
-        m[1].epoch(lr, lr, lam, lam, M)
-    for a, b in zip(batched, alone):
-        assert _params_equal(a[1], b[1])
-    for m in batched + alone:
+        sizes = bt.groups()
+    assert group >= 1 and len(sizes) == len(SPECS)
+    assert all(g >= group and g % group == 0 for g in sizes)
+    for k, (a, g) in enumerate(zip(batched, sizes)):
+        shape, nnz, ranks, R, dists = SPECS[k]
+        t, _, A0, B0, _, _ = a
+        c, v = t.split("train")
+        alone = B.Tucker(shape, ranks, c, v, r_core=R, ctas=g)
+        alone.set_params(A0, B0, epoch=0)
+        alone.epoch(lr, lr, lam, lam, M)
+        assert _params_equal(a[1], alone)
+        alone.close()
+    for m in batched:
         m[1].close()
+
+
+def test_batch_long_tensor_gets_a_larger_group(B, synth):
+    """One tensor far longer than the rest is promoted to a group of 2^k x the
+    base size, and still equals its run alone with that many CTAs."""
+    M, lr, lam = 256, 0.1, 1e-3
+    specs = [((400, 300, 200), 60000, (8, 8, 8), 5, [("uniform",)] * 3)] + \
+            [((60, 50, 40), 1500, (4, 4, 4), 3, [("uniform",)] * 3)] * 12
+    mem = []
+    for k, (shape, nnz, ranks, R, dists) in enumerate(specs):
+        t = synth.make_tensor(shape, nnz, dists, ranks, 0.05, 0.1, seed=500 + k)
+        c, v = t.split("train")
+        A0, B0 = synth.init_params(shape, ranks, R, mode="normal", seed=1)
+        g = B.Tucker(shape, ranks, c, v, r_core=R)
+        g.set_params(A0, B0, epoch=0)
+        mem.append((t, g, A0, B0, shape, ranks, R))
+    with B.Batch([m[1] for m in mem], ctas_per_tensor=0) as bt:
+        st = bt.epoch(lr, lr, lam, lam, M)
+        sizes = bt.groups()
+    base = st["ctas_per_tensor"]
+    assert sizes[0] == max(sizes) and (sizes[0] > base or base == 32), (sizes, base)
+    assert all(n == base for n in sizes[1:])
+    for (t, g, A0, B0, shape, ranks, R), n in zip(mem, sizes):
+        c, v = t.split("train")
+        alone = B.Tucker(shape, ranks, c, v, r_core=R, ctas=n)
+        alone.set_params(A0, B0, epoch=0)
+        alone.epoch(lr, lr, lam, lam, M)
+        assert _params_equal(g, alone)
+        alone.close()
+        g.close()
 
 
 def test_batch_member_tracks_oracle(B, synth):
