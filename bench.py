@@ -68,7 +68,9 @@ def _args():
     p.add_argument("--serve-pool", type=int, default=48, help="distinct job tensors generated up front")
     p.add_argument("--serve-budget-gb", type=float, default=120.0)
     p.add_argument("--serve-batches", type=int, default=32, help="minibatches per job per tick")
-    p.add_argument("--serve-ctas", type=int, default=4, help="CTAs per job (0 = tuned at the first tick)")
+    p.add_argument("--serve-ctas", type=int, default=4,
+                   help="CTAs per job; 0 = tuned at the first tick; -1 = from each job's own size "
+                        "(4 below 400k nonzeros, 8 below 1.2M, else 16)")
     p.add_argument("--serve-seed", type=int, default=0)
     p.add_argument("--serve-fp32", action="store_true")
     p.add_argument("--sweep", action="store_true",
@@ -673,8 +675,11 @@ def run_serve(a):
     gen_s = time.time() - t0
     M, lr, lam = 256, 1e-3, 1e-3
     eng = serve.CudaEngine(precision=0 if a.serve_fp32 else 1, max_query=4096)
+    def by_size(job):
+        return 4 if job.nnz < 400_000 else (8 if job.nnz < 1_200_000 else 16)
+
     srv = serve.Server(eng, budget_bytes=int(a.serve_budget_gb * 1e9), batches_per_tick=a.serve_batches,
-                       ctas_per_tensor=a.serve_ctas)
+                       ctas_per_tensor=by_size if a.serve_ctas < 0 else a.serve_ctas)
     # arrival times (s from the start): jobs and query batches, both Poisson
     jobs_t = np.cumsum(rng.exponential(1.0 / a.serve_rate, size=int(a.serve_rate * a.serve_seconds * 2) + 16))
     jobs_t = jobs_t[jobs_t < a.serve_seconds]
@@ -737,7 +742,8 @@ def run_serve(a):
                                f"{a.serve_epochs} epochs each, M = {M}, lr = lambda = 1e-3; a pool of "
                                f"{len(pool)} distinct tensors, each arrival with its own seeds",
                        "budget_gb": a.serve_budget_gb, "batches_per_tick": a.serve_batches,
-                       "ctas_per_tensor": srv.group, "window_s": round(window_s, 2),
+                       "ctas_per_job": "4 / 8 / 16 by the job's nonzeros (<400k / <1.2M / more)"
+                       if a.serve_ctas < 0 else srv.group, "window_s": round(window_s, 2),
                        "drain_s": round(total_s - window_s, 2), "datagen_s": round(gen_s, 1)},
             "job_epoch_p50_s": r["job_epoch_p50_s"], "job_epoch_p99_s": r["job_epoch_p99_s"],
             "job_p50_s": r["job_p50_s"], "job_p99_s": r["job_p99_s"],

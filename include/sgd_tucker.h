@@ -251,6 +251,14 @@ typedef struct {
 int std_batch_step(std_batch* batch, float lr_a, float lr_b, float lambda_a, float lambda_b,
                    int32_t minibatch, int64_t max_batches, std_batch_stats* out);
 
+/* Fix each tensor's group size (count entries in [1, 32], in the order of
+ * std_batch_create): no tuner and no promotion; tensors of one size share
+ * groups of that size, and each size class gets groups while its estimated
+ * finish is the latest and CTAs remain.  A tensor's result then depends only
+ * on its own size, not on the other tensors (the serving loop sizes each job
+ * from its own shape).  Errors: STD_EINVAL. */
+int std_batch_set_groups(std_batch* batch, const int32_t* ctas_per_tensor);
+
 /* CTAs each tensor of the batch had in the last launch (count entries, in
  * the order of std_batch_create; 0 before the first launch).  A tensor's
  * result equals std_sgd_epoch's with that many CTAs. */

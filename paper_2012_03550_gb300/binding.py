@@ -122,6 +122,7 @@ SIGNATURES = {
     "std_device_bytes": (ctypes.c_int, [_P, _P]),
     "std_watchdog_probe": (ctypes.c_int, [ctypes.c_uint64, _P]),
     "std_batch_groups": (ctypes.c_int, [_P, _P]),
+    "std_batch_set_groups": (ctypes.c_int, [_P, _P]),
 }
 
 
@@ -392,6 +393,11 @@ def std_batch_groups(batch, count):
     return [int(x) for x in out]
 
 
+def std_batch_set_groups(batch, sizes):
+    arr = (ctypes.c_int32 * len(sizes))(*[int(x) for x in sizes])
+    _check(lib().std_batch_set_groups(batch, ctypes.cast(arr, ctypes.c_void_p)))
+
+
 def std_watchdog_probe(watchdog_ns):
     st = ctypes.c_int32()
     _check(lib().std_watchdog_probe(int(watchdog_ns), ctypes.byref(st)))
@@ -417,6 +423,9 @@ class Batch:
 
     def groups(self):
         return std_batch_groups(self.ptr, len(self.members))
+
+    def set_groups(self, sizes):
+        std_batch_set_groups(self.ptr, sizes)
 
     def close(self):
         if self.ptr is not None:

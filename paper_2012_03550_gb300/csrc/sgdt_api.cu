@@ -769,6 +769,7 @@ struct std_batch {
   int group = 0;          // CTAs per tensor (the base size); 0 until tuned
   bool tuned = false;
   bool promote = false;   // long tensors may get groups of 2^k x group CTAs
+  std::vector<int> fixed_g; // per-tensor group sizes set by the caller (empty: none)
   std::vector<int> last_g; // CTAs each tensor had in the last launch
   int* err = nullptr;     // one error word shared by every tensor of a launch
   EpochArgs* d_items = nullptr;
@@ -856,7 +857,8 @@ int batch_launch(std_batch* bt, float lr_a, float lr_b, float lam_a, float lam_b
     std_ctx* c = bt->ctxs[t];
     int rc = ensure_schedule(c, M);
     if (rc) return rc;
-    const size_t sm = batch_smem(c, M, G);
+    const int gown = bt->fixed_g.empty() ? G : bt->fixed_g[t];
+    const size_t sm = batch_smem(c, M, gown);
     if (sm == 0) return set_error(STD_EUNSUPPORTED, "a tensor of the batch does not fit a CTA at this group size");
     smem = sm > smem ? sm : smem;
     const int64_t nb = (c->nnz + M - 1) / M;
@@ -935,13 +937,78 @@ int batch_launch(std_batch* bt, float lr_a, float lr_b, float lam_a, float lam_b
         ++promoted;
       }
   }
+  std::vector<std::vector<int>> lists;
+  std::vector<int> gsize;
+  if (!bt->fixed_g.empty()) {
+    // caller-fixed sizes: one class of groups per distinct size; every class
+    // starts with one group, then the class with the latest estimated finish
+    // (mean load per group, at least its longest tensor; time per size from
+    // the same speed model) gains a group while CTAs remain
+    gt = bt->fixed_g;
+    std::vector<int> sizes(gt.begin(), gt.end());
+    std::sort(sizes.begin(), sizes.end());
+    sizes.erase(std::unique(sizes.begin(), sizes.end()), sizes.end());
+    const int S = (int)sizes.size();
+    auto speed = [](int g) {
+      // relative to 4 CTAs: doubling 0.77, 0.86, 0.95; halving 1.5 per step
+      double f = 1.0;
+      for (int x = 4; x < g; x *= 2) f *= x == 4 ? 0.77 : (x == 8 ? 0.86 : 0.95);
+      for (int x = 4; x > g; x /= 2) f *= 1.5;
+      return f;
+    };
+    std::vector<int> ng(S, 1), cnt(S, 0);
+    std::vector<double> sum(S, 0.0), mx(S, 0.0);
+    int used = 0;
+    for (int k = 0; k < S; ++k) used += sizes[k];
+    if (used > maxc) return set_error(STD_EUNSUPPORTED, "the fixed group sizes do not fit the co-resident CTAs");
+    for (int t = 0; t < T; ++t) {
+      const int k = (int)(std::lower_bound(sizes.begin(), sizes.end(), gt[t]) - sizes.begin());
+      const double e = (double)w[t] * speed(gt[t]);
+      sum[k] += e;
+      mx[k] = e > mx[k] ? e : mx[k];
+      ++cnt[k];
+    }
+#pragma unroll 1
+    while (true) {
+      int best = -1;
+      double best_f = -1.0;
+      for (int k = 0; k < S; ++k) {
+        if (ng[k] >= cnt[k] || used + sizes[k] > maxc) continue;
+        const double f = sum[k] / ng[k] > mx[k] ? sum[k] / ng[k] : mx[k];
+        if (f > best_f && sum[k] / ng[k] > mx[k]) {
+          best_f = f;
+          best = k;
+        }
+      }
+      if (best < 0) break;
+      ++ng[best];
+      used += sizes[best];
+    }
+    std::vector<int> first_group(S, 0);
+    int q0 = 0;
+    for (int k = 0; k < S; ++k) {
+      first_group[k] = q0;
+      for (int i = 0; i < ng[k]; ++i) gsize.push_back(sizes[k]);
+      q0 += ng[k];
+    }
+    lists.assign(q0, {});
+    std::vector<double> load(q0, 0.0);
+    for (int t : byw) {
+      const int k = (int)(std::lower_bound(sizes.begin(), sizes.end(), gt[t]) - sizes.begin());
+      int b = first_group[k];
+      for (int q = first_group[k] + 1; q < first_group[k] + ng[k]; ++q)
+        if (load[q] < load[b]) b = q;
+      load[b] += (double)w[t];
+      lists[b].push_back(t);
+    }
+  }
   int nbase = (maxc - promoted_ctas) / G;
   if (nbase > T - promoted) nbase = T - promoted;
-  const int groups = promoted + nbase;
+  const int groups = bt->fixed_g.empty() ? promoted + nbase : (int)gsize.size();
   if (groups < 1) return set_error(STD_EUNSUPPORTED, "batched kernel cannot be resident at this group size");
-  std::vector<std::vector<int>> lists(groups);
-  std::vector<int> gsize(groups, G);
-  {
+  if (bt->fixed_g.empty()) {
+    lists.assign(groups, {});
+    gsize.assign(groups, G);
     int q = 0;
     for (int t : byw)
       if (gt[t] > G) {
@@ -1179,6 +1246,23 @@ int std_batch_step(std_batch* bt, float lr_a, float lr_b, float lambda_a, float 
     out->graph_replayed = bt->replayed ? 1 : 0;
     out->reserved = 0;
   }
+  return STD_OK;
+}
+
+int std_batch_set_groups(std_batch* bt, const int32_t* ctas_per_tensor) {
+  if (!bt || !ctas_per_tensor) return set_error(STD_EINVAL, "batch or sizes is NULL");
+  std::vector<int> g(bt->ctxs.size());
+  int mn = 0;
+  for (size_t t = 0; t < g.size(); ++t) {
+    if (ctas_per_tensor[t] < 1 || ctas_per_tensor[t] > 32)
+      return set_error(STD_EINVAL, "a group size is outside [1, 32]");
+    g[t] = ctas_per_tensor[t];
+    mn = (mn == 0 || g[t] < mn) ? g[t] : mn;
+  }
+  bt->fixed_g = g;
+  bt->group = mn;
+  bt->tuned = true;
+  bt->promote = false;
   return STD_OK;
 }
 

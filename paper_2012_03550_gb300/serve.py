@@ -66,6 +66,7 @@ class Job:
     finished: float = 0.0
     epoch_times: List[float] = dataclasses.field(default_factory=list)
     device_bytes: int = 0
+    ctas: int = 0                 # CTAs of the job's group in every launch (0: tuned at the first step)
     params: Optional[tuple] = None
     handle: object = None
 
@@ -132,14 +133,20 @@ class CudaEngine:
             self._batches.pop(k).close()
         h.close()
 
-    def step(self, handles: Sequence, key: tuple, batches: int, ctas_per_tensor: int) -> dict:
+    def step(self, handles: Sequence, key: tuple, batches: int, sizes: Sequence[int]) -> dict:
+        """One batched step; sizes[i] = CTAs of handle i's group (all 0: the
+        library's tuner picks one size for every tensor)."""
         b = self._b
-        ident = (tuple(id(h) for h in handles), int(ctas_per_tensor))
+        ident = (tuple(id(h) for h in handles), tuple(int(x) for x in sizes))
         bt = self._batches.get(ident)
         if bt is None:
             for k in [k for k in self._batches if set(k[0]) & set(ident[0])]:
                 self._batches.pop(k).close()
-            bt = b.Batch(handles, ctas_per_tensor)
+            if all(x == 0 for x in sizes):
+                bt = b.Batch(handles, 0)
+            else:
+                bt = b.Batch(handles, min(sizes))
+                bt.set_groups(sizes)
             self._batches[ident] = bt
         lr_a, lr_b, lam_a, lam_b, m = key
         return bt.step(lr_a, lr_b, lam_a, lam_b, m, batches)
@@ -169,8 +176,12 @@ class Server:
     """Admission, ticks and bookkeeping; see the module docstring."""
 
     def __init__(self, engine, budget_bytes: int, batches_per_tick: int = 32, max_jobs: int = 0,
-                 ctas_per_tensor: int = 0, keep_finished: bool = True,
+                 ctas_per_tensor=0, keep_finished: bool = True,
                  clock: Callable[[], float] = time.perf_counter):
+        """ctas_per_tensor: CTAs of every job's group (0: tuned at the first
+        step), or a function of the job giving its own size; either way a
+        job keeps its size for its whole life, so its result does not depend
+        on the jobs it shares launches with."""
         if budget_bytes <= 0:
             raise ValueError("budget_bytes must be positive")
         if batches_per_tick < 1:
@@ -179,7 +190,8 @@ class Server:
         self.budget = int(budget_bytes)
         self.batches_per_tick = int(batches_per_tick)
         self.max_jobs = int(max_jobs)
-        self.group = int(ctas_per_tensor)     # 0: chosen by the library's tuner at the first step
+        self.policy = ctas_per_tensor if callable(ctas_per_tensor) else None
+        self.group = 0 if self.policy else int(ctas_per_tensor)   # 0: chosen by the tuner at the first step
         self.keep_finished = keep_finished
         self.clock = clock
         self.jobs: Dict[int, Job] = {}
@@ -237,12 +249,12 @@ class Server:
         return True
 
     def _admit(self) -> None:
-        reserve_g = self.group if self.group > 0 else 32
         while self.queue and (self.max_jobs <= 0 or len(self.running) < self.max_jobs):
             job = self.queue[0]
+            job.ctas = int(self.policy(job)) if self.policy else self.group
             free = self.budget - self.used_bytes()
             try:
-                h = self.engine.open(job, free, reserve_g)
+                h = self.engine.open(job, free, job.ctas if job.ctas > 0 else 32)
             except BudgetExceeded as e:
                 if self._evict_oldest_done():
                     continue
@@ -305,9 +317,13 @@ class Server:
             groups.setdefault(j.key(), []).append(j)
         t0 = self.clock()
         for key, js in groups.items():
-            st = self.engine.step([j.handle for j in js], key, self.batches_per_tick, self.group)
-            if self.group <= 0:
+            st = self.engine.step([j.handle for j in js], key, self.batches_per_tick, [j.ctas for j in js])
+            if any(j.ctas == 0 for j in js):
+                # the tuner ran: every job keeps the size it chose
                 self.group = int(st["ctas_per_tensor"])
+                for j in self.running:
+                    if j.ctas == 0:
+                        j.ctas = self.group
             self.nnz += int(st["nnz"])
             self.gpu_seconds += float(st["seconds"])
         t1 = self.clock()

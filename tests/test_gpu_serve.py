@@ -51,18 +51,23 @@ def _job(serve, k, t, **kw):
                      options={"seed_init": 11 + k, "seed_sched": 5 + k}, fetch_params=True, **kw)
 
 
-def _alone(B, k, t, precision):
+def _alone(B, k, t, precision, ctas=GROUP):
     shape, nnz, ranks, R, dists, M = JOBS[k]
     c, v = t.split("train")
-    g = B.Tucker(shape, ranks, c, v, r_core=R, ctas=GROUP, precision=precision, seed_init=11 + k,
+    g = B.Tucker(shape, ranks, c, v, r_core=R, ctas=ctas, precision=precision, seed_init=11 + k,
                  seed_sched=5 + k)
     for _ in range(EPOCHS):
         g.epoch(LR, LR, LAM, LAM, M)
     return g
 
 
-@pytest.mark.parametrize("precision", [0, 1])
-def test_each_job_is_the_same_alone_and_in_the_mix(B, tensors, precision):
+def _by_size(job):
+    # a job's group size from its own shape only
+    return 8 if job.nnz >= 10000 else 2
+
+
+@pytest.mark.parametrize("precision,policy", [(0, None), (1, None), (0, _by_size)])
+def test_each_job_is_the_same_alone_and_in_the_mix(B, tensors, precision, policy):
     from paper_2012_03550_gb300 import serve
     eng = serve.CudaEngine(precision=precision, max_query=512)
     # footprints with the reservation the server makes, to size a budget that holds two or three jobs
@@ -72,7 +77,7 @@ def test_each_job_is_the_same_alone_and_in_the_mix(B, tensors, precision):
         sizes.append(eng.device_bytes(h))
         eng.close(h)
     budget = sorted(sizes)[-1] + sorted(sizes)[-2] + min(sizes) // 2
-    srv = serve.Server(eng, budget_bytes=budget, batches_per_tick=7, ctas_per_tensor=GROUP)
+    srv = serve.Server(eng, budget_bytes=budget, batches_per_tick=7, ctas_per_tensor=policy or GROUP)
     rng = np.random.default_rng(0)
     queries = []
     try:
@@ -107,7 +112,8 @@ def test_each_job_is_the_same_alone_and_in_the_mix(B, tensors, precision):
             j = srv.jobs[jid]
             assert j.status in ("done", "evicted"), (jid, j.status, j.error)
             assert len(j.epoch_times) == EPOCHS
-            g = _alone(B, k, tensors[k], precision)
+            assert j.ctas == (policy(j) if policy else GROUP)
+            g = _alone(B, k, tensors[k], precision, j.ctas)
             A, Bm, core, ep = g.get_params()
             A2, B2, core2, ep2 = j.params
             assert ep == ep2 == EPOCHS

@@ -50,10 +50,11 @@ class FakeEngine:
         h.closed = True
         self.open_handles.remove(h)
 
-    def step(self, handles, key, K, G):
+    def step(self, handles, key, K, sizes):
         assert all(not h.closed for h in handles)
-        g = G if G > 0 else self.tuned_group
-        self.steps.append((tuple(h.job.id for h in handles), key, K, G))
+        assert len(sizes) == len(handles)
+        g = sizes[0] if sizes[0] > 0 else self.tuned_group
+        self.steps.append((tuple(h.job.id for h in handles), key, K, tuple(sizes)))
         nnz = 0
         M = key[4]
         for h in handles:
@@ -131,8 +132,22 @@ def test_group_size_fixed_after_first_tuned_step():
     srv.tick()
     srv.submit(job(500))
     srv.run_until_idle()
-    assert eng.steps[0][3] == 0                    # the first step asks the tuner
-    assert all(s[3] == 8 for s in eng.steps[1:])   # later steps reuse its choice
+    assert eng.steps[0][3] == (0,)                 # the first step asks the tuner
+    assert all(set(s[3]) == {8} for s in eng.steps[1:])   # later steps reuse its choice
+
+
+def test_per_job_group_sizes_from_a_policy_stay_fixed():
+    eng = FakeEngine()
+    srv = Server(eng, budget_bytes=10**9, batches_per_tick=2, clock=Clock(),
+                 ctas_per_tensor=lambda job: 8 if job.nnz >= 1000 else 2)
+    a = srv.submit(job(1500))
+    b = srv.submit(job(300))
+    srv.tick()
+    c = srv.submit(job(2000))
+    srv.run_until_idle()
+    assert srv.jobs[a].ctas == 8 and srv.jobs[b].ctas == 2 and srv.jobs[c].ctas == 8
+    for ids, key, K, sizes in eng.steps:
+        assert sizes == tuple(srv.jobs[i].ctas for i in ids)
 
 
 def test_jobs_with_different_hyperparameters_step_in_separate_launches():
