@@ -57,6 +57,8 @@ def _args():
     p.add_argument("--batched", action="store_true",
                    help="batched workload instead of the default line: 256 independent 3-order tensors "
                         "(lognormal sizes, J in {4, 8, 16}) in one persistent launch per epoch")
+    p.add_argument("--order4", action="store_true",
+                   help="the 4-order workload (50M nonzeros at --scale 1), FP32 and BF16 epochs")
     p.add_argument("--msweep", action="store_true",
                    help="throughput against the minibatch size on the rating tensor (--scale, default 0.25)")
     p.add_argument("--serve", action="store_true",
@@ -558,6 +560,66 @@ def run_msweep(a):
     return 0
 
 
+def run_order4(a):
+    """The 4-order workload (200,000 x 100,000 x 500 x 24, 50M nonzeros at
+    scale 1, J = 8, M = 8192): epoch throughput and test RMSE of the FP32 form
+    and of the BF16 form, whose factor-phase contraction (512 x 8 per mode and
+    sample) runs on the tensor cores."""
+    import numpy as np
+    import torch
+
+    import __graft_entry__ as ge
+    ge.build()
+    from paper_2012_03550_gb300 import binding as B
+    from paper_2012_03550_gb300 import synth
+
+    t0 = time.time()
+    w = synth.config3(scale=a.scale)
+    gen_s = time.time() - t0
+    t = w.tensor
+    c, v = t.split("train")
+    tc, tv = t.split("test")
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.Stream(device=dev)
+    dc, dv = torch.from_numpy(c).to(dev), torch.from_numpy(v).to(dev)
+    dtc, dtv = torch.from_numpy(tc).to(dev), torch.from_numpy(tv).to(dev)
+    A0, B0 = synth.init_params(t.shape, w.ranks, w.r_core, mode="normal", seed=1)
+    res = {}
+    for prec in (0, 1):
+        opt = B.std_default_options()
+        opt.r_core = w.r_core
+        opt.ptr_kind = 1
+        opt.precision = prec
+        opt.stream = stream.cuda_stream
+        ctx = B.std_create(t.order, t.shape, w.ranks, c.shape[0], dc, dv, opt)
+        B.std_set_params(ctx, [np.ascontiguousarray(x) for x in A0], [np.ascontiguousarray(x) for x in B0], 0)
+        for _ in range(a.warmup):
+            B.std_sgd_epoch(ctx, w.lr, w.lr, w.lam, w.lam, w.minibatch)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        upd = 0.0
+        e0.record(stream)
+        for _ in range(a.steps):
+            upd += B.std_sgd_epoch(ctx, w.lr, w.lr, w.lam, w.lam, w.minibatch)["update_seconds"]
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / a.steps
+        rm = B.std_rmse(ctx, tc.shape[0], dtc, dtv)
+        B.std_destroy(ctx)
+        nb = (c.shape[0] + w.minibatch - 1) // w.minibatch
+        res[prec] = {"value": c.shape[0] / (ms * 1e-3), "ms_per_epoch": ms,
+                     "us_per_minibatch": 1e6 * upd / a.steps / nb, "test_rmse": rm[0]}
+    line = {"metric": "4-order workload: sampled nonzeros/s per epoch, FP32 and BF16", "workload": w.name,
+            "nnz_train": int(c.shape[0]), "minibatch": w.minibatch, "ranks": list(w.ranks), "r_core": w.r_core,
+            "epochs": a.warmup + a.steps, "value": res[0]["value"], "unit": "nnz/s", "fp32": res[0], "bf16": res[1],
+            "bf16_speedup": res[1]["value"] / res[0]["value"],
+            "bf16_test_rmse_gap": abs(res[1]["test_rmse"] - res[0]["test_rmse"]), "datagen_s": round(gen_s, 1),
+            "data": "synthetic"}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_batched(a):
     """Epochs of 256 independent decompositions in one launch per epoch, FP32 and
     BF16, against the same tensors run one after another on the whole GPU."""
@@ -766,6 +828,8 @@ def main():
         return run_sweep(a)
     if a.msweep:
         return run_msweep(a)
+    if a.order4:
+        return run_order4(a)
     if a.batched:
         return run_batched(a)
     if a.serve:

@@ -180,6 +180,16 @@ int std_schedule(std_ctx* ctx, int32_t minibatch, int64_t batch_begin, int64_t b
 /* x-hat at k coordinates (Def. 6 with the Kruskal core of Eq. 4); out[k]. */
 int std_predict(std_ctx* ctx, int64_t k, const int32_t* coords, float* out);
 
+/* std_predict for several contexts in ONE launch (Def. 6 with the core of
+ * Eq. 4): k[i] coordinates coords[i] (k[i] x N_i int32, row-major) of
+ * ctxs[i] into out[i].  Every context must have the same ptr_kind; host
+ * buffers are staged through one stream-ordered allocation on ctxs[0]'s
+ * stream.  Each result equals that context's own std_predict bit for bit.
+ * Errors: STD_EINVAL (bad arguments, mixed ptr_kind, a coordinate outside
+ * [0, I_n): its result is NaN), STD_ECUDA. */
+int std_predict_many(int32_t count, std_ctx* const* ctxs, const int64_t* k, const int32_t* const* coords,
+                     float* const* out);
+
 /*
  * RMSE and MAE (Eq. 19) of the model over k entries (coords k x N, values k),
  * accumulated in FP64 in a fixed order (bit-reproducible).  mae may be NULL.

@@ -123,6 +123,7 @@ SIGNATURES = {
     "std_watchdog_probe": (ctypes.c_int, [ctypes.c_uint64, _P]),
     "std_batch_groups": (ctypes.c_int, [_P, _P]),
     "std_batch_set_groups": (ctypes.c_int, [_P, _P]),
+    "std_predict_many": (ctypes.c_int, [ctypes.c_int32, _P, _P, _P, _P]),
 }
 
 
@@ -391,6 +392,24 @@ def std_batch_groups(batch, count):
     out = (ctypes.c_int32 * int(count))()
     _check(lib().std_batch_groups(batch, ctypes.cast(out, ctypes.c_void_p)))
     return [int(x) for x in out]
+
+
+def std_predict_many(ctxs, coords_list, outs):
+    n = len(ctxs)
+    carr = (ctypes.c_void_p * n)(*[c.value if isinstance(c, ctypes.c_void_p) else c for c in ctxs])
+    karr = (ctypes.c_int64 * n)(*[int(x.shape[0]) for x in coords_list])
+    parr = (ctypes.c_void_p * n)(*[_addr(x) for x in coords_list])
+    oarr = (ctypes.c_void_p * n)(*[_addr(x) for x in outs])
+    _check(lib().std_predict_many(n, ctypes.cast(carr, ctypes.c_void_p), ctypes.cast(karr, ctypes.c_void_p),
+                                  ctypes.cast(parr, ctypes.c_void_p), ctypes.cast(oarr, ctypes.c_void_p)))
+
+
+def predict_many(tuckers, coords_list):
+    """Host numpy coordinates for several Tucker objects; one launch."""
+    coords_list = [np.ascontiguousarray(c, dtype=np.int32) for c in coords_list]
+    outs = [np.zeros(c.shape[0], np.float32) for c in coords_list]
+    std_predict_many([t.ctx for t in tuckers], coords_list, outs)
+    return outs
 
 
 def std_batch_set_groups(batch, sizes):

@@ -673,6 +673,76 @@ int std_predict(std_ctx* c, int64_t k, const int32_t* coords, float* out) {
   return read_err(c, "std_predict");
 }
 
+int std_predict_many(int32_t count, std_ctx* const* ctxs, const int64_t* k, const int32_t* const* coords,
+                     float* const* out) {
+  if (count < 1 || !ctxs || !k || !coords || !out) return set_error(STD_EINVAL, "bad arguments");
+  const int kind = ctxs[0] ? ctxs[0]->opt.ptr_kind : 0;
+  int64_t total = 0;
+  size_t cwords = 0;
+  for (int i = 0; i < count; ++i) {
+    if (!ctxs[i]) return set_error(STD_EINVAL, "NULL context");
+    if (ctxs[i]->opt.ptr_kind != kind) return set_error(STD_EINVAL, "contexts differ in ptr_kind");
+    if (k[i] < 0) return set_error(STD_EINVAL, "k must be >= 0");
+    if (k[i] > 0 && (!coords[i] || !out[i])) return set_error(STD_EINVAL, "NULL array argument");
+    total += k[i];
+    cwords += (size_t)k[i] * ctxs[i]->g.N;
+  }
+  if (total == 0) return STD_OK;
+  cudaStream_t st = ctxs[0]->stream;
+  // one stream-ordered allocation: items, error word, (host pointers) staged
+  // coordinates and results
+  const size_t items_b = (size_t)count * sizeof(PredictItem);
+  const size_t err_off = (items_b + 15) & ~(size_t)15;
+  const size_t crd_off = err_off + 16;
+  const size_t out_off = (crd_off + (kind == 0 ? cwords * 4 : 0) + 15) & ~(size_t)15;
+  const size_t bytes = out_off + (kind == 0 ? (size_t)total * 4 : 0);
+  char* dev = nullptr;
+  STD_CUDA(cudaMallocAsync((void**)&dev, bytes, st), "multi-predict staging");
+  std::vector<PredictItem> h(count);
+  int64_t off = 0;
+  size_t cw = 0;
+  cudaError_t e = cudaSuccess;
+  for (int i = 0; i < count && e == cudaSuccess; ++i) {
+    std_ctx* c = ctxs[i];
+    PredictItem& it = h[i];
+    it.g = c->g;
+    for (int n = 0; n < c->g.N; ++n) it.A.A[n] = c->A[n];
+    it.B = c->B;
+    it.k = k[i];
+    it.off = off;
+    if (kind == 0) {
+      int32_t* dc = reinterpret_cast<int32_t*>(dev + crd_off) + cw;
+      it.coords = dc;
+      it.out = reinterpret_cast<float*>(dev + out_off) + off;
+      if (k[i] > 0)
+        e = cudaMemcpyAsync(dc, coords[i], (size_t)k[i] * c->g.N * 4, cudaMemcpyHostToDevice, st);
+    } else {
+      it.coords = coords[i];
+      it.out = out[i];
+    }
+    off += k[i];
+    cw += (size_t)k[i] * c->g.N;
+  }
+  if (e == cudaSuccess) e = cudaMemcpyAsync(dev, h.data(), items_b, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(dev + err_off, 0, sizeof(int), st);
+  if (e == cudaSuccess)
+    e = launch_predict_multi(reinterpret_cast<const PredictItem*>(dev), count, total,
+                             reinterpret_cast<int*>(dev + err_off), st);
+  if (e == cudaSuccess && kind == 0)
+    for (int i = 0; i < count && e == cudaSuccess; ++i)
+      if (k[i] > 0)
+        e = cudaMemcpyAsync(out[i], reinterpret_cast<float*>(dev + out_off) + h[i].off, (size_t)k[i] * 4,
+                            cudaMemcpyDeviceToHost, st);
+  int herr = 0;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&herr, dev + err_off, sizeof(int), cudaMemcpyDeviceToHost, st);
+  const cudaError_t ef = cudaFreeAsync(dev, st);
+  if (e == cudaSuccess) e = ef;
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_error(e, "multi-predict");
+  if (herr != 0) return set_error(STD_EINVAL, "std_predict_many: coordinate outside [0, I_n)");
+  return STD_OK;
+}
+
 int std_rmse(std_ctx* c, int64_t k, const int32_t* coords, const float* values, double* rmse, double* mae) {
   if (!c) return set_error(STD_EINVAL, "context is NULL");
   if (k < 0 || !rmse) return set_error(STD_EINVAL, "bad arguments");

@@ -166,6 +166,19 @@ struct AParams {
   float* A[kMaxN];
 };
 
+// One context's share of a multi-context prediction launch: queries
+// [off, off + k) of the launch are its k coordinates (coords, k x N) and
+// results (out).
+struct PredictItem {
+  Geometry g;
+  AParams A;
+  const float* B;
+  const int32_t* coords;
+  float* out;
+  int64_t k;
+  int64_t off;
+};
+
 // Launchers (host side, defined in the .cu files).
 cudaError_t launch_schedule(const Geometry& g, const uint32_t* coo, int cs, const Feistel& f,
                             const Schedule& s, int64_t b0, int64_t b1, cudaStream_t st);
@@ -194,6 +207,7 @@ cudaError_t launch_predict(const Geometry& g, const AParams& A, const float* B, 
                            const float* values, int64_t k, float* out, double* partials, int blocks,
                            int* err, cudaStream_t st);
 cudaError_t launch_rmse_finish(const double* partials, int blocks, double* result, cudaStream_t st);
+cudaError_t launch_predict_multi(const PredictItem* items, int count, int64_t total, int* err, cudaStream_t st);
 
 // Sets the thread-local message returned by std_last_error(); returns code.
 int record_error(int code, const std::string& msg);

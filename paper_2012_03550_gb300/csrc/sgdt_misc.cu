@@ -234,6 +234,55 @@ cudaError_t launch_predict(const Geometry& g, const AParams& A, const float* B, 
   return cudaGetLastError();
 }
 
+// Predictions for several contexts in one launch: thread per query of the
+// concatenated list, which finds its context by binary search over the
+// items' offsets; the arithmetic is k_predict's, term for term, so each
+// result equals that context's own std_predict.
+__global__ void __launch_bounds__(kPredictThreads)
+k_predict_multi(const PredictItem* __restrict__ items, int count, int64_t total, int* err) {
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < total; q += (int64_t)gridDim.x * blockDim.x) {
+    int lo = 0, hi = count - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (items[mid].off <= q) lo = mid;
+      else hi = mid - 1;
+    }
+    const PredictItem& it = items[lo];
+    const Geometry& g = it.g;
+    const int64_t i = q - it.off;
+    const float* rows[kMaxN];
+    bool ok = true;
+    for (int n = 0; n < g.N; ++n) {
+      const int32_t v = it.coords[(size_t)i * g.N + n];
+      if (v < 0 || (int64_t)v >= g.I[n]) { ok = false; rows[n] = nullptr; }
+      else rows[n] = it.A.A[n] + (size_t)v * g.Jp[n];
+    }
+    if (!ok) {
+      atomicExch(err, STD_EINVAL);
+      it.out[i] = __int_as_float(0x7fc00000);
+      continue;
+    }
+    float xhat = 0.f;
+    for (int r = 0; r < g.R; ++r) {
+      float prod = 1.f;
+      for (int n = 0; n < g.N; ++n) {
+        const float* br = it.B + g.boff[n] + r;
+        float dot = 0.f;
+        for (int j = 0; j < g.J[n]; ++j) dot = fmaf(rows[n][j], br[j * g.R], dot);
+        prod *= dot;
+      }
+      xhat += prod;
+    }
+    it.out[i] = xhat;
+  }
+}
+
+cudaError_t launch_predict_multi(const PredictItem* items, int count, int64_t total, int* err, cudaStream_t st) {
+  if (total <= 0) return cudaSuccess;
+  k_predict_multi<<<predict_blocks(total), kPredictThreads, 0, st>>>(items, count, total, err);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_rmse_finish(const double* partials, int blocks, double* result, cudaStream_t st) {
   k_rmse_finish<<<1, 256, 0, st>>>(partials, blocks, result);
   return cudaGetLastError();

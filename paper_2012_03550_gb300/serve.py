@@ -13,8 +13,9 @@ works in ticks.  Each tick
    follow allocate nothing.  A job that does not fit waits at the head of the
    queue; finished models that are still resident are evicted oldest first to
    make room; a job larger than the whole budget is rejected;
-2. answers every pending query, one std_predict launch per job over the
-   concatenated coordinates of all of that job's queries;
+2. answers every pending query in one launch over all jobs
+   (std_predict_many, each job's queries concatenated), or one std_predict
+   per job when the engine has no multi-job form;
 3. advances every admitted job by up to `batches_per_tick` minibatches of its
    current epoch with one std_batch_step per group of jobs that share
    hyperparameters: all jobs of a group run in the same persistent launch,
@@ -157,6 +158,10 @@ class CudaEngine:
     def predict(self, h, coords: np.ndarray) -> np.ndarray:
         return h.predict(coords)
 
+    def predict_many(self, handles: Sequence, coords_list: Sequence[np.ndarray]) -> List[np.ndarray]:
+        """Every job's queries in one launch (std_predict_many)."""
+        return self._b.predict_many(handles, coords_list)
+
     def params(self, h):
         return h.get_params()
 
@@ -292,13 +297,24 @@ class Server:
                 waiting.append(q)           # queued: answered once the job is admitted
             else:
                 per_job[q.job_id].append(q)
-        for jid, qs in per_job.items():
-            j = self.jobs[jid]
-            coords = np.concatenate([q.coords for q in qs], axis=0) if len(qs) > 1 else qs[0].coords
-            limit = getattr(self.engine, "max_query", 0) or coords.shape[0]
-            vals = np.empty(coords.shape[0], np.float32)
-            for a in range(0, coords.shape[0], limit):
-                vals[a:a + limit] = self.engine.predict(j.handle, coords[a:a + limit])
+        jids = list(per_job)
+        coords_of = {jid: (np.concatenate([q.coords for q in per_job[jid]], axis=0) if len(per_job[jid]) > 1
+                           else per_job[jid][0].coords) for jid in jids}
+        vals_of = {}
+        if jids and hasattr(self.engine, "predict_many"):
+            outs = self.engine.predict_many([self.jobs[jid].handle for jid in jids], [coords_of[jid] for jid in jids])
+            vals_of = dict(zip(jids, outs))
+        else:
+            for jid in jids:
+                coords = coords_of[jid]
+                limit = getattr(self.engine, "max_query", 0) or coords.shape[0]
+                vals = np.empty(coords.shape[0], np.float32)
+                for a in range(0, coords.shape[0], limit):
+                    vals[a:a + limit] = self.engine.predict(self.jobs[jid].handle, coords[a:a + limit])
+                vals_of[jid] = vals
+        for jid in jids:
+            qs = per_job[jid]
+            vals = vals_of[jid]
             t = self.clock()
             off = 0
             for q in qs:

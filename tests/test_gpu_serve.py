@@ -182,3 +182,28 @@ def test_epoch_in_progress_is_protected(B, tensors):
         assert g.progress() == (2, 0)
     finally:
         g.close()
+
+
+def test_predict_many_equals_each_context_alone(B, tensors):
+    """One launch over jobs of orders 3 and 4 gives each job's std_predict bit for bit."""
+    rng = np.random.default_rng(3)
+    gs, crds = [], []
+    try:
+        for k in (0, 1, 3):
+            shape, nnz, ranks, R, dists, M = JOBS[k]
+            c, v = tensors[k].split("train")
+            g = B.Tucker(shape, ranks, c, v, r_core=R, seed_init=40 + k)
+            g.epoch(LR, LR, LAM, LAM, M)
+            gs.append(g)
+            n = (1, 700, 4096)[k % 3]
+            crds.append(np.stack([rng.integers(0, s, size=n) for s in shape], axis=1).astype(np.int32))
+        outs = B.predict_many(gs, crds)
+        for g, cc, o in zip(gs, crds, outs):
+            assert np.array_equal(o, g.predict(cc))
+        bad = crds[1].copy()
+        bad[5, 0] = gs[1].shape[0]
+        with pytest.raises(B.StdError):
+            B.predict_many(gs, [crds[0], bad, crds[2]])
+    finally:
+        for g in gs:
+            g.close()

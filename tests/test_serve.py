@@ -241,3 +241,28 @@ def test_bad_server_arguments():
         Server(FakeEngine(), budget_bytes=0)
     with pytest.raises(ValueError):
         Server(FakeEngine(), budget_bytes=10, batches_per_tick=0)
+
+
+class FakeManyEngine(FakeEngine):
+    def __init__(self):
+        super().__init__()
+        self.many = []
+
+    def predict_many(self, handles, coords_list):
+        self.many.append(tuple((h.job.id, c.shape[0]) for h, c in zip(handles, coords_list)))
+        return [c.sum(axis=1).astype(np.float32) + 1000.0 * h.job.id for h, c in zip(handles, coords_list)]
+
+
+def test_queries_of_all_jobs_go_in_one_launch_when_the_engine_allows():
+    eng = FakeManyEngine()
+    srv = Server(eng, budget_bytes=10**9, batches_per_tick=1, clock=Clock())
+    a = srv.submit(job(1000, epochs=5))
+    b = srv.submit(job(1000, epochs=5))
+    srv.tick()
+    rng = np.random.default_rng(1)
+    qs = [(jid, srv.query(jid, rng.integers(0, 10, size=(k, 3)).astype(np.int32)))
+          for k in (5, 2000, 3) for jid in (a, b)]
+    srv.tick()
+    assert eng.many == [((a, 2008), (b, 2008))] and not eng.predicts
+    for jid, q in qs:
+        assert np.array_equal(q.values, q.coords.sum(axis=1).astype(np.float32) + 1000.0 * jid)
