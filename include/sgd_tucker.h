@@ -233,7 +233,8 @@ const char* std_last_error(void);
  *                     and, at every launch, a group of 2^k times the base
  *                     size (up to 32 CTAs, chunks of at least 8 samples) for
  *                     each tensor whose work alone exceeds the average load
- *                     of a base group (std_batch_groups reports the sizes)
+ *                     of a base group (std_batch_groups reports the sizes);
+ *                     -1 = the tuned size for every tensor, no larger groups
  * Errors: STD_EINVAL, STD_ECUDA.
  */
 typedef struct std_batch std_batch;
@@ -261,10 +262,17 @@ typedef struct {
 int std_batch_step(std_batch* batch, float lr_a, float lr_b, float lambda_a, float lambda_b,
                    int32_t minibatch, int64_t max_batches, std_batch_stats* out);
 
+/* Replace the batch's tensors (same rules as std_batch_create; same precision
+ * and stream as the batch), keeping its buffers, its tuned group size and
+ * its captured launch for reuse; per-tensor sizes from std_batch_set_groups
+ * are dropped (set them again for the new members).  For a serving loop whose
+ * set of jobs changes between steps.  Errors: STD_EINVAL. */
+int std_batch_reset(std_batch* batch, int32_t count, std_ctx* const* ctxs);
+
 /* Fix each tensor's group size (count entries in [1, 32], in the order of
  * std_batch_create): no tuner and no promotion; tensors of one size share
- * groups of that size, and each size class gets groups while its estimated
- * finish is the latest and CTAs remain.  A tensor's result then depends only
+ * groups of that size, and the size class with the highest mean load per
+ * group gains a group while CTAs remain, up to one group per tensor.  A tensor's result then depends only
  * on its own size, not on the other tensors (the serving loop sizes each job
  * from its own shape).  Errors: STD_EINVAL. */
 int std_batch_set_groups(std_batch* batch, const int32_t* ctas_per_tensor);

@@ -124,6 +124,7 @@ SIGNATURES = {
     "std_batch_groups": (ctypes.c_int, [_P, _P]),
     "std_batch_set_groups": (ctypes.c_int, [_P, _P]),
     "std_predict_many": (ctypes.c_int, [ctypes.c_int32, _P, _P, _P, _P]),
+    "std_batch_reset": (ctypes.c_int, [_P, ctypes.c_int32, _P]),
 }
 
 
@@ -412,6 +413,11 @@ def predict_many(tuckers, coords_list):
     return outs
 
 
+def std_batch_reset(batch, ctxs):
+    arr = (ctypes.c_void_p * len(ctxs))(*[c.value if isinstance(c, ctypes.c_void_p) else c for c in ctxs])
+    _check(lib().std_batch_reset(batch, len(ctxs), ctypes.cast(arr, ctypes.c_void_p)))
+
+
 def std_batch_set_groups(batch, sizes):
     arr = (ctypes.c_int32 * len(sizes))(*[int(x) for x in sizes])
     _check(lib().std_batch_set_groups(batch, ctypes.cast(arr, ctypes.c_void_p)))
@@ -445,6 +451,10 @@ class Batch:
 
     def set_groups(self, sizes):
         std_batch_set_groups(self.ptr, sizes)
+
+    def reset(self, tuckers):
+        std_batch_reset(self.ptr, [t.ctx for t in tuckers])
+        self.members = list(tuckers)
 
     def close(self):
         if self.ptr is not None:

@@ -1011,9 +1011,9 @@ int batch_launch(std_batch* bt, float lr_a, float lr_b, float lam_a, float lam_b
   std::vector<int> gsize;
   if (!bt->fixed_g.empty()) {
     // caller-fixed sizes: one class of groups per distinct size; every class
-    // starts with one group, then the class with the latest estimated finish
-    // (mean load per group, at least its longest tensor; time per size from
-    // the same speed model) gains a group while CTAs remain
+    // starts with one group, then the class with the highest mean load per
+    // group (time per size from the same speed model) gains a group while
+    // CTAs remain, up to one group per tensor
     gt = bt->fixed_g;
     std::vector<int> sizes(gt.begin(), gt.end());
     std::sort(sizes.begin(), sizes.end());
@@ -1044,8 +1044,8 @@ int batch_launch(std_batch* bt, float lr_a, float lr_b, float lam_a, float lam_b
       double best_f = -1.0;
       for (int k = 0; k < S; ++k) {
         if (ng[k] >= cnt[k] || used + sizes[k] > maxc) continue;
-        const double f = sum[k] / ng[k] > mx[k] ? sum[k] / ng[k] : mx[k];
-        if (f > best_f && sum[k] / ng[k] > mx[k]) {
+        const double f = sum[k] / ng[k];
+        if (f > best_f) {
           best_f = f;
           best = k;
         }
@@ -1190,7 +1190,7 @@ int std_batch_create(std_batch** out, int32_t count, std_ctx* const* ctxs, int32
   if (!out) return set_error(STD_EINVAL, "out is NULL");
   *out = nullptr;
   if (count < 1 || !ctxs) return set_error(STD_EINVAL, "a batch needs at least one context");
-  if (ctas_per_tensor < 0) return set_error(STD_EINVAL, "ctas_per_tensor must be >= 0");
+  if (ctas_per_tensor < -1) return set_error(STD_EINVAL, "ctas_per_tensor must be >= -1");
   for (int t = 0; t < count; ++t) {
     if (!ctxs[t]) return set_error(STD_EINVAL, "NULL context in the batch");
     if (ctxs[t]->opt.precision != ctxs[0]->opt.precision)
@@ -1204,7 +1204,7 @@ int std_batch_create(std_batch** out, int32_t count, std_ctx* const* ctxs, int32
   bt->ctxs.assign(ctxs, ctxs + count);
   bt->stream = ctxs[0]->stream;
   bt->precision = ctxs[0]->opt.precision;
-  bt->group = ctas_per_tensor;
+  bt->group = ctas_per_tensor > 0 ? ctas_per_tensor : 0;
   bt->tuned = ctas_per_tensor > 0;
   bt->promote = ctas_per_tensor == 0;
   cudaError_t e = cudaMalloc((void**)&bt->err, sizeof(int));
@@ -1316,6 +1316,26 @@ int std_batch_step(std_batch* bt, float lr_a, float lr_b, float lambda_a, float 
     out->graph_replayed = bt->replayed ? 1 : 0;
     out->reserved = 0;
   }
+  return STD_OK;
+}
+
+int std_batch_reset(std_batch* bt, int32_t count, std_ctx* const* ctxs) {
+  if (!bt) return set_error(STD_EINVAL, "batch is NULL");
+  if (count < 1 || !ctxs) return set_error(STD_EINVAL, "a batch needs at least one context");
+  for (int t = 0; t < count; ++t) {
+    if (!ctxs[t]) return set_error(STD_EINVAL, "NULL context in the batch");
+    if (ctxs[t]->opt.precision != bt->precision)
+      return set_error(STD_EINVAL, "every context of a batch must use the batch's precision");
+    if (ctxs[t]->stream != bt->stream) return set_error(STD_EINVAL, "every context of a batch must use its stream");
+    for (int u = 0; u < t; ++u)
+      if (ctxs[u] == ctxs[t]) return set_error(STD_EINVAL, "a context appears twice in the batch");
+  }
+  bt->ctxs.assign(ctxs, ctxs + count);
+  if (!bt->fixed_g.empty()) {
+    // per-tensor sizes belonged to the old members: back to the uniform base size
+    bt->fixed_g.clear();
+  }
+  bt->last_g.clear();
   return STD_OK;
 }
 

@@ -105,7 +105,7 @@ class CudaEngine:
         self._b = binding
         self.precision = int(precision)
         self.max_query = int(max_query)
-        self._batches: Dict[tuple, object] = {}
+        self._batches: Dict[tuple, object] = {}   # hyperparameter key -> (members, sizes, Batch)
 
     def open(self, job: Job, budget_bytes: int, ctas_per_tensor: int):
         b = self._b
@@ -130,25 +130,37 @@ class CudaEngine:
         return h.device_bytes()
 
     def close(self, h) -> None:
-        for k in [k for k in self._batches if id(h) in k[0]]:
-            self._batches.pop(k).close()
+        # a batch that still lists this job forgets it before the context goes
+        for key in [k for k, v in self._batches.items() if any(m is h for m in v[0])]:
+            members, sizes, bt = self._batches[key]
+            rest = [(m, z) for m, z in zip(members, sizes) if m is not h]
+            if rest:
+                bt.reset([m for m, _ in rest])
+                self._batches[key] = ([m for m, _ in rest], None, bt)
+            else:
+                self._batches.pop(key)[2].close()
         h.close()
 
     def step(self, handles: Sequence, key: tuple, batches: int, sizes: Sequence[int]) -> dict:
         """One batched step; sizes[i] = CTAs of handle i's group (all 0: the
-        library's tuner picks one size for every tensor)."""
+        library's tuner picks one size for every tensor).  One batch object
+        per hyperparameter key is kept and re-pointed at the current jobs."""
         b = self._b
-        ident = (tuple(id(h) for h in handles), tuple(int(x) for x in sizes))
-        bt = self._batches.get(ident)
-        if bt is None:
-            for k in [k for k in self._batches if set(k[0]) & set(ident[0])]:
-                self._batches.pop(k).close()
-            if all(x == 0 for x in sizes):
-                bt = b.Batch(handles, 0)
-            else:
-                bt = b.Batch(handles, min(sizes))
-                bt.set_groups(sizes)
-            self._batches[ident] = bt
+        sizes = [int(x) for x in sizes]
+        tune = all(x == 0 for x in sizes)
+        entry = self._batches.get(key)
+        if entry is None:
+            bt = b.Batch(handles, -1 if tune else min(sizes))   # -1: tuned, one size for all
+            changed = True
+        else:
+            members, old_sizes, bt = entry
+            same = len(members) == len(handles) and all(m is h for m, h in zip(members, handles))
+            if not same:
+                bt.reset(list(handles))
+            changed = not same or old_sizes != sizes
+        if changed and not tune:
+            bt.set_groups(sizes)      # every job at its own size, whatever the others are
+        self._batches[key] = (list(handles), sizes, bt)
         lr_a, lr_b, lam_a, lam_b, m = key
         return bt.step(lr_a, lr_b, lam_a, lam_b, m, batches)
 
@@ -166,7 +178,7 @@ class CudaEngine:
         return h.get_params()
 
     def shutdown(self) -> None:
-        for bt in self._batches.values():
+        for _, _, bt in self._batches.values():
             bt.close()
         self._batches.clear()
 
