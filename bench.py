@@ -70,7 +70,7 @@ def _args():
     p.add_argument("--serve-pool", type=int, default=48, help="distinct job tensors generated up front")
     p.add_argument("--serve-budget-gb", type=float, default=120.0)
     p.add_argument("--serve-batches", type=int, default=32, help="minibatches per job per tick")
-    p.add_argument("--serve-ctas", type=int, default=4,
+    p.add_argument("--serve-ctas", type=int, default=-1,
                    help="CTAs per job; 0 = tuned at the first tick; -1 = from each job's own size "
                         "(4 below 400k nonzeros, 8 below 1.2M, else 16)")
     p.add_argument("--serve-seed", type=int, default=0)
