@@ -132,11 +132,11 @@ class CudaEngine:
     def close(self, h) -> None:
         # a batch that still lists this job forgets it before the context goes
         for key in [k for k, v in self._batches.items() if any(m is h for m in v[0])]:
-            members, sizes, bt = self._batches[key]
-            rest = [(m, z) for m, z in zip(members, sizes) if m is not h]
+            members, _, bt = self._batches[key]
+            rest = [m for m in members if m is not h]
             if rest:
-                bt.reset([m for m, _ in rest])
-                self._batches[key] = ([m for m, _ in rest], None, bt)
+                bt.reset(rest)
+                self._batches[key] = (rest, None, bt)   # sizes are set again at the next step
             else:
                 self._batches.pop(key)[2].close()
         h.close()

@@ -266,3 +266,63 @@ def test_queries_of_all_jobs_go_in_one_launch_when_the_engine_allows():
     assert eng.many == [((a, 2008), (b, 2008))] and not eng.predicts
     for jid, q in qs:
         assert np.array_equal(q.values, q.coords.sum(axis=1).astype(np.float32) + 1000.0 * jid)
+
+
+class _FakeBatch:
+    log = []
+
+    def __init__(self, members, ctas):
+        self.members = list(members)
+        self.closed = False
+        _FakeBatch.log.append(("create", len(members), ctas))
+
+    def reset(self, members):
+        assert not self.closed
+        self.members = list(members)
+        _FakeBatch.log.append(("reset", len(members)))
+
+    def set_groups(self, sizes):
+        assert len(sizes) == len(self.members)
+        _FakeBatch.log.append(("groups", tuple(sizes)))
+
+    def step(self, *args):
+        assert not self.closed
+        return {"seconds": 0.0, "nnz": 0, "ctas_per_tensor": 4}
+
+    def close(self):
+        self.closed = True
+        _FakeBatch.log.append(("close",))
+
+
+class _FakeBinding:
+    Batch = _FakeBatch
+
+
+class _H:
+    def __init__(self):
+        self.closed = False
+
+    def close(self):
+        self.closed = True
+
+
+def test_engine_keeps_one_batch_per_key_and_forgets_closed_jobs():
+    from paper_2012_03550_gb300.serve import CudaEngine
+    eng = CudaEngine.__new__(CudaEngine)
+    eng._b = _FakeBinding
+    eng._batches = {}
+    _FakeBatch.log = []
+    key = (0.1, 0.1, 0.0, 0.0, 256)
+    a, b, c = _H(), _H(), _H()
+    eng.step([a, b], key, 4, [4, 8])
+    eng.step([a, b], key, 4, [4, 8])            # same jobs and sizes: nothing re-pointed
+    eng.step([a, b, c], key, 4, [4, 8, 4])      # a job joins: reset + sizes
+    eng.close(b)                                # a member goes: the batch forgets it first
+    eng.close(a)
+    eng.step([c], key, 4, [4])
+    eng.close(c)                                # the last member: the batch is closed
+    assert _FakeBatch.log == [("create", 2, 4), ("groups", (4, 8)),
+                              ("reset", 3), ("groups", (4, 8, 4)),
+                              ("reset", 2), ("reset", 1),
+                              ("groups", (4,)), ("close",)]
+    assert a.closed and b.closed and c.closed and not eng._batches
