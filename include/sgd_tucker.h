@@ -246,7 +246,7 @@ typedef struct {
     double  nnz_per_s;        /* total training nonzeros / seconds */
     int64_t nnz;              /* total training nonzeros visited */
     int32_t tensors;
-    int32_t ctas_per_tensor;  /* the group size used */
+    int32_t ctas_per_tensor;  /* the base group size (std_batch_groups gives each tensor's) */
     int32_t graph_replayed;   /* 1: the launch replayed the captured graph; 0: it was (re)captured */
     int32_t reserved;
 } std_batch_stats;
