@@ -125,4 +125,12 @@ def test_null_context_is_rejected(lib):
         lib.std_device_bytes(None)
     with pytest.raises(lib.StdError):
         lib.std_batch_step(None, 0.1, 0.1, 0.0, 0.0, 16, 1)
+    with pytest.raises(lib.StdError):
+        lib.std_batch_reset(None, [])
+    with pytest.raises(lib.StdError):
+        lib.std_batch_set_groups(None, [4])
+    with pytest.raises(lib.StdError):
+        lib.std_batch_groups(None, 1)
+    with pytest.raises(lib.StdError):
+        lib.std_predict_many([None], [np.zeros((1, 3), np.int32)], [np.zeros(1, np.float32)])
     lib.std_destroy(None)
