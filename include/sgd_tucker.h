@@ -93,7 +93,10 @@ typedef struct {
 void std_default_options(std_options* opt);
 
 /*
- * Create a context holding the training tensor and the model.
+ * Create a context holding the training tensor and the model: the problem of
+ * Sec. 3.2 (the sparse tensor X over the observed set Omega, Table 1 notation;
+ * the low-rank model of Def. 6 with the core of Eq. 4, Sec. 4.1), with X held
+ * as one COO copy on the device (Sec. 4.4.2).
  *   order        N (2..STD_MAX_ORDER)
  *   mode_sizes   I_n, n < N (each >= 1, < 2^31)
  *   ranks        J_n, n < N (1..STD_MAX_RANK)
@@ -109,7 +112,9 @@ void std_default_options(std_options* opt);
 int std_create(std_ctx** out, int32_t order, const int64_t* mode_sizes, const int32_t* ranks,
                int64_t nnz, const int32_t* indices, const float* values, const std_options* opt);
 
-/* Release every resource of the context (NULL is a no-op). */
+/* Release every resource of the context created by std_create (the COO copy
+ * of Sec. 4.4.2 and the model of Def. 6 / Eq. 4) after the context's
+ * stream drains; NULL is a no-op.  Returns STD_OK. */
 int std_destroy(std_ctx* ctx);
 
 /* Per-epoch statistics (nullable output of std_sgd_epoch). */
@@ -205,8 +210,11 @@ int std_rmse(std_ctx* ctx, int64_t k, const int32_t* coords, const float* values
  */
 int std_get_params(std_ctx* ctx, float* const* A, float* const* B, float* core, int64_t* epoch);
 
-/* Overwrite the model (A[n], B[n] as in std_get_params; NULL entries are left
- * unchanged) and the epoch counter (ignored when < 0). */
+/* Overwrite the model parameters of Def. 6 and Eq. 4 (A[n] in R^{I_n x J_n},
+ * B[n] in R^{J_n x R_core}, as in std_get_params; NULL entries are left
+ * unchanged), rebuild G-hat from B (Eq. 4), and set the epoch counter
+ * (ignored when < 0).  Heavy-ball velocities are reset to zero.  Errors:
+ * STD_EINVAL (NULL context), STD_ECUDA. */
 int std_set_params(std_ctx* ctx, const float* const* A, const float* const* B, int64_t epoch);
 
 /* Thread-local description of the last error ("" if none). */
@@ -330,15 +338,20 @@ int std_batch_destroy(std_batch* batch);
  *   out      device, 2 doubles: {rmse, mae}; {0, 0} when k = 0
  *   stream   cudaStream_t (NULL = legacy stream)
  * The call only enqueues two kernels on `stream` and returns; read `out`
- * after synchronising the stream.  A coordinate outside [0, I_n) makes the
- * result NaN.  Sizes beyond the limits return STD_EUNSUPPORTED.
+ * after synchronising the stream.  A coordinate outside [0, I_n) is never
+ * read through: it makes both results NaN.  Sizes beyond the limits return
+ * STD_EUNSUPPORTED.  The library cannot check the device pointers: A[n],
+ * B[n], coords, values and out must be device memory of the stated sizes on
+ * the current device (the Python binding checks this before the call).
  * Scratch: a fixed __device__ array of STD_STATIC_RMSE_BLOCKS x 2 doubles
  * (16 KiB) inside the library, held by every GPU that loads the library until
  * the process exits.  It is not zeroed: each call writes every slot it reads.
  * Every call shares it, so calls that overlap on the GPU (concurrent streams,
  * other threads) race and must be serialised by the caller.  The first call
  * on each device looks up the array's device address with that device
- * current; make that first call before any stream capture.
+ * current; make that first call before any stream capture.  The address is
+ * kept for the life of the process, so the call must not be used on a device
+ * after cudaDeviceReset in the same process.
  */
 #define STD_STATIC_RMSE_BLOCKS 1024
 int std_rmse_static(int32_t order, const int64_t* mode_sizes, const int32_t* ranks, int32_t r_core,

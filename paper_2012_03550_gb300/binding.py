@@ -247,10 +247,63 @@ def std_set_params(ctx, A=None, B=None, epoch: int = -1) -> None:
     _check(lib().std_set_params(ctx, Ap, Bp, int(epoch)))
 
 
+def check_static_args(order, mode_sizes, ranks, r_core, A, B, k, coords, values, out, current_device=None):
+    """Host-side checks of std_rmse_static's arguments, raising ValueError.
+
+    The library receives raw device pointers and cannot tell a host array, a
+    tensor on another device, a wrong dtype or a short buffer from a valid
+    one; any of those would make its kernels read out of bounds.  So every
+    array must be a contiguous CUDA tensor on `current_device` (an index; the
+    current device when None): A[n] float32 (I_n, J_n), B[n] float32 (J_n,
+    r_core), coords int32 with at least k rows of N columns, values float32
+    with at least k entries, out float64 with at least 2 entries."""
+    order, r_core, k = int(order), int(r_core), int(k)
+    mode_sizes = [int(x) for x in mode_sizes]
+    ranks = [int(x) for x in ranks]
+    if len(mode_sizes) != order or len(ranks) != order:
+        raise ValueError("mode_sizes and ranks need one entry per mode")
+    if len(A) != order or len(B) != order:
+        raise ValueError("A and B need one matrix per mode")
+    if k < 0:
+        raise ValueError("k must be >= 0")
+    if current_device is None:
+        import torch
+        if not torch.cuda.is_available():
+            raise ValueError("std_rmse_static needs a CUDA device")
+        current_device = torch.cuda.current_device()
+
+    def tensor(x, what, dtype_name, shape=None, min_rows=None, min_numel=None):
+        if not (hasattr(x, "is_cuda") and hasattr(x, "data_ptr")):
+            raise ValueError(f"{what} must be a CUDA torch tensor, got {type(x).__name__}")
+        if not x.is_cuda or x.device.index != current_device:
+            raise ValueError(f"{what} must live on cuda:{current_device}, not {x.device}")
+        if str(x.dtype) != f"torch.{dtype_name}":
+            raise ValueError(f"{what} must be {dtype_name}, not {x.dtype}")
+        if not x.is_contiguous():
+            raise ValueError(f"{what} must be contiguous")
+        if shape is not None and tuple(x.shape) != tuple(shape):
+            raise ValueError(f"{what} has shape {tuple(x.shape)}, expected {tuple(shape)}")
+        if min_rows is not None and (x.dim() != 2 or x.shape[0] < min_rows[0] or x.shape[1] != min_rows[1]):
+            raise ValueError(f"{what} has shape {tuple(x.shape)}, expected at least ({min_rows[0]}, {min_rows[1]})")
+        if min_numel is not None and x.numel() < min_numel:
+            raise ValueError(f"{what} has {x.numel()} entries, needs at least {min_numel}")
+
+    for n in range(order):
+        tensor(A[n], f"A[{n}]", "float32", shape=(mode_sizes[n], ranks[n]))
+        tensor(B[n], f"B[{n}]", "float32", shape=(ranks[n], r_core))
+    if k > 0:
+        tensor(coords, "coords", "int32", min_rows=(k, order))
+        tensor(values, "values", "float32", min_numel=k)
+    tensor(out, "out", "float64", min_numel=2)
+
+
 def std_rmse_static(order, mode_sizes, ranks, r_core, A, B, k, coords, values, out, stream=None) -> None:
     """Allocation-free RMSE/MAE: A, B lists of device tensors, coords/values/out
     device tensors (out: 2 float64); enqueued on `stream` (a cudaStream_t
-    handle or None).  Read `out` after synchronising the stream."""
+    handle or None).  Read `out` after synchronising the stream.  The
+    arguments are checked on the host first (check_static_args): a bad one
+    raises ValueError and nothing is launched."""
+    check_static_args(order, mode_sizes, ranks, r_core, A, B, k, coords, values, out)
     ms = np.ascontiguousarray(mode_sizes, dtype=np.int64)
     rk = np.ascontiguousarray(ranks, dtype=np.int32)
     _check(lib().std_rmse_static(int(order), ms.ctypes.data, rk.ctypes.data, int(r_core), _ptr_array(A),

@@ -36,7 +36,8 @@ struct StaticArgs {
 // Same arithmetic as the context's prediction/RMSE kernel: x-hat =
 // sum_r prod_n <a(n)_{i_n}, b(n)_r>, FP64 sums of (x - x-hat)^2 and
 // |x - x-hat| per block in a fixed tree order.  An index outside [0, I_n)
-// contributes NaN, so the result is NaN.
+// contributes NaN to both sums (the bounds are checked before any read), so
+// both results are NaN.
 __global__ void __launch_bounds__(kStaticThreads)
 k_rmse_static(StaticArgs a, double* __restrict__ scratch) {
   extern __shared__ float Bs[];
@@ -54,7 +55,9 @@ k_rmse_static(StaticArgs a, double* __restrict__ scratch) {
       else rows[n] = a.A[n] + (size_t)v * g.J[n];
     }
     if (!ok) {
-      se += __longlong_as_double(0x7ff8000000000000LL);
+      const double nan = __longlong_as_double(0x7ff8000000000000LL);
+      se += nan;
+      ae += nan;
       continue;
     }
     float xhat = 0.f;
@@ -108,7 +111,10 @@ __global__ void k_rmse_static_finish(const double* __restrict__ scratch, int blo
 }
 
 // Device address of g_rmse_scratch, looked up once per device with that
-// device current (the host-side name of the array is only a stand-in).
+// device current (the host-side name of the array is only a stand-in).  The
+// address is cached for the life of the process: it belongs to the device's
+// primary context, so after cudaDeviceReset it is stale and this entry point
+// must not be called again in that process.
 constexpr int kMaxDevices = 64;
 std::mutex g_mu;
 double* g_scratch_ptr[kMaxDevices] = {};

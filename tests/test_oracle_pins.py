@@ -335,6 +335,43 @@ def test_momentum_first_step_is_plain_sgd_and_zero_momentum_is_sgd():
         assert not np.array_equal(mom.A[n], plain.A[n])
 
 
+def test_momentum_kruskal_columns_three_steps_by_hand():
+    # Heavy-ball on the Kruskal columns alone (lr_a = 0 freezes every factor
+    # row), written out from the model's definition: x-hat_s = sum_r prod_n
+    # <a(n)_{i_n}, b(n)_r> (Def. 6 with the core of Eq. 4), so the bracket of
+    # Eq. 15 for column r of mode n is V = sum_s (x-hat_s - x_s) w_s[r] a(n)_{i_n},
+    # w_s[r] = prod_{k != n} <a(k)_{i_k}, b(k)_r>, with x-hat taken at the
+    # current columns (Algorithm 1 moves one column at a time, modes in order).
+    # Then g = V / M + lambda b, v <- mu v + g, b <- b - gamma v, velocities
+    # carried from one minibatch to the next.  A velocity that is not carried,
+    # or one kept under the wrong (mode, j, r) index, changes steps 2 and 3.
+    shape, ranks, R, mu = (6, 5, 4), (3, 2, 3), 3, 0.6
+    gam, lam = 0.05, 0.02
+    base = _random_model(shape, ranks, R, seed=61, scale=0.7)
+    md = O.Model(shape, ranks, R, base.A, base.B, momentum=mu)
+    A = [a.copy() for a in base.A]
+    Bh = [b.copy() for b in base.B]
+    VB = [np.zeros_like(b) for b in Bh]
+    for step in range(3):
+        coords, x = _random_batch(shape, 15, seed=70 + step, distinct=False)
+        md.step(coords, x, 0.0, gam, 0.3, lam)
+        M = coords.shape[0]
+        rows = [A[n][coords[:, n]] for n in range(3)]          # a(n)_{i_n} per sample, M x J_n
+        for n in range(3):
+            for r in range(R):
+                dots = np.stack([rows[k] @ Bh[k] for k in range(3)])     # [k][s][r']
+                xhat = np.prod(dots, axis=0).sum(axis=1)
+                w = np.prod([dots[k][:, r] for k in range(3) if k != n], axis=0)
+                V = ((xhat - x.astype(np.float64)) * w) @ rows[n]
+                g = V / M + lam * Bh[n][:, r]
+                VB[n][:, r] = mu * VB[n][:, r] + g
+                Bh[n][:, r] = Bh[n][:, r] - gam * VB[n][:, r]
+        for n in range(3):
+            np.testing.assert_allclose(md.B[n], Bh[n], rtol=1e-11, atol=1e-13)
+            np.testing.assert_allclose(md.VB[n], VB[n], rtol=1e-11, atol=1e-13)
+            np.testing.assert_array_equal(md.A[n], A[n])
+
+
 # ---------------------------------------------------------------------------
 # Descent (Theorem 3): each block step is a small gradient step on a convex
 # quadratic, so the sampled objective decreases.

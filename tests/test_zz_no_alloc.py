@@ -6,7 +6,10 @@ afford cudaMalloc/cudaFree, which synchronises the device).  Its scratch is a
 fixed array inside the library shared by every call, so this test calls it
 twice in a row, with different sizes, and checks each result against the
 context's std_rmse within the tolerance of the RMSE parity tests (1e-5
-relative).  This file is collected last on purpose.
+relative) and against the FP64 oracle's RMSE/MAE of the same FP32 model; it
+also checks that a call after the first allocates no device memory, and that
+an out-of-range coordinate gives NaN without being read through.  This file
+is collected last on purpose.
 """
 import numpy as np
 import pytest
@@ -43,21 +46,54 @@ def test_rmse_static_matches_std_rmse_on_consecutive_calls():
     dv = torch.from_numpy(tv).to(dev)
     out = torch.empty(2, dtype=torch.float64, device=dev)
     stream = torch.cuda.current_stream(dev)
-    cases = [(tc.shape[0], dc, dv, want_full), (sub, dc[:sub], dv[:sub], want_sub),
-             (tc.shape[0], dc, dv, want_full)]
-    for k, cc, vv, want in cases:
+    from oracle import oracle as O
+    ref = O.Model(shape, ranks, R, A1, B1)
+    ref.build_core()
+    orc_full = ref.rmse_mae(tc, tv)
+    orc_sub = ref.rmse_mae(tc[:sub], tv[:sub])
+    cases = [(tc.shape[0], dc, dv, want_full, orc_full), (sub, dc[:sub], dv[:sub], want_sub, orc_sub),
+             (tc.shape[0], dc, dv, want_full, orc_full)]
+    for i, (k, cc, vv, want, orc) in enumerate(cases):
         out.fill_(-1.0)
+        if i == 1:
+            torch.cuda.synchronize()
+            alloc0 = torch.cuda.memory_allocated(dev)
+            free0 = torch.cuda.mem_get_info(dev)[0]
         B.std_rmse_static(3, shape, ranks, R, dA, dB, k, cc, vv, out, stream.cuda_stream)
         stream.synchronize()
+        if i == 1:
+            # after the first call (which may load the module and look up the
+            # scratch address) a call takes no device memory at all
+            assert torch.cuda.memory_allocated(dev) == alloc0
+            assert torch.cuda.mem_get_info(dev)[0] == free0
         got = out.cpu().numpy()
         assert abs(got[0] - want[0]) <= 1e-5 * want[0], (got, want)
         assert abs(got[1] - want[1]) <= 1e-5 * want[1], (got, want)
+        # the FP32 model's RMSE/MAE in FP64 (Eq. 19): FP32 predictions differ
+        # from the oracle's FP64 ones by a few ulps of x-hat
+        assert abs(got[0] - orc[0]) <= 1e-5 * orc[0], (got, orc)
+        assert abs(got[1] - orc[1]) <= 1e-5 * orc[1], (got, orc)
+
+    # a coordinate equal to I_n is checked before any read: both results NaN
+    bad = dc[:16].clone()
+    bad[5, 1] = shape[1]
+    out.fill_(-1.0)
+    B.std_rmse_static(3, shape, ranks, R, dA, dB, 16, bad, dv[:16], out, stream.cuda_stream)
+    stream.synchronize()
+    assert np.isnan(out.cpu().numpy()).all()
 
     # k = 0 writes {0, 0}; a size beyond the limits is refused
     out.fill_(-1.0)
     B.std_rmse_static(3, shape, ranks, R, dA, dB, 0, dc, dv, out, stream.cuda_stream)
     stream.synchronize()
     assert out.cpu().tolist() == [0.0, 0.0]
-    with pytest.raises(B.StdError) as ei:
+    # the library's own limit check (the binding's shape checks would stop
+    # this call first, so the library is called directly)
+    import ctypes
+    ms = np.ascontiguousarray(shape, dtype=np.int64)
+    rk = np.ascontiguousarray(ranks, dtype=np.int32)
+    rc = B.lib().std_rmse_static(3, ms.ctypes.data, rk.ctypes.data, 64, B._ptr_array(dA), B._ptr_array(dB), 10,
+                                 dc.data_ptr(), dv.data_ptr(), out.data_ptr(), ctypes.c_void_p(stream.cuda_stream))
+    assert rc == B.STD_EUNSUPPORTED
+    with pytest.raises(ValueError):
         B.std_rmse_static(3, shape, ranks, 64, dA, dB, 10, dc, dv, out, stream.cuda_stream)
-    assert ei.value.code == B.STD_EUNSUPPORTED
