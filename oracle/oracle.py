@@ -79,6 +79,9 @@ def _declare(L):
     L.orc_step_momentum.restype = _int
     L.orc_step_momentum.argtypes = common + [_P, _i64, _P, _P, _dbl, _dbl, _dbl, _dbl, _int, _int, _P, _P, _P,
                                              _dbl, _P, _P]
+    L.orc_epoch_snapshot.restype = _int
+    L.orc_epoch_snapshot.argtypes = common + [_P, _i64, _P, _P, _i64, _u64, _u64, _i64, _i64, _i64,
+                                              _dbl, _dbl, _dbl, _dbl, _int]
     L.orc_epoch_momentum.restype = _int
     L.orc_epoch_momentum.argtypes = common + [_P, _i64, _P, _P, _i64, _u64, _u64, _i64, _i64,
                                               _dbl, _dbl, _dbl, _dbl, _int, _dbl, _P, _P]
@@ -256,3 +259,19 @@ class Model:
                                         float(lr_a), float(lr_b), float(lam_a), float(lam_b), int(norm_mode),
                                         *self._vel()))
         self.build_core()
+
+    def epoch_snapshot(self, coords, values, M, seed, epoch, K, lr_a, lr_b, lam_a, lam_b, norm_mode=0,
+                       batch_begin=0, batch_end=None):
+        """K-snapshot form: minibatches in blocks of K (from batch_begin), each
+        minibatch of a block stepping from the block's starting model, their
+        changes added to it in minibatch order (orc_epoch_snapshot)."""
+        if self.mu != 0.0 and K > 1:
+            raise ValueError("momentum is not defined for the K-snapshot form")
+        coords = np.ascontiguousarray(coords, dtype=np.int32)
+        values = np.ascontiguousarray(values, dtype=np.float32)
+        n = coords.shape[0]
+        if batch_end is None:
+            batch_end = (n + M - 1) // M
+        _check(lib().orc_epoch_snapshot(*self._args(), _ptr(self.G), n, _ptr(coords), _ptr(values), int(M),
+                                        int(seed), int(epoch), int(batch_begin), int(batch_end), int(K),
+                                        float(lr_a), float(lr_b), float(lam_a), float(lam_b), int(norm_mode)))

@@ -366,21 +366,25 @@ static void orc_core_V(const orc_model *md, int n, int rc, int64_t m, const doub
     }
 }
 
-/* SGD(M, lambda, gamma, w, grad) (Sec. 3.2, Eq. 3): w <- w - gamma (grad/M + lambda w). */
-static double orc_sgd(double w, double grad, double M, double lambda, double gamma)
+/* SGD(M, lambda, gamma, w, grad) (Sec. 3.2, Eq. 3): w <- w - gamma (grad/M + lambda w),
+ * returned as the change delta = -(gamma (grad/M + lambda w)); the caller sets
+ * w <- w + delta, which is the same IEEE result as w - gamma (...) (x - y is
+ * x + (-y) exactly, and this file is compiled without contraction). */
+static double orc_sgd_delta(double w, double grad, double M, double lambda, double gamma)
 {
-    return w - gamma * (grad / M + lambda * w);
+    return -(gamma * (grad / M + lambda * w));
 }
 
 /* Heavy-ball momentum (Polyak 1964), the accelerated SGD the paper names as
  * future work (Sec. 6): with g = grad / M + lambda w the velocity becomes
- * v <- mu v + g and the parameter w <- w - gamma v.  mu = 0 gives orc_sgd. */
-static double orc_sgd_momentum(double w, double *v, double grad, double M, double lambda, double gamma,
-                               double mu)
+ * v <- mu v + g and the parameter w <- w - gamma v (returned as the change
+ * -(gamma v)).  mu = 0 gives orc_sgd_delta. */
+static double orc_sgd_momentum_delta(double w, double *v, double grad, double M, double lambda, double gamma,
+                                     double mu)
 {
     const double g = grad / M + lambda * w;
     *v = mu * (*v) + g;
-    return w - gamma * (*v);
+    return -(gamma * (*v));
 }
 
 /* ------------------------------------------------------------------------ */
@@ -557,6 +561,12 @@ int orc_factor_gradient(int N, const int64_t *I, const int32_t *J, int R, double
  * i_n, the factor-phase bracket F of Eq. 18 (layout [n][u][Jmax], u < m), with the number of
  * segments per mode in probe_nseg[n].
  */
+static int orc_step_impl(int N, const int64_t *I, const int32_t *J, int R, double **A, double **B, double *G,
+                         int64_t m, const int32_t *coords, const float *values,
+                         double gamma_a, double gamma_b, double lambda_a, double lambda_b,
+                         int norm_mode, int literal, double *probe_V, double *probe_F, int64_t *probe_nseg,
+                         double mu, double **VA, double **VB, double **accA, double **accB);
+
 int orc_step_momentum(int N, const int64_t *I, const int32_t *J, int R, double **A, double **B, double *G,
                       int64_t m, const int32_t *coords, const float *values,
                       double gamma_a, double gamma_b, double lambda_a, double lambda_b,
@@ -584,6 +594,23 @@ int orc_step_momentum(int N, const int64_t *I, const int32_t *J, int R, double *
                       double gamma_a, double gamma_b, double lambda_a, double lambda_b,
                       int norm_mode, int literal, double *probe_V, double *probe_F, int64_t *probe_nseg,
                       double mu, double **VA, double **VB)
+{
+    return orc_step_impl(N, I, J, R, A, B, G, m, coords, values, gamma_a, gamma_b, lambda_a, lambda_b, norm_mode,
+                         literal, probe_V, probe_F, probe_nseg, mu, VA, VB, NULL, NULL);
+}
+
+/*
+ * The step itself.  Every update w <- w + delta of Algorithm 1 is applied to
+ * the model (A, B), which this minibatch's own later steps read (Gauss-Seidel
+ * order); when accA / accB are given, the same delta is also added to the
+ * matching entry of a second model (accA[n] like A[n], accB[n] like B[n]):
+ * the accumulation of the K-snapshot form (orc_epoch_snapshot).
+ */
+static int orc_step_impl(int N, const int64_t *I, const int32_t *J, int R, double **A, double **B, double *G,
+                         int64_t m, const int32_t *coords, const float *values,
+                         double gamma_a, double gamma_b, double lambda_a, double lambda_b,
+                         int norm_mode, int literal, double *probe_V, double *probe_F, int64_t *probe_nseg,
+                         double mu, double **VA, double **VB, double **accA, double **accB)
 {
     orc_model md;
     int rc = orc_setup(&md, N, I, J, R, A, B, G);
@@ -615,10 +642,14 @@ int orc_step_momentum(int N, const int64_t *I, const int32_t *J, int R, double *
                 for (int j = 0; j < Jn; ++j) probe_V[((int64_t)n * R + r) * Jmax + j] = V[j];
             for (int j = 0; j < Jn; ++j) {                            /* b_r update */
                 double *b = &md.B[n][(int64_t)j * R + r];
+                double d;
                 if (VB)
-                    *b = orc_sgd_momentum(*b, &VB[n][(int64_t)j * R + r], V[j], (double)m, lambda_b, gamma_b, mu);
+                    d = orc_sgd_momentum_delta(*b, &VB[n][(int64_t)j * R + r], V[j], (double)m, lambda_b,
+                                               gamma_b, mu);
                 else
-                    *b = orc_sgd(*b, V[j], (double)m, lambda_b, gamma_b);
+                    d = orc_sgd_delta(*b, V[j], (double)m, lambda_b, gamma_b);
+                *b = *b + d;
+                if (accB) accB[n][(int64_t)j * R + r] += d;
             }
         }
     }
@@ -641,10 +672,13 @@ int orc_step_momentum(int N, const int64_t *I, const int32_t *J, int R, double *
             const int64_t row = coords[(int64_t)ids[0] * N + n];
             double *a = md.A[n] + row * Jn;
             for (int j = 0; j < Jn; ++j) {                            /* row update */
+                double d;
                 if (VA)
-                    a[j] = orc_sgd_momentum(a[j], &VA[n][row * Jn + j], F[j], denom, lambda_a, gamma_a, mu);
+                    d = orc_sgd_momentum_delta(a[j], &VA[n][row * Jn + j], F[j], denom, lambda_a, gamma_a, mu);
                 else
-                    a[j] = orc_sgd(a[j], F[j], denom, lambda_a, gamma_a);
+                    d = orc_sgd_delta(a[j], F[j], denom, lambda_a, gamma_a);
+                a[j] = a[j] + d;
+                if (accA) accA[n][row * Jn + j] += d;
             }
         }
     }
@@ -704,5 +738,75 @@ int orc_epoch_momentum(int N, const int64_t *I, const int32_t *J, int R, double 
                                norm_mode, 0, NULL, NULL, NULL, mu, VA, VB);
     }
     free(bc); free(bv);
+    return rc;
+}
+
+/*
+ * K-snapshot form of the minibatch sequence (not Algorithm 1's order: a
+ * labelled variant).  The minibatches [batch_begin, batch_end) of epoch
+ * `epoch` are taken in blocks of K consecutive ones, the first block starting
+ * at batch_begin.  Every minibatch of a block runs Algorithm 1's step (core
+ * phase, G-hat, factor phase, with its own Gauss-Seidel order) from the same
+ * snapshot: the model as it stood when the block began.  The changes delta
+ * each minibatch made to the Kruskal columns and factor rows are then added
+ * to the snapshot in minibatch order:
+ *     theta <- ((theta_0 + delta_1) + delta_2) + ... + delta_K.
+ * K = 1 is orc_epoch exactly (theta_0 + delta_1 is the strict step's
+ * result).  Heavy-ball momentum is not defined for K > 1 (ORC_EINVAL).
+ */
+int orc_epoch_snapshot(int N, const int64_t *I, const int32_t *J, int R, double **A, double **B, double *G,
+                       int64_t n_train, const int32_t *coords, const float *values, int64_t M,
+                       uint64_t seed, uint64_t epoch, int64_t batch_begin, int64_t batch_end, int64_t K,
+                       double gamma_a, double gamma_b, double lambda_a, double lambda_b, int norm_mode)
+{
+    if (M < 1 || n_train < 1 || N < 1 || N > ORC_MAXN || K < 1) return ORC_EINVAL;
+    int64_t nb = (n_train + M - 1) / M;
+    if (batch_begin < 0) batch_begin = 0;
+    if (batch_end > nb) batch_end = nb;
+    int32_t *bc = (int32_t *)malloc((size_t)(M * N) * sizeof(int32_t));
+    float *bv = (float *)malloc((size_t)M * sizeof(float));
+    double *WA[ORC_MAXN] = {0}, *WB[ORC_MAXN] = {0}, *SA[ORC_MAXN] = {0}, *SB[ORC_MAXN] = {0};
+    int64_t P = 1;
+    for (int n = 0; n < N; ++n) P *= J[n];
+    double *WG = (double *)malloc((size_t)P * sizeof(double));
+    int rc = (bc && bv && WG) ? ORC_OK : ORC_ENOMEM;
+    for (int n = 0; n < N && rc == ORC_OK; ++n) {
+        const size_t na = (size_t)I[n] * (size_t)J[n] * sizeof(double), nbb = (size_t)J[n] * R * sizeof(double);
+        WA[n] = (double *)malloc(na); SA[n] = (double *)malloc(na);
+        WB[n] = (double *)malloc(nbb); SB[n] = (double *)malloc(nbb);
+        if (!WA[n] || !SA[n] || !WB[n] || !SB[n]) rc = ORC_ENOMEM;
+    }
+    uint64_t key[6];
+    orc_round_keys(seed, epoch, key);
+    int h = orc_half_bits((uint64_t)n_train);
+    for (int64_t q0 = batch_begin; q0 < batch_end && rc == ORC_OK; q0 += K) {
+        for (int n = 0; n < N; ++n) {                                   /* the snapshot theta_0 */
+            memcpy(SA[n], A[n], (size_t)I[n] * J[n] * sizeof(double));
+            memcpy(SB[n], B[n], (size_t)J[n] * R * sizeof(double));
+        }
+        for (int64_t b = q0; b < q0 + K && b < batch_end && rc == ORC_OK; ++b) {
+            int64_t t0 = b * M;
+            int64_t m = (t0 + M <= n_train) ? M : n_train - t0;
+            for (int64_t q = 0; q < m; ++q) {
+                uint64_t y = orc_feistel((uint64_t)(t0 + q), h, key);
+                while (y >= (uint64_t)n_train) y = orc_feistel(y, h, key);
+                for (int n = 0; n < N; ++n) bc[q * N + n] = coords[(int64_t)y * N + n];
+                bv[q] = values[y];
+            }
+            for (int n = 0; n < N; ++n) {                               /* this minibatch starts at theta_0 */
+                memcpy(WA[n], SA[n], (size_t)I[n] * J[n] * sizeof(double));
+                memcpy(WB[n], SB[n], (size_t)J[n] * R * sizeof(double));
+            }
+            rc = orc_step_impl(N, I, J, R, WA, WB, WG, m, bc, bv, gamma_a, gamma_b, lambda_a, lambda_b,
+                               norm_mode, 0, NULL, NULL, NULL, 0.0, NULL, NULL, A, B);
+        }
+    }
+    if (rc == ORC_OK) {
+        orc_model md;
+        rc = orc_setup(&md, N, I, J, R, A, B, G);
+        if (rc == ORC_OK) orc_core_from_B(&md);
+    }
+    for (int n = 0; n < N; ++n) { free(WA[n]); free(SA[n]); free(WB[n]); free(SB[n]); }
+    free(WG); free(bc); free(bv);
     return rc;
 }

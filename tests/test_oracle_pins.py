@@ -538,3 +538,135 @@ def test_step_is_cyclic_block_sgd(norm_mode):
     for n in range(3):
         np.testing.assert_allclose(md.B[n], ref.B[n], rtol=1e-12, atol=1e-13)
         np.testing.assert_allclose(md.A[n], ref.A[n], rtol=1e-12, atol=1e-13)
+
+
+# ---------------------------------------------------------------------------
+# K-snapshot form (a labelled variant of the minibatch order): blocks of K
+# minibatches, each stepping from the block's starting model; their changes
+# are added to it in minibatch order.
+# ---------------------------------------------------------------------------
+
+def test_snapshot_k1_is_the_strict_sequence_bit_for_bit():
+    shape, ranks, R = (9, 8, 7), (3, 2, 3), 2
+    coords, x = _random_batch(shape, 150, seed=81)
+    base = _random_model(shape, ranks, R, seed=82, scale=0.6)
+    strict = O.Model(shape, ranks, R, base.A, base.B)
+    snap = O.Model(shape, ranks, R, base.A, base.B)
+    strict.epoch(coords, x, 16, 5, 0, 0.2, 0.1, 0.01, 0.02)
+    snap.epoch_snapshot(coords, x, 16, 5, 0, 1, 0.2, 0.1, 0.01, 0.02)
+    for n in range(3):
+        np.testing.assert_array_equal(snap.A[n], strict.A[n])
+        np.testing.assert_array_equal(snap.B[n], strict.B[n])
+
+
+def _mf_step_delta(U, Vm, coords, x, gam, lam):
+    """One minibatch of textbook alternating matrix-factorisation SGD from
+    (U, Vm): the changes it makes to the rows of U, then (with U updated) to
+    the rows of Vm, as dicts row -> change."""
+    M = coords.shape[0]
+    dU, dV = {}, {}
+    U1 = U.copy()
+    for i in np.unique(coords[:, 0]):
+        grad = np.zeros(U.shape[1])
+        for s in np.where(coords[:, 0] == i)[0]:
+            grad += (U[i] @ Vm[coords[s, 1]] - float(x[s])) * Vm[coords[s, 1]]
+        dU[i] = -(gam * (grad / M + lam * U[i]))
+        U1[i] = U[i] + dU[i]
+    for k in np.unique(coords[:, 1]):
+        grad = np.zeros(U.shape[1])
+        for s in np.where(coords[:, 1] == k)[0]:
+            grad += (U1[coords[s, 0]] @ Vm[k] - float(x[s])) * U1[coords[s, 0]]
+        dV[k] = -(gam * (grad / M + lam * Vm[k]))
+    return dU, dV
+
+
+def test_snapshot_k2_matrix_factorisation_by_hand():
+    # N = 2, B = I, lr_b = 0: the factor phase is textbook alternating MF SGD.
+    # Two blocks of K = 2 minibatches (the second block a single short one):
+    # in a block both minibatches step from the block's start, and the rows'
+    # changes are added in minibatch order (row 2 is touched by both).
+    J = 3
+    g = _rng(83)
+    U = g.standard_normal((5, J))
+    Vm = g.standard_normal((4, J))
+    md = O.Model((5, 4), (J, J), J, [U, Vm], [np.eye(J), np.eye(J)])
+    coords = np.array([[2, 1], [2, 3], [0, 1], [2, 0], [1, 1], [4, 3], [3, 2]], dtype=np.int32)
+    x = np.array([0.7, -1.2, 0.4, 0.1, 0.9, -0.5, 0.3], dtype=np.float32)
+    gam, lam, M, K = 0.3, 0.05, 3, 2
+    # the oracle's minibatch b holds the entries at positions pi_0(bM ..)
+    order = O.perm_range(7, 2, 0, 0, 7)
+    md.epoch_snapshot(coords[order], x[order], M, 2, 0, K, gam, 0.0, lam, 0.0)
+    # by hand: re-read the same permutation of the permuted arrays
+    perm = O.perm_range(7, 2, 0, 0, 7)
+    cb, xb = coords[order][perm], x[order][perm]
+    u, v = U.copy(), Vm.copy()
+    for q0 in range(0, 3, K):
+        u0, v0 = u.copy(), v.copy()
+        for b in range(q0, min(q0 + K, 3)):
+            sl = slice(b * M, min((b + 1) * M, 7))
+            dU, dV = _mf_step_delta(u0, v0, cb[sl], xb[sl], gam, lam)
+            for i, d in dU.items():
+                u[i] = u[i] + d
+            for k, d in dV.items():
+                v[k] = v[k] + d
+    np.testing.assert_allclose(md.A[0], u, rtol=1e-13, atol=1e-14)
+    np.testing.assert_allclose(md.A[1], v, rtol=1e-13, atol=1e-14)
+    np.testing.assert_array_equal(md.B[0], np.eye(J))
+
+
+def test_snapshot_k2_kruskal_columns_by_hand():
+    # lr_a = 0: only the core phase moves.  Each minibatch of the block runs
+    # the cyclic column updates (Eq. 15 bracket from the model's definition)
+    # from the block's starting B; the column changes are added in order.
+    shape, ranks, R = (6, 5, 4), (3, 2, 3), 3
+    gam, lam, M, K = 0.05, 0.02, 12, 2
+    base = _random_model(shape, ranks, R, seed=84, scale=0.7)
+    coords, x = _random_batch(shape, 36, seed=85, distinct=False)
+    md = O.Model(shape, ranks, R, base.A, base.B)
+    md.epoch_snapshot(coords, x, M, 3, 1, K, 0.0, gam, 0.4, lam)
+    perm = O.perm_range(36, 3, 1, 0, 36)
+    cb, xb = coords[perm], x[perm].astype(np.float64)
+    A = [a.copy() for a in base.A]
+    Bh = [b.copy() for b in base.B]
+    for q0 in range(0, 3, K):
+        B0 = [b.copy() for b in Bh]
+        for b in range(q0, min(q0 + K, 3)):
+            sl = slice(b * M, (b + 1) * M)
+            rows = [A[n][cb[sl, n]] for n in range(3)]
+            W = [b_.copy() for b_ in B0]
+            for n in range(3):
+                for r in range(R):
+                    dots = np.stack([rows[k] @ W[k] for k in range(3)])
+                    xhat = np.prod(dots, axis=0).sum(axis=1)
+                    w = np.prod([dots[k][:, r] for k in range(3) if k != n], axis=0)
+                    V = ((xhat - xb[sl]) * w) @ rows[n]
+                    d = -(gam * (V / M + lam * W[n][:, r]))
+                    W[n][:, r] = W[n][:, r] + d
+                    Bh[n][:, r] = Bh[n][:, r] + d
+    for n in range(3):
+        np.testing.assert_allclose(md.B[n], Bh[n], rtol=1e-11, atol=1e-13)
+        np.testing.assert_array_equal(md.A[n], A[n])
+
+
+def test_snapshot_block_covering_the_epoch_steps_everything_from_the_start():
+    # K at least the number of minibatches: every minibatch steps from the
+    # initial model, so the result is the initial model plus the sum of the
+    # single-minibatch changes, whatever their order of computation.
+    shape, ranks, R = (7, 6, 5), (2, 3, 2), 2
+    coords, x = _random_batch(shape, 40, seed=86)
+    base = _random_model(shape, ranks, R, seed=87, scale=0.6)
+    md = O.Model(shape, ranks, R, base.A, base.B)
+    md.epoch_snapshot(coords, x, 10, 4, 2, 8, 0.2, 0.1, 0.01, 0.02)
+    perm = O.perm_range(40, 4, 2, 0, 40)
+    want_A = [a.copy() for a in base.A]
+    want_B = [b.copy() for b in base.B]
+    for b in range(4):
+        one = O.Model(shape, ranks, R, base.A, base.B)
+        sl = perm[b * 10:(b + 1) * 10]
+        one.step(coords[sl], x[sl], 0.2, 0.1, 0.01, 0.02)
+        for n in range(3):
+            want_A[n] += one.A[n] - base.A[n]
+            want_B[n] += one.B[n] - base.B[n]
+    for n in range(3):
+        np.testing.assert_allclose(md.A[n], want_A[n], rtol=1e-12, atol=1e-14)
+        np.testing.assert_allclose(md.B[n], want_B[n], rtol=1e-12, atol=1e-14)
