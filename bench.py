@@ -54,6 +54,16 @@ def _args():
     p.add_argument("--no-bf16", action="store_true")
     p.add_argument("--no-kruskal", action="store_true")
     p.add_argument("--no-momentum", action="store_true")
+    p.add_argument("--no-parity", action="store_true", help="skip the GPU-vs-oracle parameter comparison")
+    p.add_argument("--no-snapshot", action="store_true", help="skip the K-snapshot form")
+    p.add_argument("--snapshot-ks", type=int, nargs="*", default=[2, 4, 8])
+    p.add_argument("--no-sub", action="store_true",
+                   help="skip the 4-order, batched and serving sub-records of the default line")
+    p.add_argument("--variant-steps", type=int, default=5,
+                   help="timed epochs of the BF16, Kruskal and momentum forms in the default line")
+    p.add_argument("--sub-serve-seconds", type=float, default=30.0)
+    p.add_argument("--sub-order4-scale", type=float, default=0.25)
+    p.add_argument("--sub-batched-scale", type=float, default=1.0)
     p.add_argument("--batched", action="store_true",
                    help="batched workload instead of the default line: 256 independent 3-order tensors "
                         "(lognormal sizes, J in {4, 8, 16}) in one persistent launch per epoch")
@@ -126,6 +136,48 @@ def _bytes_per_nnz(N, J, s_f=4):
     # (N+1) passes each read the COO entry ((N+1) words) and N factor rows;
     # the N factor modes each write and read back one FP32 gradient row.
     return (N + 1) * ((4 * N + 4) + N * J * s_f) + N * J * 8
+
+
+def _oracle_worker(args):
+    """One host core: the oracle's minibatch steps on its own minibatches
+    from the shared initial state; returns the seconds they took."""
+    shape, ranks, R, A0, B0, batches, lr, lam = args
+    from oracle import oracle as O
+    md = O.Model(shape, ranks, R, A0, B0)
+    t0 = time.perf_counter()
+    for bc, bv in batches:
+        md.step(bc, bv, lr, lr, lam, lam)
+    return time.perf_counter() - t0
+
+
+def _oracle_all_cores(t, w, c, v, A0, B0, M, per_core=8):
+    """The oracle (unchanged, one process per host core) on independent
+    minibatches from one state: the host's aggregate oracle throughput.  The
+    strict minibatch sequence has no parallel split, so this is a capacity
+    figure (replicas), and the epoch time from it is an extrapolation."""
+    import multiprocessing as mp
+    cores = os.cpu_count() or 1
+    from oracle import oracle as O
+    try:
+        O.build()
+        ids = O.perm_range(c.shape[0], 2, 0, 0, cores * per_core * M)
+        jobs = []
+        for q in range(cores):
+            bl = []
+            for b in range(per_core):
+                sl = ids[(q * per_core + b) * M:(q * per_core + b + 1) * M]
+                bl.append((c[sl], v[sl]))
+            jobs.append((t.shape, w.ranks, w.r_core, A0, B0, bl, w.lr, w.lam))
+        ctx = mp.get_context("spawn")
+        with ctx.Pool(cores) as pool:
+            secs = pool.map(_oracle_worker, jobs)
+    except Exception as e:                                      # reported, never fatal to the bench
+        return {"error": f"{type(e).__name__}: {e}"}
+    rate = cores * per_core * M / max(secs)
+    return {"value": rate, "unit": "nnz/s", "cores": cores, "kind": "oracle",
+            "sample": f"{per_core} minibatches of {M} per core, one process per core, all from the initial state "
+                      f"(independent replicas; the slowest core's time)",
+            "epoch_s_extrapolated": c.shape[0] / rate}
 
 
 class ClockSampler:
@@ -266,11 +318,16 @@ def run_gpu(a):
     ctx = B.std_create(N, t.shape, w.ranks, c.shape[0], dc, dv, opt)
     B.std_set_params(ctx, [np.ascontiguousarray(x) for x in A0], [np.ascontiguousarray(x) for x in B0], 0)
 
+    rm_at = {}    # test RMSE of the main run after e epochs
+
     def step():
         st = B.std_sgd_epoch(ctx, w.lr, w.lr, w.lam, w.lam, M)
         r = B.std_rmse(ctx, tc.shape[0], dtc, dtv)
+        rm_at[st["epoch"] + 1] = r[0]
         return st, r
 
+    vsteps = max(1, min(a.steps, a.variant_steps))
+    vwarm = min(a.warmup, 3)
     for _ in range(a.warmup):
         step()
     sampler = ClockSampler(local)
@@ -308,7 +365,7 @@ def run_gpu(a):
         cx16 = B.std_create(N, t.shape, w.ranks, c.shape[0], dc, dv, o16)
         B.std_set_params(cx16, [np.ascontiguousarray(x) for x in A0], [np.ascontiguousarray(x) for x in B0], 0)
         rm16 = None
-        for _ in range(a.warmup):
+        for _ in range(vwarm):
             B.std_sgd_epoch(cx16, w.lr, w.lr, w.lam, w.lam, M)
             B.std_rmse(cx16, tc.shape[0], dtc, dtv)
         torch.cuda.synchronize()
@@ -316,20 +373,23 @@ def run_gpu(a):
         f1 = torch.cuda.Event(enable_timing=True)
         f0.record(stream)
         upd16 = []
-        for _ in range(a.steps):
+        for _ in range(vsteps):
             st16 = B.std_sgd_epoch(cx16, w.lr, w.lr, w.lam, w.lam, M)
             rm16 = B.std_rmse(cx16, tc.shape[0], dtc, dtv)
             upd16.append(st16["update_seconds"])
         f1.record(stream)
         torch.cuda.synchronize()
-        v16, e16 = D.weak_scaling_rate(float(n_train * a.steps), f0.elapsed_time(f1) * 1e-3, device=dev)
-        bf16 = {"value": v16, "unit": "nnz/s", "ms_per_step": 1e3 * e16 / a.steps,
+        v16, e16 = D.weak_scaling_rate(float(n_train * vsteps), f0.elapsed_time(f1) * 1e-3, device=dev)
+        bf16 = {"value": v16, "unit": "nnz/s", "ms_per_step": 1e3 * e16 / vsteps,
                 "kernel_ms": 1e3 * sum(upd16) / len(upd16),
                 "speedup_vs_fp32": v16 / value,
                 "test_rmse": rm16[0], "test_mae": rm16[1],
-                "test_rmse_gap_vs_fp32": abs(rm16[0] - rm[0]),
+                "test_rmse_gap_vs_fp32": (abs(rm16[0] - rm_at[vwarm + vsteps])
+                                          if (vwarm + vsteps) in rm_at else None),
                 "bytes_per_nnz": _bytes_per_nnz(N, J, 2),
-                "note": "same schedule and initial state as the FP32 run; RMSE after the same epochs"}
+                "epochs": vwarm + vsteps,
+                "note": ("same schedule and initial state as the FP32 run; test RMSE after its own epochs "
+                         "(the gap compares it with the FP32 run after as many epochs)")}
         B.std_destroy(cx16)
     def variant(**fields):
         """Same workload, schedule and initial state under other options."""
@@ -341,7 +401,7 @@ def run_gpu(a):
             setattr(ov, k_, v_)
         cxv = B.std_create(N, t.shape, w.ranks, c.shape[0], dc, dv, ov)
         B.std_set_params(cxv, [np.ascontiguousarray(x) for x in A0], [np.ascontiguousarray(x) for x in B0], 0)
-        for _ in range(a.warmup):
+        for _ in range(vwarm):
             B.std_sgd_epoch(cxv, w.lr, w.lr, w.lam, w.lam, M)
             B.std_rmse(cxv, tc.shape[0], dtc, dtv)
         torch.cuda.synchronize()
@@ -349,17 +409,17 @@ def run_gpu(a):
         v1 = torch.cuda.Event(enable_timing=True)
         v0.record(stream)
         updv, rmv = [], None
-        for _ in range(a.steps):
+        for _ in range(vsteps):
             stv = B.std_sgd_epoch(cxv, w.lr, w.lr, w.lam, w.lam, M)
             rmv = B.std_rmse(cxv, tc.shape[0], dtc, dtv)
             updv.append(stv["update_seconds"])
         v1.record(stream)
         torch.cuda.synchronize()
-        vv, ev = D.weak_scaling_rate(float(n_train * a.steps), v0.elapsed_time(v1) * 1e-3, device=dev)
+        vv, ev = D.weak_scaling_rate(float(n_train * vsteps), v0.elapsed_time(v1) * 1e-3, device=dev)
         B.std_destroy(cxv)
-        return {"value": vv, "unit": "nnz/s", "ms_per_step": 1e3 * ev / a.steps,
+        return {"value": vv, "unit": "nnz/s", "ms_per_step": 1e3 * ev / vsteps,
                 "kernel_ms": 1e3 * sum(updv) / len(updv), "speedup_vs_main": vv / value,
-                "test_rmse": rmv[0], "test_rmse_gap_vs_main": abs(rmv[0] - rm[0])}
+                "epochs": vwarm + vsteps, "test_rmse": rmv[0], "test_rmse_main_same_epochs": rm_at.get(vwarm + vsteps)}
 
     # the Kruskal form of the factor-phase contraction (E_s = B(n) w_s, the
     # same product as the Kronecker rows against the unfolded core)
@@ -372,6 +432,25 @@ def run_gpu(a):
     if not a.no_momentum:
         mom = variant(momentum=0.9)
         mom["note"] = "FP32, mu = 0.9, same learning rate; RMSE after the same epochs"
+    # the K-snapshot form (a labelled variant of the minibatch order: every
+    # minibatch of a block of K steps from the block's starting model, the
+    # changes added in minibatch order), K groups of CTAs at once
+    snap = None
+    if not a.no_snapshot:
+        snap = {"note": ("labelled variant, not Algorithm 1's order: blocks of K minibatches step from one model "
+                         "and their changes are added in minibatch order; FP32; roofline of its update kernel "
+                         "against the same bytes per nonzero")}
+        peak_s, _ = _peaks()
+        for K in a.snapshot_ks:
+            try:
+                r = variant(snapshot=K)
+            except B.StdError as e:
+                snap[f"K{K}"] = {"unavailable": str(e)}
+                continue
+            ach = n_train * _bytes_per_nnz(N, J) / (r["kernel_ms"] * 1e-3) / 1e9
+            r["roofline_frac"] = ach / peak_s
+            r["achieved_gbs"] = ach
+            snap[f"K{K}"] = r
     del dc, dv
 
     # roofline of the dominant kernel (the persistent update kernel)
@@ -421,6 +500,7 @@ def run_gpu(a):
 
     # CPU baseline: the oracle as it stands on a bounded sample (rank 0, N = 1)
     cpu = None
+    parity = None
     if not a.no_cpu_baseline and world == 1 and rank == 0:
         from oracle import oracle as O
         md = O.Model(t.shape, w.ranks, R, A0, B0)
@@ -428,10 +508,56 @@ def run_gpu(a):
         t0 = time.perf_counter()
         md.epoch(c, v, M, 2, 0, w.lr, w.lr, w.lam, w.lam, 0, 0, nb)
         dt = time.perf_counter() - t0
-        cpu = {"value": nb * M / dt, "unit": "nnz/s", "cores": 1, "kind": "oracle",
-               "sample": f"first {nb} minibatches ({nb * M} nonzeros) of epoch 0, FP64, single thread"}
+        cpu = {"value": nb * M / dt, "unit": "nnz/s", "cores": 1, "nproc": os.cpu_count(), "kind": "oracle",
+               "sample": f"first {nb} minibatches ({nb * M} nonzeros) of epoch 0, FP64, single thread",
+               "epoch_s_extrapolated": n_train / (nb * M / dt)}
+        allc = _oracle_all_cores(t, w, c, v, A0, B0, M)
+        if allc is not None:
+            cpu["all_cores"] = allc
+        # the same minibatches on the GPU from the same state, FP32 and BF16:
+        # parameters and test RMSE against the oracle's after them
+        if not a.no_parity:
+            parity = {"minibatches": nb, "from": "the bench's initial state, epoch 0"}
+            ro, mo = md.rmse_mae(tc, tv)
+            for name, prec in (("fp32", 0), ("bf16", 1)):
+                op = B.std_default_options()
+                op.r_core = R
+                op.ptr_kind = 1
+                op.precision = prec
+                op.stream = stream.cuda_stream
+                dcp, dvp = torch.from_numpy(c).to(dev), torch.from_numpy(v).to(dev)
+                cxp = B.std_create(N, t.shape, w.ranks, c.shape[0], dcp, dvp, op)
+                B.std_set_params(cxp, [np.ascontiguousarray(x) for x in A0],
+                                 [np.ascontiguousarray(x) for x in B0], 0)
+                B.std_sgd_batches(cxp, w.lr, w.lr, w.lam, w.lam, M, 0, nb)
+                Ag = [np.empty((t.shape[n], w.ranks[n]), np.float32) for n in range(N)]
+                Bg = [np.empty((w.ranks[n], R), np.float32) for n in range(N)]
+                B.std_get_params(cxp, Ag, Bg, None)
+                rg, mg = B.std_rmse(cxp, tc.shape[0], dtc, dtv)
+                B.std_destroy(cxp)
+                del dcp, dvp
+                parity[name] = {
+                    "max_rel_err_A": max(float(np.abs(Ag[n] - md.A[n]).max() / np.abs(md.A[n]).max())
+                                         for n in range(N)),
+                    "max_rel_err_B": max(float(np.abs(Bg[n] - md.B[n]).max() / np.abs(md.B[n]).max())
+                                         for n in range(N)),
+                    "test_rmse": rg, "test_mae": mg, "test_rmse_oracle": ro, "test_mae_oracle": mo,
+                    "test_rmse_abs_err": abs(rg - ro), "test_mae_abs_err": abs(mg - mo)}
+            parity["note"] = ("max over modes of max|gpu - oracle| / max|oracle| per factor / Kruskal matrix; "
+                              "RMSE/MAE over the test split (Eq. 19)")
 
     B.std_destroy(ctx)
+    del dtc, dtv
+    sub = {}
+    if not a.no_sub and world == 1:
+        torch.cuda.empty_cache()
+        for key, fn in (("order4", lambda: order4_record(a, a.sub_order4_scale, 1, 2)),
+                        ("batched", lambda: batched_record(a, a.sub_batched_scale, 1, 1)),
+                        ("serve", lambda: serve_record(a, a.sub_serve_seconds))):
+            t0 = time.time()
+            sub[key] = fn()
+            sub[key]["wall_s"] = round(time.time() - t0, 1)
+            torch.cuda.empty_cache()
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": "nnz/s", "n_gpus": world, "steps": a.steps,
@@ -449,6 +575,11 @@ def run_gpu(a):
             "bf16": bf16,
             "kruskal_contraction": kru,
             "momentum": mom,
+            "snapshot": snap,
+            "oracle_parity": parity,
+            "order4": sub.get("order4"),
+            "batched": sub.get("batched"),
+            "serve": sub.get("serve"),
             "gpu_launches": 4 * a.steps,
             "clocks": clocks,
             "test_rmse": rm[0] if rm else None,
@@ -563,6 +694,11 @@ def run_msweep(a):
 
 
 def run_order4(a):
+    print(json.dumps(order4_record(a, a.scale, a.warmup, a.steps)), flush=True)
+    return 0
+
+
+def order4_record(a, scale, warmup, steps):
     """The 4-order workload (200,000 x 100,000 x 500 x 24, 50M nonzeros at
     scale 1, J = 8, M = 8192): epoch throughput and test RMSE of the FP32 form
     and of the BF16 form, whose factor-phase contraction (512 x 8 per mode and
@@ -576,7 +712,7 @@ def run_order4(a):
     from paper_2012_03550_gb300 import synth
 
     t0 = time.time()
-    w = synth.config3(scale=a.scale)
+    w = synth.config3(scale=scale)
     gen_s = time.time() - t0
     t = w.tensor
     c, v = t.split("train")
@@ -595,34 +731,38 @@ def run_order4(a):
         opt.stream = stream.cuda_stream
         ctx = B.std_create(t.order, t.shape, w.ranks, c.shape[0], dc, dv, opt)
         B.std_set_params(ctx, [np.ascontiguousarray(x) for x in A0], [np.ascontiguousarray(x) for x in B0], 0)
-        for _ in range(a.warmup):
+        for _ in range(warmup):
             B.std_sgd_epoch(ctx, w.lr, w.lr, w.lam, w.lam, w.minibatch)
         torch.cuda.synchronize()
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         upd = 0.0
         e0.record(stream)
-        for _ in range(a.steps):
+        for _ in range(steps):
             upd += B.std_sgd_epoch(ctx, w.lr, w.lr, w.lam, w.lam, w.minibatch)["update_seconds"]
         e1.record(stream)
         torch.cuda.synchronize()
-        ms = e0.elapsed_time(e1) / a.steps
+        ms = e0.elapsed_time(e1) / steps
         rm = B.std_rmse(ctx, tc.shape[0], dtc, dtv)
         B.std_destroy(ctx)
         nb = (c.shape[0] + w.minibatch - 1) // w.minibatch
         res[prec] = {"value": c.shape[0] / (ms * 1e-3), "ms_per_epoch": ms,
-                     "us_per_minibatch": 1e6 * upd / a.steps / nb, "test_rmse": rm[0]}
+                     "us_per_minibatch": 1e6 * upd / steps / nb, "test_rmse": rm[0]}
     line = {"metric": "4-order workload: sampled nonzeros/s per epoch, FP32 and BF16", "workload": w.name,
             "nnz_train": int(c.shape[0]), "minibatch": w.minibatch, "ranks": list(w.ranks), "r_core": w.r_core,
-            "epochs": a.warmup + a.steps, "value": res[0]["value"], "unit": "nnz/s", "fp32": res[0], "bf16": res[1],
+            "epochs": warmup + steps, "value": res[0]["value"], "unit": "nnz/s", "fp32": res[0], "bf16": res[1],
             "bf16_speedup": res[1]["value"] / res[0]["value"],
             "bf16_test_rmse_gap": abs(res[1]["test_rmse"] - res[0]["test_rmse"]), "datagen_s": round(gen_s, 1),
             "data": "synthetic"}
-    print(json.dumps(line), flush=True)
-    return 0
+    return line
 
 
 def run_batched(a):
+    print(json.dumps(batched_record(a, a.scale, a.warmup, a.steps)), flush=True)
+    return 0
+
+
+def batched_record(a, nnz_scale, warmup, steps):
     """Epochs of 256 independent decompositions in one launch per epoch, FP32 and
     BF16, against the same tensors run one after another on the whole GPU."""
     import numpy as np
@@ -634,7 +774,7 @@ def run_batched(a):
     from paper_2012_03550_gb300 import synth
 
     t0 = time.time()
-    specs = synth.config4_specs(nnz_scale=a.scale)
+    specs = synth.config4_specs(nnz_scale=nnz_scale)
     tensors = [synth.config4_tensor(sp) for sp in specs]
     gen_s = time.time() - t0
     dev = torch.device("cuda", 0)
@@ -661,11 +801,11 @@ def run_batched(a):
     for precision in (0, 1):
         ctxs = contexts(precision)
         bt = B.std_batch_create(ctxs, 0)
-        for _ in range(a.warmup):
+        for _ in range(warmup):
             st = B.std_batch_epoch(bt, lr, lr, lam, lam, M)
         torch.cuda.synchronize()
         secs = []
-        for _ in range(a.steps):
+        for _ in range(steps):
             st = B.std_batch_epoch(bt, lr, lr, lam, lam, M)
             secs.append(st["seconds"])
         sizes = B.std_batch_groups(bt, len(ctxs))
@@ -701,7 +841,7 @@ def run_batched(a):
                             "tensors_by_group_size": hist, "graph_replayed": st["graph_replayed"],
                             "test_rmse": (se / cnt) ** 0.5 if cnt else None, "sequential_value": seq}
     line = {"metric": "batched SGD_Tucker: sampled nonzeros/s per epoch over all tensors", "value": lines[0]["value"],
-            "unit": "nnz/s", "n_gpus": 1, "steps": a.steps, "warmup": a.warmup,
+            "unit": "nnz/s", "n_gpus": 1, "steps": steps, "warmup": warmup,
             "ms_per_step": lines[0]["ms_per_epoch"], "higher_is_better": True, "dtype": "f32", "data": "synthetic",
             "config": {"workload": f"batched-{len(specs)}-tensors-{n_train}", "tensors": len(specs),
                        "nnz_train": n_train, "minibatch": M, "ranks": "J in {4, 8, 16}, R = min(5, J)",
@@ -715,11 +855,15 @@ def run_batched(a):
             "bf16": {"value": lines[1]["value"], "ms_per_step": lines[1]["ms_per_epoch"],
                      "ctas_per_tensor": lines[1]["ctas_per_tensor"], "test_rmse": lines[1]["test_rmse"],
                      "speedup_vs_fp32": lines[1]["value"] / lines[0]["value"]}}
-    print(json.dumps(line), flush=True)
-    return 0
+    return line
 
 
 def run_serve(a):
+    print(json.dumps(serve_record(a, a.serve_seconds)), flush=True)
+    return 0
+
+
+def serve_record(a, seconds):
     """Open-loop serving run: Poisson job arrivals and query batches against the
     continuous-batching server for a fixed wall time, then a drain."""
     import numpy as np
@@ -745,10 +889,10 @@ def run_serve(a):
     srv = serve.Server(eng, budget_bytes=int(a.serve_budget_gb * 1e9), batches_per_tick=a.serve_batches,
                        ctas_per_tensor=by_size if a.serve_ctas < 0 else a.serve_ctas)
     # arrival times (s from the start): jobs and query batches, both Poisson
-    jobs_t = np.cumsum(rng.exponential(1.0 / a.serve_rate, size=int(a.serve_rate * a.serve_seconds * 2) + 16))
-    jobs_t = jobs_t[jobs_t < a.serve_seconds]
-    q_t = np.cumsum(rng.exponential(1.0 / a.serve_qrate, size=int(a.serve_qrate * a.serve_seconds * 2) + 16))
-    q_t = q_t[q_t < a.serve_seconds]
+    jobs_t = np.cumsum(rng.exponential(1.0 / a.serve_rate, size=int(a.serve_rate * seconds * 2) + 16))
+    jobs_t = jobs_t[jobs_t < seconds]
+    q_t = np.cumsum(rng.exponential(1.0 / a.serve_qrate, size=int(a.serve_qrate * seconds * 2) + 16))
+    q_t = q_t[q_t < seconds]
     tables = {}
 
     def query_coords(shape):
@@ -767,7 +911,7 @@ def run_serve(a):
     try:
         while True:
             now = clk() - start
-            if now >= a.serve_seconds:
+            if now >= seconds:
                 break
             while ij < len(jobs_t) and jobs_t[ij] <= now:
                 sp, c, v = pool[ij % len(pool)]
@@ -783,8 +927,8 @@ def run_serve(a):
                     srv.query(j.id, query_coords(j.shape), now=start + float(q_t[iq]))
                 iq += 1
             if srv.idle():
-                nxt = min(jobs_t[ij] if ij < len(jobs_t) else a.serve_seconds,
-                          q_t[iq] if iq < len(q_t) else a.serve_seconds)
+                nxt = min(jobs_t[ij] if ij < len(jobs_t) else seconds,
+                          q_t[iq] if iq < len(q_t) else seconds)
                 time.sleep(max(0.0, min(0.01, nxt - (clk() - start))))
                 continue
             srv.tick()
@@ -799,7 +943,7 @@ def run_serve(a):
     line = {"metric": "serve p99 job-epoch latency", "value": r["job_epoch_p99_s"], "unit": "s",
             "higher_is_better": False, "n_gpus": 1, "dtype": "bf16-storage/f32" if not a.serve_fp32 else "f32",
             "data": "synthetic",
-            "config": {"workload": f"serve-{a.serve_rate:g}jobs_s-{a.serve_seconds:g}s",
+            "config": {"workload": f"serve-{a.serve_rate:g}jobs_s-{seconds:g}s",
                        "arrivals": f"Poisson {a.serve_rate:g} jobs/s, {a.serve_qrate:g} query batches/s "
                                    f"(1-4096 Zipf(1.1) coordinates, log-uniform size)",
                        "jobs": f"orders 3-4, J in {{4,8,16}} (order 4: {{4,8}}), nnz lognormal [1e4, 2e6], "
@@ -818,8 +962,7 @@ def run_serve(a):
             "jobs_submitted": r["jobs_submitted"], "jobs_done": r["jobs_done"],
             "jobs_rejected": r["jobs_rejected"], "queries_answered": r["queries_answered"],
             "ticks": r["ticks"]}
-    print(json.dumps(line), flush=True)
-    return 0
+    return line
 
 
 def main():

@@ -87,6 +87,17 @@ typedef struct {
                              regularised gradient; 0 = plain SGD (default).  The accelerated SGD
                              the paper names as future work (Sec. 6).  Velocities start at zero,
                              are kept per parameter on the device, and std_set_params resets them */
+    int32_t  snapshot;    /* K-snapshot form, a labelled variant of Algorithm 1's minibatch order
+                             (the paper has no counterpart; it amortises the chain of dependent
+                             phases of Algorithm 1 over K minibatches): 0 or 1 = Algorithm 1's
+                             order (default); K >= 2 = the minibatches of a call are taken in blocks
+                             of K consecutive ones (the first block starting at the call's first
+                             minibatch), every minibatch of a block runs Algorithm 1's step from the
+                             model as it stood when the block began, and their changes
+                             (w <- w + delta, delta = -lr * gradient) are added to that model in
+                             minibatch order.  K groups of CTAs run a block's minibatches at once.
+                             Limits: K <= 64, K * ceil(M / 256) CTAs resident, momentum 0
+                             (STD_EINVAL otherwise); batched launches refuse such contexts */
 } std_options;
 
 /* Fill *opt with the defaults listed above. */

@@ -55,6 +55,7 @@ class std_options(ctypes.Structure):
         ("hbm_budget_bytes", ctypes.c_uint64),
         ("contraction", ctypes.c_int32),
         ("momentum", ctypes.c_float),
+        ("snapshot", ctypes.c_int32),
     ]
 
 

@@ -73,6 +73,15 @@ struct std_ctx {
   unsigned long long* mail = nullptr;
   size_t mail_words = 0;
   uint32_t tag_base = 1;
+  // K-snapshot form: recorded changes and the per-CTA lists of rows to apply
+  float* snap_dB = nullptr;
+  size_t snap_dB_floats = 0;
+  float* snap_drow = nullptr;
+  size_t snap_drow_floats = 0;
+  int2* snap_list = nullptr;
+  size_t snap_list_items = 0;
+  int* snap_count = nullptr;
+  size_t snap_count_items = 0;
   // probe
   float* probe_mem = nullptr;
   size_t probe_floats = 0;
@@ -237,7 +246,9 @@ int ensure_scratch(std_ctx* c, int G, int payload, int M) {
   int rc = ensure_words(c, &c->part, &c->part_words, (size_t)G * ps, "core partials");
   if (!rc) rc = ensure_words(c, &c->inbox, &c->inbox_words, (size_t)G * ps, "core reduction copies");
   if (!rc) rc = ensure_words(c, &c->piece, &c->piece_words, (size_t)G * NJ, "run pieces");
-  if (!rc) rc = ensure_words(c, &c->mail, &c->mail_words, (size_t)M * NJ, "row slots");
+  // row slots: a stride of Jmax rounded up to even keeps word pairs 16-byte aligned
+  const size_t NJ2 = (size_t)c->g.N * (c->g.Jmax + (c->g.Jmax & 1));
+  if (!rc) rc = ensure_words(c, &c->mail, &c->mail_words, (size_t)M * NJ2, "row slots");
   return rc;
 }
 
@@ -305,12 +316,101 @@ EpochArgs epoch_args(std_ctx* c, float lr_a, float lr_b, float lam_a, float lam_
   return a;
 }
 
+// CTAs per group of the K-snapshot form: K groups, each of the size the
+// library would give one minibatch on 1/K of the GPU, at least enough for the
+// kernel's chunk limit.
+int choose_snap_ctas(std_ctx* c, int M, int K, int* gk, int* chunk_max, size_t* smem) {
+  const int payload = payload_floats(c->g);
+  if (payload > kMaxCorePayload)
+    return set_error(STD_EUNSUPPORTED, "core reduction payload R*J + R(R-1)/2*J(J+1)/2 exceeds 8192 floats");
+  if (!epoch_gram_fits(c->g))
+    return set_error(STD_EUNSUPPORTED, "core reduction tiles exceed the epoch kernel's per-thread limit");
+  // a group may take up to 256 samples per CTA (the strict form stops at
+  // 128, where more CTAs always pay); shared memory is checked below
+  const int cap = 2 * epoch_chunk_cap(c->g);
+  const int need = (M + cap - 1) / cap;
+  int G = c->opt.ctas > 0 ? c->opt.ctas / K : std::min(c->sms / K, (M + 15) / 16);
+  if (G < need) G = need;
+  if (G < 1) G = 1;
+  if ((int64_t)G * K > kMaxEpochCtas || G * K > c->sms)
+    return set_error(STD_EUNSUPPORTED, "K-snapshot: K groups of ceil(M/256) CTAs exceed the GPU");
+  const int ch = (M + G - 1) / G;
+  const size_t sm = epoch_smem_bytes(c->g, ch, G, c->opt.precision);
+  if (sm > 227 * 1024) return set_error(STD_EUNSUPPORTED, "shape needs more shared memory than a CTA has");
+  STD_CUDA(epoch_snap_setup(c->opt.precision, sm), "snapshot kernel attributes");
+  if (epoch_snap_max_ctas(c->opt.precision, sm) < G * K)
+    return set_error(STD_EUNSUPPORTED, "K-snapshot: the groups cannot all be resident");
+  *gk = G;
+  *chunk_max = ch;
+  *smem = sm;
+  return STD_OK;
+}
+
+template <typename T>
+int ensure_items(std_ctx* c, T** p, size_t* have, size_t items, const char* what) {
+  if (items <= *have) return STD_OK;
+  dev_free(c, *p, *have * sizeof(T));
+  *p = nullptr;
+  *have = 0;
+  int rc = dev_alloc(c, (void**)p, items * sizeof(T), what);
+  if (rc) return rc;
+  *have = items;
+  return STD_OK;
+}
+
+// Minibatches [b0, b1) in the K-snapshot form (std_options.snapshot = K).
+int run_snapshot(std_ctx* c, float lr_a, float lr_b, float lam_a, float lam_b, int32_t M, int64_t b0, int64_t b1,
+                 bool probe, bool record_end) {
+  const int K = c->opt.snapshot;
+  int Gk = 0, chunk = 0;
+  size_t smem = 0;
+  int rc = choose_snap_ctas(c, M, K, &Gk, &chunk, &smem);
+  if (rc) return rc;
+  const int G = Gk * K;
+  const int N = c->g.N;
+  int sumJR = 0;
+  for (int n = 0; n < N; ++n) sumJR += c->g.J[n] * c->g.R;
+  rc = ensure_scratch(c, G, payload_floats(c->g), M * K);
+  if (!rc) rc = ensure_items(c, &c->snap_dB, &c->snap_dB_floats, (size_t)K * sumJR, "snapshot column changes");
+  if (!rc)
+    rc = ensure_items(c, &c->snap_drow, &c->snap_drow_floats, (size_t)K * N * M * c->g.Jmax, "snapshot row changes");
+  if (!rc) rc = ensure_items(c, &c->snap_list, &c->snap_list_items, (size_t)G * K * N * M, "snapshot row lists");
+  if (!rc) rc = ensure_items(c, &c->snap_count, &c->snap_count_items, (size_t)G * K, "snapshot list counts");
+  if (rc) return rc;
+  uint32_t tag_base = 0;
+  rc = reserve_tags(c, b1 - b0, &tag_base);
+  if (rc) return rc;
+  EpochArgs a = epoch_args(c, lr_a, lr_b, lam_a, lam_b, b0, b1, chunk, tag_base);
+  if (probe) {
+    const size_t need = (size_t)N * c->g.R * kMaxJ + (size_t)N * M * kMaxJ;
+    rc = ensure_items(c, &c->probe_mem, &c->probe_floats, need, "gradient probe");
+    if (rc) return rc;
+    STD_CUDA(cudaMemsetAsync(c->probe_mem, 0, need * 4, c->stream), "probe clear");
+    a.probe_batch = b0;
+    a.probeV = c->probe_mem;
+    a.probeF = c->probe_mem + (size_t)N * c->g.R * kMaxJ;
+  }
+  a.snap_k = K;
+  a.snap_gk = Gk;
+  a.snap_dB = c->snap_dB;
+  a.snap_drow = c->snap_drow;
+  a.snap_list = c->snap_list;
+  a.snap_count = c->snap_count;
+  STD_CUDA(cudaMemsetAsync(c->snap_count, 0, (size_t)G * K * sizeof(int), c->stream), "snapshot counts");
+  STD_CUDA(cudaMemsetAsync(c->bar, 0, sizeof(unsigned long long), c->stream), "barrier clear");
+  if (record_end) STD_CUDA(cudaEventRecord(c->evm, c->stream), "event");
+  if (b1 > b0) STD_CUDA(launch_epoch_snap(a, G, smem, c->stream), "snapshot kernel launch");
+  if (record_end) STD_CUDA(cudaEventRecord(c->ev1, c->stream), "event");
+  return read_err(c, "snapshot kernel");
+}
+
 // Runs minibatches [b0, b1) of the current schedule.  With record_end, ev1
 // is recorded on the stream right after the kernel (the caller records ev0).
 int run_batches(std_ctx* c, float lr_a, float lr_b, float lam_a, float lam_b, int32_t M, int64_t b0, int64_t b1,
                 bool probe, bool record_end) {
   int rc = ensure_schedule(c, M);
   if (rc) return rc;
+  if (c->opt.snapshot >= 2) return run_snapshot(c, lr_a, lr_b, lam_a, lam_b, M, b0, b1, probe, record_end);
   int G = 0, chunk = 0;
   size_t smem = 0;
   rc = choose_ctas(c, M, &G, &chunk, &smem);
@@ -393,6 +493,7 @@ void std_default_options(std_options* opt) {
   opt->hbm_budget_bytes = 0;
   opt->contraction = 0;
   opt->momentum = 0.f;
+  opt->snapshot = 0;
 }
 
 const char* std_last_error(void) { return g_last_error.c_str(); }
@@ -407,7 +508,8 @@ int std_destroy(std_ctx* c) {
   }
   if (c->vB) cudaFree(c->vB);
   void* ptrs[] = {c->coo, c->B, c->core, c->err, c->bar, c->sched_mem, c->part, c->inbox,
-                  c->piece, c->mail, c->probe_mem, c->stage, c->rpart, c->result};
+                  c->piece, c->mail, c->probe_mem, c->stage, c->rpart, c->result,
+                  c->snap_dB, c->snap_drow, c->snap_list, c->snap_count};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (c->ev0) cudaEventDestroy(c->ev0);
@@ -437,6 +539,10 @@ int std_create(std_ctx** out, int32_t order, const int64_t* mode_sizes, const in
   if (opt.ctas < 0) return set_error(STD_EINVAL, "ctas must be >= 0");
   if (opt.contraction != 0 && opt.contraction != 1) return set_error(STD_EINVAL, "contraction must be 0 or 1");
   if (!(opt.momentum >= 0.f && opt.momentum < 1.f)) return set_error(STD_EINVAL, "momentum must be in [0, 1)");
+  if (opt.snapshot < 0) return set_error(STD_EINVAL, "snapshot must be >= 0");
+  if (opt.snapshot > 64) return set_error(STD_EUNSUPPORTED, "snapshot exceeds 64 minibatches per block");
+  if (opt.snapshot >= 2 && opt.momentum != 0.f)
+    return set_error(STD_EINVAL, "the K-snapshot form is defined without momentum");
   Geometry g{};
   g.N = order;
   g.R = opt.r_core;
@@ -1197,6 +1303,8 @@ int std_batch_create(std_batch** out, int32_t count, std_ctx* const* ctxs, int32
       return set_error(STD_EINVAL, "every context of a batch must use the same precision");
     if (ctxs[t]->stream != ctxs[0]->stream)
       return set_error(STD_EINVAL, "every context of a batch must use the same stream");
+    if (ctxs[t]->opt.snapshot >= 2)
+      return set_error(STD_EINVAL, "batched launches run Algorithm 1's order (snapshot 0 or 1)");
     for (int u = 0; u < t; ++u)
       if (ctxs[u] == ctxs[t]) return set_error(STD_EINVAL, "a context appears twice in the batch");
   }
@@ -1327,6 +1435,8 @@ int std_batch_reset(std_batch* bt, int32_t count, std_ctx* const* ctxs) {
     if (ctxs[t]->opt.precision != bt->precision)
       return set_error(STD_EINVAL, "every context of a batch must use the batch's precision");
     if (ctxs[t]->stream != bt->stream) return set_error(STD_EINVAL, "every context of a batch must use its stream");
+    if (ctxs[t]->opt.snapshot >= 2)
+      return set_error(STD_EINVAL, "batched launches run Algorithm 1's order (snapshot 0 or 1)");
     for (int u = 0; u < t; ++u)
       if (ctxs[u] == ctxs[t]) return set_error(STD_EINVAL, "a context appears twice in the batch");
   }

@@ -65,6 +65,8 @@ namespace {
 constexpr int kRightBudget = 16384;  // floats of precomputed right Gram operands (all modes)
 constexpr int kSBudget = 32768;      // floats of Kronecker rows materialised at once (FP32 form)
 constexpr int kMaxSmemBytes = 227 * 1024;
+constexpr int kDigitTable = 4096;    // core entries whose packed digits are tabulated in shared memory
+constexpr int kVecItems = kMaxN * (kMaxJ / 2);   // 16-byte loads per sample of one row gather, at most
 
 __host__ __device__ inline int pad4(int x) { return (x + 3) & ~3; }
 
@@ -141,9 +143,9 @@ __host__ __device__ inline int fp32_row_stride(int Pn) {
 }
 
 struct SmemLayout {
-  int B, VB, G, GT, GTh, Sh, S, ldig, cdig, rowtab, trij, sc[2], rows, master, p, left, right, red, D, q, head, fown,
-      pbuf, total_words;
-  int lw, rw, sfloats, rpre;
+  int B, VB, Bs, G, GT, GTh, Sh, S, ldig, cdig, vtab, trij, sc[2], rows, master, p, left, right, red, D, q,
+      head, fown, pbuf, total_words;
+  int lw, rw, sfloats, rpre, ldig_on;
 };
 
 // Words of one phase's schedule chunk: coordinates [s][N], value, run
@@ -176,16 +178,26 @@ __host__ __device__ inline SmemLayout smem_layout_v(const Geometry& g, int chunk
   const int spmax = fp32_row_stride(Pmax);
   L.sfloats = (bf || v == 2) ? 0 : (chunk * spmax < kSBudget ? chunk * spmax : kSBudget);
   const int kpmax = bf16_row_stride(Pmax);
+  // the unfolded core of one mode at a time: J_n rows of P_n (padded) columns
+  int gt32 = 0, gt16 = 0;
+  for (int n = 0; n < g.N; ++n) {
+    const int pn = g.prodJ / g.J[n];
+    const int f = g.J[n] * fp32_row_stride(pn), h = round_up(g.J[n], 8) * bf16_row_stride(pn) / 2;
+    gt32 = f > gt32 ? f : gt32;
+    gt16 = h > gt16 ? h : gt16;
+  }
+  L.ldig_on = g.prodJ <= kDigitTable ? 1 : 0;
   L.B = take(sumJR);
   L.VB = take(sumJR);
+  L.Bs = take(sumJR);
   L.G = take(g.prodJ);
-  L.GT = take(bf ? 0 : g.Jmax * spmax);
-  L.GTh = take(bf ? round_up(g.Jmax, 16) * kpmax / 2 : 0);
+  L.GT = take(bf ? 0 : gt32);
+  L.GTh = take(bf ? gt16 : 0);
   L.Sh = take(bf ? round_up(chunk, 16) * kpmax / 2 : 0);
   L.S = take(L.sfloats);
-  L.ldig = take(g.prodJ);
+  L.ldig = take(L.ldig_on ? g.prodJ : 0);
   L.cdig = take(2 * sum_pn(g));
-  L.rowtab = take(g.sumJ);
+  L.vtab = take(g.N * kVecItems);
   L.trij = take(tri(g.Jmax));
   L.sc[0] = take(sched_chunk_words(g.N, chunk));
   L.sc[1] = take(sched_chunk_words(g.N, chunk));
@@ -280,6 +292,16 @@ __device__ __forceinline__ ulonglong2 get_pair(const unsigned long long* p) {
 }
 
 __device__ __forceinline__ uint32_t tag_of(unsigned long long w) { return (uint32_t)(w >> 32); }
+
+// 16 bytes from global memory through L2 only (the factor rows change every
+// minibatch, so L1 copies would go stale).
+__device__ __forceinline__ uint4 ldcg_v4(const void* p) {
+  uint4 v;
+  asm volatile("ld.global.cg.v4.u32 {%0, %1, %2, %3}, [%4];"
+               : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+               : "l"(p));
+  return v;
+}
 __device__ __forceinline__ float val_of(unsigned long long w) { return __uint_as_float((uint32_t)w); }
 
 // Re-reads *p until it carries `tag` (short back-off after the first rounds,
@@ -361,6 +383,35 @@ __device__ __forceinline__ bool wait_pairs(const unsigned long long* const (&p)[
 #pragma unroll
     for (int u = 0; u < K; ++u)
       if (p[u] && (tag_of(w[u].x) != tag || tag_of(w[u].y) != tag)) {
+        done = false;
+        w[u] = get_pair(p[u]);
+      }
+    if (done) return true;
+    if (t0 == 0) t0 = globaltimer_ns();
+    if (++spins > 4) __nanosleep(32);
+    if ((spins & 15u) == 0u) {
+      if (ld_volatile_int(a.err) != 0) return false;
+      if (globaltimer_ns() - t0 > a.watchdog_ns) {
+        atomicCAS(a.err, 0, STD_ETIMEOUT);
+        return false;
+      }
+    }
+  }
+}
+
+// wait_pairs with a tag per pair; two[u] false: only the first word of pair u
+// is live (the second is row padding nobody writes).
+template <int K>
+__device__ __forceinline__ bool wait_pairs_tagged(const unsigned long long* const (&p)[K], ulonglong2 (&w)[K],
+                                                  const uint32_t (&tg)[K], const bool (&two)[K], const EpochArgs& a) {
+  unsigned long long t0 = 0;
+  unsigned spins = 0;
+#pragma unroll 1
+  while (true) {
+    bool done = true;
+#pragma unroll
+    for (int u = 0; u < K; ++u)
+      if (p[u] && (tag_of(w[u].x) != tg[u] || (two[u] && tag_of(w[u].y) != tg[u]))) {
         done = false;
         w[u] = get_pair(p[u]);
       }
@@ -596,14 +647,16 @@ __device__ __forceinline__ void right_row(float* dst, const float* an, int Jn, i
 
 }  // namespace
 
-// The epoch of one tensor on the G CTAs c = 0..G-1 that own it.
-template <bool BF>
+// The epoch of one tensor on the G CTAs c = 0..G-1 that own it.  SNAP: the
+// K-snapshot form, G CTAs per group and a.snap_k groups (see k_epoch_snap).
+template <bool BF, bool SNAP>
 __device__ __forceinline__ void epoch_body(const EpochArgs& a, const int G, const int c) {
   extern __shared__ __align__(16) float sm[];
   // per-mode constants, indexed by the (runtime) mode
   __shared__ int mJ[kMaxN], mJoff[kMaxN], mBoff[kMaxN], mJp[kMaxN], mJb[kMaxN], mPn[kMaxN], mToff[kMaxN],
       mGs[kMaxN], mRoff[kMaxN];
-  __shared__ FastDiv mFna4[kMaxN], mFnq4[kMaxN], mFtJ[kMaxN], mFJ[kMaxN], mFper[kMaxN];
+  __shared__ FastDiv mFna4[kMaxN], mFnq4[kMaxN], mFtJ[kMaxN], mFJ[kMaxN], mFper[kMaxN], mFv[kMaxN];
+  __shared__ int mVc[kMaxN];
   __shared__ float* mA[kMaxN];
   __shared__ float* mvA[kMaxN];
   __shared__ unsigned short* mAb[kMaxN];
@@ -613,6 +666,7 @@ __device__ __forceinline__ void epoch_body(const EpochArgs& a, const int G, cons
   const SmemLayout L = smem_layout(a.g, chunk_max, G, BF ? 1 : 0);
   float* Bsm = sm + L.B;
   float* VBsm = sm + L.VB;   // Kruskal-column velocities (momentum)
+  float* Bsnap = sm + L.Bs;  // K-snapshot form: B at the start of the block (then the combined B)
   float* Gsm = sm + L.G;
   float* GT = sm + L.GT;
   __nv_bfloat16* GTh = reinterpret_cast<__nv_bfloat16*>(sm + L.GTh);
@@ -620,7 +674,7 @@ __device__ __forceinline__ void epoch_body(const EpochArgs& a, const int G, cons
   float* Sbuf = sm + L.S;
   uint32_t* ldig = reinterpret_cast<uint32_t*>(sm + L.ldig);
   unsigned long long* cdig = reinterpret_cast<unsigned long long*>(sm + L.cdig);
-  int* rowtab = reinterpret_cast<int*>(sm + L.rowtab);
+  int* vtab = reinterpret_cast<int*>(sm + L.vtab);
   int* trij = reinterpret_cast<int*>(sm + L.trij);
   int* scb[2] = {reinterpret_cast<int*>(sm + L.sc[0]), reinterpret_cast<int*>(sm + L.sc[1])};
   float* rows = sm + L.rows;
@@ -672,8 +726,23 @@ __device__ __forceinline__ void epoch_body(const EpochArgs& a, const int G, cons
       mFper[k] = make_fastdiv((uint32_t)(N + 2 + k));
     }
   }
+  // 16-byte loads per sample of the row gathers.  Phase 0 (core phase and
+  // factor mode 1): every mode's row from A, 4 FP32 (or 8 BF16) entries per
+  // load.  Phase p = 1..N-1 (factor mode p+1): rows of modes k < p from this
+  // minibatch's row slots as tagged word pairs, the others from A.  Entry:
+  // k | pair << 7 | j0 << 8.
+  if (tid < N) {
+    const int ph = tid;
+    int cntv = 0;
+    for (int k = 0; k < N; ++k) {
+      const bool pr = ph > 0 && k < ph;
+      const int step = pr ? 2 : (BF ? 8 : 4);
+      for (int j0 = 0; j0 < a.g.J[k]; j0 += step) vtab[ph * kVecItems + cntv++] = k | (pr ? 128 : 0) | (j0 << 8);
+    }
+    mVc[ph] = cntv;
+    mFv[ph] = make_fastdiv((uint32_t)cntv);
+  }
   __syncthreads();
-  const FastDiv f_sumJ = make_fastdiv((uint32_t)sumJ);
   const FastDiv f_R = make_fastdiv((uint32_t)R);
   const FastDiv f_NR = make_fastdiv((uint32_t)(N * R));
   int sumJR = 0;
@@ -682,17 +751,32 @@ __device__ __forceinline__ void epoch_body(const EpochArgs& a, const int G, cons
   for (int i = tid; i < sumJR; i += T) {
     Bsm[i] = __ldcg(a.B + i);
     VBsm[i] = a.momentum != 0.f ? __ldcg(a.vB + i) : 0.f;
+    if (SNAP) Bsnap[i] = Bsm[i];
   }
-#pragma unroll 1
-  for (int lin = tid; lin < prodJ; lin += T) {
-    int t = lin;
+  // packed digits (5 bits per mode, mode 1 lowest) of core entry lin, from
+  // the table when it fits in shared memory
+  auto core_digits = [&](int lin) -> uint32_t {
+    if (L.ldig_on) return ldig[lin];
     uint32_t packed = 0;
+    int t = lin;
     for (int k = 0; k < N; ++k) {
-      packed |= (uint32_t)(t % mJ[k]) << (5 * k);
-      t /= mJ[k];
+      const int q = fdiv(t, mFJ[k]);
+      packed |= (uint32_t)(t - q * mJ[k]) << (5 * k);
+      t = q;
     }
-    ldig[lin] = packed;
-  }
+    return packed;
+  };
+  if (L.ldig_on)
+#pragma unroll 1
+    for (int lin = tid; lin < prodJ; lin += T) {
+      int t = lin;
+      uint32_t packed = 0;
+      for (int k = 0; k < N; ++k) {
+        packed |= (uint32_t)(t % mJ[k]) << (5 * k);
+        t /= mJ[k];
+      }
+      ldig[lin] = packed;
+    }
 #pragma unroll 1
   for (int n = 0; n < N; ++n) {
 #pragma unroll 1
@@ -710,24 +794,71 @@ __device__ __forceinline__ void epoch_body(const EpochArgs& a, const int G, cons
     }
   }
 #pragma unroll 1
-  for (int jj = tid; jj < sumJ; jj += T) {
-    int k = 0, j = jj;
-    while (j >= mJ[k]) { j -= mJ[k]; ++k; }
-    rowtab[jj] = k | (j << 8);
-  }
-#pragma unroll 1
   for (int q = tid; q < tri(Jmax); q += T) {
     int jb = 0;
     while (tri(jb + 1) <= q) ++jb;
     trij[q] = (q - tri(jb)) | (jb << 8);   // packed upper-triangle index q = jb (jb + 1) / 2 + ja
   }
   int buf = 0;
-  if (a.b0 < a.b1) prefetch_schedule(a, N, a.b0, 0, scb[0], chunk_max, mFper[0], G, c);
+  // minibatches b0 + it * stride + first, it = 0 .. iters-1 (the K-snapshot
+  // form: group q takes minibatch q of every block of K)
+  const int stride = SNAP ? a.snap_k : 1;
+  const int64_t first = SNAP ? a.snap_grp : 0;
+  const int64_t iters = (a.b1 - a.b0 + stride - 1) / stride;
+  const int Gtot = SNAP ? a.snap_k * G : G;
+  if (a.b0 + first < a.b1) prefetch_schedule(a, N, a.b0 + first, 0, scb[0], chunk_max, mFper[0], G, c);
   cp_async_commit();
   __syncthreads();
 
+  // K-snapshot block boundary after block `blk`: every group has finished its
+  // minibatch; the Kruskal-column changes are added to the block's B and the
+  // factor-row changes to A, in minibatch order, and every CTA continues from
+  // the combined model
+  auto snap_boundary = [&](int64_t blk) -> bool {
+    if (!grid_barrier(a, generation, Gtot)) return false;
+    const int64_t bs = a.b0 + blk * stride;
+    const int kq = (int)((a.b1 - bs) < (int64_t)stride ? (a.b1 - bs) : (int64_t)stride);
 #pragma unroll 1
-  for (int64_t b = a.b0; b < a.b1; ++b) {
+    for (int i = tid; i < sumJR; i += T) {
+      float v = Bsnap[i];
+      if (a.lr_b != 0.f)
+#pragma unroll 1
+        for (int k = 0; k < kq; ++k) v = __fadd_rn(v, __ldcg(a.snap_dB + (size_t)k * sumJR + i));
+      Bsnap[i] = v;
+      Bsm[i] = v;
+    }
+    // the rows this CTA owns, minibatch after minibatch (a row's changes
+    // from different minibatches are added in order)
+#pragma unroll 1
+    for (int k = 0; k < kq; ++k) {
+      const int cnt_k = __ldcg(a.snap_count + a.snap_cta * stride + k);
+      const int2* lst = a.snap_list + ((size_t)a.snap_cta * stride + k) * (size_t)(N * M);
+#pragma unroll 1
+      for (int e = warp; e < cnt_k; e += nwarps) {
+        const int2 en = __ldcg(lst + e);
+        const int n = en.y >> 16, st = en.y & 0xffff;
+        const unsigned row = (unsigned)en.x;
+        if (lane < mJ[n]) {
+          const float d = __ldcg(a.snap_drow + (((size_t)k * N + n) * M + st) * Jmax + lane);
+          float* ap = mA[n] + row * (unsigned)mJp[n] + lane;
+          const float nv = __fadd_rn(__ldcg(ap), d);
+          __stcg(ap, nv);
+          if (BF) __stcg(mAb[n] + row * (unsigned)mJb[n] + lane, __bfloat16_as_ushort(__float2bfloat16_rn(nv)));
+        }
+      }
+      __syncthreads();
+    }
+    if (tid < stride) a.snap_count[a.snap_cta * stride + tid] = 0;
+    return grid_barrier(a, generation, Gtot);
+  };
+
+#pragma unroll 1
+  for (int64_t it = 0; it < iters; ++it) {
+    const int64_t b = a.b0 + it * stride + first;
+    if (SNAP) {
+      if (it > 0 && !snap_boundary(it - 1)) return;
+      if (b >= a.b1) continue;   // a group without a minibatch in the last block
+    }
     const Phase ph = phase_of(a, b, G, c);
     const int cnt = ph.cnt, lo = ph.lo, hi = ph.hi;
     const bool probe = (b == a.probe_batch);
@@ -736,7 +867,7 @@ __device__ __forceinline__ void epoch_body(const EpochArgs& a, const int G, cons
     const uint32_t tag0 = a.tag_base + (uint32_t)((b - a.b0) * 8);
 
     // every row update of the previous minibatch is visible after this
-    if (b > a.b0 && !grid_barrier(a, generation, G)) return;
+    if (!SNAP && b > a.b0 && !grid_barrier(a, generation, G)) return;
     cp_async_wait_all();
     __syncthreads();
     // factor mode 2's chunk arrives while the core phase runs
@@ -749,29 +880,46 @@ __device__ __forceinline__ void epoch_body(const EpochArgs& a, const int G, cons
     // ------------------------------------------------------------------
     const int* crd = scb[buf];
     const float* xs = reinterpret_cast<const float*>(scb[buf] + N * chunk_max);
+    {
+      // every sample's N rows with 16-byte loads, four in flight per thread
+      const int nv = mVc[0], tot = cnt * nv;
+      const FastDiv fv = mFv[0];
 #pragma unroll 1
-    for (int i0 = tid; i0 < cnt * sumJ; i0 += 2 * T) {
-      float v[2];
+      for (int i0 = tid; i0 < tot; i0 += 4 * T) {
+        uint4 x[4];
+        int dst[4], e[4];
 #pragma unroll
-      for (int u = 0; u < 2; ++u) {
-        const int i = i0 + u * T;
-        v[u] = 0.f;
-        if (i < cnt * sumJ) {
-          const int s = fdiv(i, f_sumJ), jj = i - s * sumJ;
-          const int k = rowtab[jj] & 0xff, j = rowtab[jj] >> 8;
-          const unsigned row = (unsigned)crd[s * N + k];
-          if (BF) v[u] = __uint_as_float((uint32_t)__ldcg(mAb[k] + row * (unsigned)mJb[k] + j) << 16);
-          else v[u] = __ldcg(mA[k] + row * (unsigned)mJp[k] + j);
+        for (int u = 0; u < 4; ++u) {
+          const int i = i0 + u * T;
+          e[u] = -1;
+          if (i < tot) {
+            const int s = fdiv(i, fv);
+            e[u] = vtab[i - s * nv];
+            const int k = e[u] & 127, j0 = e[u] >> 8;
+            const unsigned row = (unsigned)crd[s * N + k];
+            dst[u] = s * sumJ + mJoff[k] + j0;
+            x[u] = BF ? ldcg_v4(mAb[k] + row * (unsigned)mJb[k] + j0) : ldcg_v4(mA[k] + row * (unsigned)mJp[k] + j0);
+          }
         }
-      }
 #pragma unroll
-      for (int u = 0; u < 2; ++u)
-        if (i0 + u * T < cnt * sumJ) rows[i0 + u * T] = v[u];
+        for (int u = 0; u < 4; ++u)
+          if (e[u] >= 0) {
+            const int left = mJ[e[u] & 127] - (e[u] >> 8);
+            float* d = rows + dst[u];
+            if (BF) {
+              const uint32_t q[4] = {x[u].x, x[u].y, x[u].z, x[u].w};
+#pragma unroll
+              for (int h = 0; h < 8; ++h)
+                if (h < left) d[h] = __uint_as_float((h & 1) ? (q[h >> 1] & 0xffff0000u) : (q[h >> 1] << 16));
+            } else {
+              const uint32_t q[4] = {x[u].x, x[u].y, x[u].z, x[u].w};
+#pragma unroll
+              for (int h = 0; h < 4; ++h)
+                if (h < left) d[h] = __uint_as_float(q[h]);
+            }
+          }
+      }
     }
-    if (BF)
-#pragma unroll 1
-      for (int s = warp; s < cnt; s += nwarps)
-        if (lane < mJ[0]) master[s * Jmax + lane] = __ldcg(mA[0] + (unsigned)crd[s * N] * (unsigned)mJp[0] + lane);
     __syncthreads();
     // lr_b = 0 leaves B unchanged: the core phase is skipped
     if (a.lr_b != 0.f) {
@@ -1034,7 +1182,15 @@ __device__ __forceinline__ void epoch_body(const EpochArgs& a, const int G, cons
                     step = a.momentum * *vb + gb;
                     *vb = step;
                   }
-                  const float bn = bo - a.lr_b * step;
+                  float bn;
+                  if (SNAP) {
+                    // the change is recorded for the block's end (w + delta form)
+                    const float dl = -__fmul_rn(a.lr_b, step);
+                    bn = __fadd_rn(bo, dl);
+                    if (c == 0) a.snap_dB[(size_t)a.snap_grp * sumJR + mBoff[n] + lane * R + r] = dl;
+                  } else {
+                    bn = bo - a.lr_b * step;
+                  }
                   d = bn - bo;
                   Bn[lane * R + r] = bn;
                   if (probe && c == 0 && a.probeV) a.probeV[((unsigned)n * R + r) * kMaxJ + lane] = V;
@@ -1092,7 +1248,7 @@ __device__ __forceinline__ void epoch_body(const EpochArgs& a, const int G, cons
     // ------------------------------------------------------------------
 #pragma unroll 1
     for (int lin = tid; lin < prodJ; lin += T) {
-      const uint32_t packed = ldig[lin];
+      const uint32_t packed = core_digits(lin);
       float acc = 0.f;
 #pragma unroll 1
       for (int r = 0; r < R; ++r) {
@@ -1121,7 +1277,7 @@ __device__ __forceinline__ void epoch_body(const EpochArgs& a, const int G, cons
         __syncthreads();
         buf ^= 1;
         // the next phase's chunk: mode n+1 of this minibatch, or mode 1 of the next
-        const int64_t nb = (n + 1 < N) ? b : b + 1;
+        const int64_t nb = (n + 1 < N) ? b : b + stride;
         const int nmode = (n + 1 < N) ? n + 1 : 0;
         if (nb < a.b1) prefetch_schedule(a, N, nb, nmode, scb[buf ^ 1], chunk_max, mFper[nmode], G, c);
         cp_async_commit();
@@ -1131,43 +1287,47 @@ __device__ __forceinline__ void epoch_body(const EpochArgs& a, const int G, cons
       const uint32_t* fseg = reinterpret_cast<const uint32_t*>(scb[buf] + (N + 1) * chunk_max);
       const int* fl = scb[buf] + (N + 2) * chunk_max;
       // rows: modes k < n as updated earlier in this minibatch (tagged slots,
-      // through the links), modes k >= n from A; G_(n) and the run heads are
-      // built while the first loads are in flight
-      const int total = n > 0 ? cnt * sumJ : 0;
-      unsigned long long w2[2];
-      const unsigned long long* p2[2];
-      uint32_t t2[2];
-      float v2[2];
+      // through the links, as 16-byte word pairs), modes k >= n from A
+      // (16-byte loads); G_(n) and the run heads are built while the first
+      // loads are in flight
+      const int nvf = n > 0 ? mVc[n] : 0;
+      const int total = cnt * nvf;
+      const FastDiv fvf = mFv[n];
+      const int* vt = vtab + n * kVecItems;
+      const unsigned mst = (unsigned)(Jmax + (Jmax & 1));   // row-slot stride: pairs stay 16-byte aligned
+      uint4 x4[4];
+      ulonglong2 w4[4];
+      const unsigned long long* p4[4];
+      uint32_t t4[4];
+      bool two4[4];
+      int e4[4], d4[4];
       int i0 = tid;
 #pragma unroll 1
-      for (bool first = true; i0 < total || first; i0 += 2 * T, first = false) {
+      for (bool first = true; i0 < total || first; i0 += 4 * T, first = false) {
 #pragma unroll
-        for (int u = 0; u < 2; ++u) {
+        for (int u = 0; u < 4; ++u) {
           const int i = i0 + u * T;
-          p2[u] = nullptr;
-          w2[u] = 0ULL;
-          t2[u] = 0u;
-          v2[u] = 0.f;
+          p4[u] = nullptr;
+          e4[u] = -1;
+          t4[u] = 0u;
+          two4[u] = false;
           if (i < total) {
-            const int s = fdiv(i, f_sumJ), jj = i - s * sumJ;
-            const int k = rowtab[jj] & 0xff, j = rowtab[jj] >> 8;
-            if (k < n) {
-              p2[u] = a.mail + ((unsigned)k * (unsigned)M + (unsigned)fl[s * N + k]) * (unsigned)Jmax + j;
-              w2[u] = get_word(p2[u]);
-              t2[u] = tag0 + (uint32_t)k;
+            const int s = fdiv(i, fvf);
+            e4[u] = vt[i - s * nvf];
+            const int k = e4[u] & 127, j0 = e4[u] >> 8;
+            d4[u] = s * sumJ + mJoff[k] + j0;
+            if (e4[u] & 128) {
+              p4[u] = a.mail + ((unsigned)k * (unsigned)M + (unsigned)fl[s * N + k]) * mst + j0;
+              w4[u] = get_pair(p4[u]);
+              t4[u] = tag0 + (uint32_t)k;
+              two4[u] = j0 + 1 < mJ[k];
             } else {
               const unsigned row = (unsigned)fcrd[s * N + k];
-              if (BF) v2[u] = __uint_as_float((uint32_t)__ldcg(mAb[k] + row * (unsigned)mJb[k] + j) << 16);
-              else v2[u] = __ldcg(mA[k] + row * (unsigned)mJp[k] + j);
+              x4[u] = BF ? ldcg_v4(mAb[k] + row * (unsigned)mJb[k] + j0) : ldcg_v4(mA[k] + row * (unsigned)mJp[k] + j0);
             }
           }
         }
         if (first) {
-          if (BF && n > 0)
-#pragma unroll 1
-            for (int s = warp; s < cnt; s += nwarps)
-              if (lane < Jn)
-                master[s * Jmax + lane] = __ldcg(mA[n] + (unsigned)fcrd[s * N + n] * (unsigned)mJp[n] + lane);
           // G_(n) for the contraction, [j][c]: warp per j, lanes over c;
           // column c sits at the offset of its other-mode digits in G-hat
           // (BF16: the rows and columns the tensor-core tiles read, J_n
@@ -1223,14 +1383,42 @@ __device__ __forceinline__ void epoch_body(const EpochArgs& a, const int G, cons
             }
           }
         }
-        if (ok) ok = wait_all<2>(p2, w2, t2, a);
+        if (ok) ok = wait_pairs_tagged<4>(p4, w4, t4, two4, a);
 #pragma unroll
-        for (int u = 0; u < 2; ++u) {
-          const int i = i0 + u * T;
-          if (i < total) rows[i] = p2[u] ? (BF ? bf16_round(val_of(w2[u])) : val_of(w2[u])) : v2[u];
-        }
+        for (int u = 0; u < 4; ++u)
+          if (e4[u] >= 0) {
+            float* d = rows + d4[u];
+            if (p4[u]) {
+              d[0] = BF ? bf16_round(val_of(w4[u].x)) : val_of(w4[u].x);
+              if (two4[u]) d[1] = BF ? bf16_round(val_of(w4[u].y)) : val_of(w4[u].y);
+            } else {
+              const int left = mJ[e4[u] & 127] - (e4[u] >> 8);
+              const uint32_t q[4] = {x4[u].x, x4[u].y, x4[u].z, x4[u].w};
+              if (BF) {
+#pragma unroll
+                for (int h = 0; h < 8; ++h)
+                  if (h < left) d[h] = __uint_as_float((h & 1) ? (q[h >> 1] & 0xffff0000u) : (q[h >> 1] << 16));
+              } else {
+#pragma unroll
+                for (int h = 0; h < 4; ++h)
+                  if (h < left) d[h] = __uint_as_float(q[h]);
+              }
+            }
+          }
       }
       if (!__syncthreads_and(ok)) return;
+      const int nheads = s_nheads;
+      // BF16 form: the FP32 master rows, fetched only for the runs this CTA
+      // updates (run heads that start in this chunk), while the contraction runs
+      if (BF) {
+#pragma unroll 1
+        for (int h = warp; h < nheads; h += nwarps) {
+          const int s0 = head[h];
+          if (lane < Jn && (int)(fseg[s0] & 0xffffu) >= lo)
+            cp_async4(master + h * Jmax + lane, mA[n] + (unsigned)fcrd[s0 * N + n] * (unsigned)mJp[n] + lane);
+        }
+        cp_async_commit();
+      }
       // Kronecker rows S_s (Eq. 10), warp per sample, lanes over columns
       const int nm1 = N - 1;
       const bool kru = a.contraction == 1;
@@ -1302,7 +1490,6 @@ __device__ __forceinline__ void epoch_body(const EpochArgs& a, const int G, cons
         }
       }
       __syncthreads();
-      const int nheads = s_nheads;
       if (kru) {
         // E_s and the contributions were formed above
       } else if (BF) {
@@ -1389,6 +1576,7 @@ __device__ __forceinline__ void epoch_body(const EpochArgs& a, const int G, cons
         const unsigned long long* p = a.piece + ((unsigned)n * G + (unsigned)(c + 1 + pc)) * (unsigned)Jmax + j;
         pieces_sm[i] = val_of(settle(p, get_word(p), tag, ok, a));
       }
+      if (BF) cp_async_wait_all();
       if (!__syncthreads_and(ok)) return;
       // the factor-row update of every run that starts in this chunk (pieces of
       // a continuing run added in chunk order), warp per run, lane j
@@ -1405,7 +1593,7 @@ __device__ __forceinline__ void epoch_body(const EpochArgs& a, const int G, cons
               for (int i = lane; i < npc; i += Jn) F += pieces_sm[i];
             const float denom = a.norm_mode == 1 ? (float)(en - st + 1) : fm;
             const unsigned row = (unsigned)fcrd[s0 * N + n];
-            const float av = BF ? master[s0 * Jmax + lane] : rows[s0 * sumJ + mJoff[n] + lane];
+            const float av = BF ? master[h * Jmax + lane] : rows[s0 * sumJ + mJoff[n] + lane];
             const float ga = F / denom + a.lam_a * av;
             float step = ga;
             if (a.momentum != 0.f) {
@@ -1413,20 +1601,37 @@ __device__ __forceinline__ void epoch_body(const EpochArgs& a, const int G, cons
               step = a.momentum * __ldcg(vp) + ga;
               if (!a.dry) __stcg(vp, step);
             }
-            const float nv = av - a.lr_a * step;
-            if (!a.dry) {
-              __stcg(mA[n] + row * (unsigned)mJp[n] + lane, nv);
-              if (BF) __stcg(mAb[n] + row * (unsigned)mJb[n] + lane, __bfloat16_as_ushort(__float2bfloat16_rn(nv)));
+            float nv;
+            if (SNAP) {
+              // the change goes to the block's end; this CTA's later modes
+              // read the row as this minibatch left it (w + delta form)
+              const float dl = -__fmul_rn(a.lr_a, step);
+              nv = __fadd_rn(av, dl);
+              a.snap_drow[(((size_t)a.snap_grp * N + n) * M + st) * Jmax + lane] = dl;
+              if (lane == 0) {
+                const unsigned owner = (row * 2654435761u + (unsigned)n * 40503u) % (unsigned)Gtot;
+                const int at = atomicAdd(a.snap_count + owner * stride + a.snap_grp, 1);
+                a.snap_list[((size_t)owner * stride + a.snap_grp) * (size_t)(N * M) + at] =
+                    make_int2((int)row, (n << 16) | st);
+              }
+            } else {
+              nv = av - a.lr_a * step;
+              if (!a.dry) {
+                __stcg(mA[n] + row * (unsigned)mJp[n] + lane, nv);
+                if (BF) __stcg(mAb[n] + row * (unsigned)mJb[n] + lane, __bfloat16_as_ushort(__float2bfloat16_rn(nv)));
+              }
             }
-            if (n + 1 < N) put_word(a.mail + ((unsigned)n * (unsigned)M + st) * (unsigned)Jmax + lane, tag, nv);
+            if (n + 1 < N)
+              put_word(a.mail + ((unsigned)n * (unsigned)M + st) * (unsigned)(Jmax + (Jmax & 1)) + lane, tag, nv);
             if (probe && a.probeF) a.probeF[((unsigned)n * M + st) * kMaxJ + lane] = F;
           }
         }
     }
     buf ^= 1;
   }
+  if (SNAP && iters > 0 && !snap_boundary(iters - 1)) return;
 
-  if (c == 0 && !a.dry) {
+  if ((SNAP ? a.snap_cta == 0 : c == 0) && !a.dry) {
 #pragma unroll 1
     for (int i = tid; i < sumJR; i += T) {
       a.B[i] = Bsm[i];
@@ -1434,7 +1639,7 @@ __device__ __forceinline__ void epoch_body(const EpochArgs& a, const int G, cons
     }
 #pragma unroll 1
     for (int lin = tid; lin < prodJ; lin += T) {
-      const uint32_t packed = ldig[lin];
+      const uint32_t packed = core_digits(lin);
       float acc = 0.f;
       for (int r = 0; r < R; ++r) {
         float prod = 1.f;
@@ -1450,7 +1655,37 @@ __device__ __forceinline__ void epoch_body(const EpochArgs& a, const int G, cons
 template <bool BF>
 __global__ void __launch_bounds__(kEpochThreads, 1)
 k_epoch(EpochArgs a) {
-  epoch_body<BF>(a, gridDim.x, blockIdx.x);
+  epoch_body<BF, false>(a, gridDim.x, blockIdx.x);
+}
+
+// K-snapshot form (a labelled variant of Algorithm 1's minibatch order): the
+// grid is a.snap_k groups of a.snap_gk CTAs.  In every block of K consecutive
+// minibatches, group q runs minibatch q of the block exactly as k_epoch would
+// on snap_gk CTAs (its own exchange buffers, its own chain of core and factor
+// phases), but from the model as it stood when the block began: it writes no
+// parameter and records its changes.  At the block's end (two grid barriers)
+// the Kruskal-column changes are added to B and the factor-row changes to A in
+// minibatch order, each row by the one CTA its index hashes to, so the result
+// does not depend on timing.  One chain of dependent phases per block instead
+// of per minibatch.
+template <bool BF>
+__global__ void __launch_bounds__(kEpochThreads, 1)
+k_epoch_snap(EpochArgs a) {
+  __shared__ __align__(16) EpochArgs s_a;
+  const int grp = (int)blockIdx.x / a.snap_gk, c = (int)blockIdx.x - grp * a.snap_gk;
+  if (threadIdx.x == 0) {
+    s_a = a;
+    s_a.snap_grp = grp;
+    s_a.snap_cta = (int)blockIdx.x;
+    // this group's exchange buffers
+    const size_t NJ = (size_t)a.g.N * a.g.Jmax;
+    s_a.part = a.part + (size_t)grp * a.snap_gk * a.pstride;
+    s_a.inbox = a.inbox + (size_t)grp * a.snap_gk * a.pstride;
+    s_a.piece = a.piece + (size_t)grp * a.snap_gk * NJ;
+    s_a.mail = a.mail + (size_t)grp * a.s.M * a.g.N * (a.g.Jmax + (a.g.Jmax & 1));
+  }
+  __syncthreads();
+  epoch_body<BF, true>(s_a, a.snap_gk, c);
 }
 
 // Many independent tensors in one persistent launch: the grid is split into
@@ -1472,7 +1707,7 @@ k_epoch_multi(MultiArgs m) {
 #pragma unroll 1
     for (int i = threadIdx.x; i < (int)(sizeof(EpochArgs) / 4); i += blockDim.x) dst[i] = src[i];
     __syncthreads();
-    epoch_body<BF>(s_a, G, c);
+    epoch_body<BF, false>(s_a, G, c);
     __syncthreads();
   }
 }
@@ -1495,6 +1730,10 @@ const void* kernel_for(int precision) {
 
 const void* multi_kernel_for(int precision) {
   return precision == 1 ? (const void*)k_epoch_multi<true> : (const void*)k_epoch_multi<false>;
+}
+
+const void* snap_kernel_for(int precision) {
+  return precision == 1 ? (const void*)k_epoch_snap<true> : (const void*)k_epoch_snap<false>;
 }
 
 }  // namespace
@@ -1531,6 +1770,25 @@ cudaError_t launch_epoch(const EpochArgs& a, int ctas, size_t smem, cudaStream_t
   EpochArgs copy = a;
   void* args[] = {&copy};
   return cudaLaunchCooperativeKernel(kernel_for(a.precision), dim3(ctas), dim3(kEpochThreads), args, smem, st);
+}
+
+cudaError_t epoch_snap_setup(int precision, size_t smem) {
+  return cudaFuncSetAttribute(snap_kernel_for(precision), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+}
+
+int epoch_snap_max_ctas(int precision, size_t smem) {
+  const void* fn = snap_kernel_for(precision);
+  int dev = 0, sms = 0, per = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fn, kEpochThreads, smem) != cudaSuccess) return 0;
+  return per * sms;
+}
+
+cudaError_t launch_epoch_snap(const EpochArgs& a, int ctas, size_t smem, cudaStream_t st) {
+  EpochArgs copy = a;
+  void* args[] = {&copy};
+  return cudaLaunchCooperativeKernel(snap_kernel_for(a.precision), dim3(ctas), dim3(kEpochThreads), args, smem, st);
 }
 
 cudaError_t launch_wait_probe(unsigned long long watchdog_ns, int* err, const unsigned long long* word,

@@ -149,6 +149,17 @@ struct EpochArgs {
   int64_t probe_batch;
   float* probeV;         // [N][R][kMaxJ]
   float* probeF;         // [N][M][kMaxJ], indexed by the run's first sorted position
+  // K-snapshot form (k_epoch_snap): snap_k groups of snap_gk CTAs; group q
+  // runs minibatch b0 + iK + q of block i from the block's starting model and
+  // records its changes; at the block's end they are added in minibatch order.
+  int snap_k;
+  int snap_gk;
+  int snap_grp;          // this CTA's group (set per CTA in the kernel)
+  int snap_cta;          // this CTA's index in the whole grid
+  float* snap_dB;        // [K][sum_n J_n R] changes of the Kruskal columns
+  float* snap_drow;      // [K][N][M][Jmax] changes of the factor rows, by mode-n run start
+  int2* snap_list;       // [G][K][N M] (row, mode << 16 | run start) of the rows CTA g applies
+  int* snap_count;       // [G][K] entries of each list
 };
 
 // A batched launch: EpochArgs of every tensor (device array), and for each
@@ -190,6 +201,9 @@ size_t epoch_smem_bytes(const Geometry& g, int chunk_max, int ctas, int precisio
 cudaError_t epoch_kernel_setup(int precision, size_t smem);
 int epoch_max_ctas(int precision, size_t smem);
 cudaError_t launch_epoch(const EpochArgs& a, int ctas, size_t smem, cudaStream_t st);
+cudaError_t epoch_snap_setup(int precision, size_t smem);
+int epoch_snap_max_ctas(int precision, size_t smem);
+cudaError_t launch_epoch_snap(const EpochArgs& a, int ctas, size_t smem, cudaStream_t st);
 cudaError_t launch_wait_probe(unsigned long long watchdog_ns, int* err, const unsigned long long* word,
                               cudaStream_t st);
 cudaError_t epoch_multi_setup(int precision, size_t smem);

@@ -289,13 +289,17 @@ def config2(scale: float = 1.0, seed: int = 0) -> Workload:
     """Netflix-shaped rating tensor 480,189 x 17,770 x 2,182 with 100M nonzeros;
     Zipf 1.1 (users), Zipf 1.3 (items), uniform (time); planted J=(10,10,10),
     values quantised into {1..5} with N(0, 0.3^2) noise; 99/1 split; J=10, R=5,
-    M=4096, lr=lambda=1e-3, 20 epochs."""
+    M=4096, lr=0.05, lambda=1e-3, 20 epochs.  The learning rate is not part of
+    the workload's definition: with the 1/M normaliser of Eq. 18, lr = 1e-3
+    leaves the model at its initial test RMSE, while 0.05 lowers it steadily
+    (measured with the FP64 oracle at 0.4% scale: 0.998, 0.990, 0.986, 0.983
+    after epochs 1-4 against a spread of 0.995)."""
     shape = (_scaled(480_189, scale), _scaled(17_770, scale), _scaled(2_182, math.sqrt(scale) if scale < 1 else 1.0))
     nnz = _scaled(100_000_000, scale, lo=1000)
     t = make_tensor(shape, nnz, [("zipf", 1.1), ("zipf", 1.3), ("uniform",)], (10, 10, 10),
                     0.3, 0.01, seed, rating=True)
     return Workload(f"netflix-like-{shape[0]}x{shape[1]}x{shape[2]}-{nnz}", t, (10, 10, 10), 5,
-                    4096, 1e-3, 1e-3, 20)
+                    4096, 0.05, 1e-3, 20)
 
 
 def config3(scale: float = 1.0, seed: int = 0) -> Workload:
@@ -319,7 +323,7 @@ RANK_SWEEP = [((J, 5, 5), 5) for J in (5, 10, 15, 20, 25)] + [((5, 5, 5), R) for
 def ranksweep(scale: float = 0.05, seed: int = 0):
     """The rank-sweep workload: one rating tensor with config 2's shape and
     distributions at `scale` (the data stay fixed across the sweep), and the
-    (ranks, R_core) points of RANK_SWEEP.  M = 4096, lr = lambda = 1e-3."""
+    (ranks, R_core) points of RANK_SWEEP.  M = 4096, lr = 0.05, lambda = 1e-3."""
     return config2(scale=scale, seed=seed), list(RANK_SWEEP)
 
 

@@ -55,6 +55,7 @@ def test_struct_layouts_match_c(lib, tmp_path):
         " sizeof(std_epoch_stats), sizeof(std_probe));\n"
         'printf("%zu %zu %zu %zu\\n", sizeof(std_batch_stats), offsetof(std_batch_stats, graph_replayed),'
         " offsetof(std_options, contraction), offsetof(std_options, momentum));\n"
+        'printf("%zu\\n", offsetof(std_options, snapshot));\n'
         'printf("%d %d %d %d\\n", STD_MAX_ORDER, STD_MAX_RANK, STD_MAX_CORE, STD_MAX_MINIBATCH);\n'
         "return 0;}\n")
     exe = tmp_path / "layout"
@@ -67,7 +68,8 @@ def test_struct_layouts_match_c(lib, tmp_path):
     b_sizes = [int(v) for v in out[1].split()]
     assert b_sizes == [ctypes.sizeof(lib.std_batch_stats), lib.std_batch_stats.graph_replayed.offset,
                        lib.std_options.contraction.offset, lib.std_options.momentum.offset]
-    lims = [int(v) for v in out[2].split()]
+    assert int(out[2]) == lib.std_options.snapshot.offset
+    lims = [int(v) for v in out[3].split()]
     assert lims == [lib.STD_MAX_ORDER, lib.STD_MAX_RANK, lib.STD_MAX_CORE, lib.STD_MAX_MINIBATCH]
 
 
@@ -101,7 +103,8 @@ def test_create_rejects_bad_options_and_nnz(lib):
     idx = np.zeros((1, 3), np.int32)
     val = np.zeros(1, np.float32)
     for field, value in [("precision", 2), ("norm_mode", 3), ("ptr_kind", 5), ("ctas", -1), ("init_mode", 9),
-                         ("contraction", 2), ("momentum", 1.0), ("momentum", -0.1), ("momentum", float("nan"))]:
+                         ("contraction", 2), ("momentum", 1.0), ("momentum", -0.1), ("momentum", float("nan")),
+                         ("snapshot", -1)]:
         o = lib.std_default_options()
         setattr(o, field, value)
         with pytest.raises(lib.StdError) as ei:
@@ -109,6 +112,17 @@ def test_create_rejects_bad_options_and_nnz(lib):
         assert ei.value.code == lib.STD_EINVAL
     with pytest.raises(lib.StdError) as ei:
         lib.std_create(3, [4, 4, 4], [2, 2, 2], 0, idx, val, None)
+    assert ei.value.code == lib.STD_EINVAL
+    # the K-snapshot form: at most 64 minibatches per block, and no momentum
+    o = lib.std_default_options()
+    o.snapshot = 65
+    with pytest.raises(lib.StdError) as ei:
+        lib.std_create(3, [4, 4, 4], [2, 2, 2], 1, idx, val, o)
+    assert ei.value.code == lib.STD_EUNSUPPORTED
+    o.snapshot = 4
+    o.momentum = 0.5
+    with pytest.raises(lib.StdError) as ei:
+        lib.std_create(3, [4, 4, 4], [2, 2, 2], 1, idx, val, o)
     assert ei.value.code == lib.STD_EINVAL
 
 

@@ -506,3 +506,105 @@ def test_fullsize_schedule_bitexact_sampled_minibatches(B, full2):
 def test_fullsize_step_gradients_first_minibatch(B, synth, full2):
     _step_case(B, synth, full2.tensor, full2.ranks, full2.r_core, full2.minibatch, batch=0, init="rating",
                lr=(0.05, 0.05))
+
+
+# ---------------------------------------------------------------------------
+# The bench's launch shape over many minibatches: M = 4096 on the rating
+# tensor's distributions (Zipf-hot rows that span many chunks) runs on
+# min(256, SMs) = 152 CTAs of a GB300 by the library's default choice, the
+# full-warp reduce-scatter branch; M = 8192 on the 4-order workload likewise.
+# Tag sequencing across minibatches and epochs, the grid barrier and run
+# pieces carried over many minibatches are all exercised here.
+# ---------------------------------------------------------------------------
+
+def _epoch_parity(B, synth, w, epochs, lr, check_after, bf16=False, lam=1e-3):
+    t = w.tensor
+    c, v = t.split("train")
+    tc, tv = t.split("test")
+    R, M = w.r_core, w.minibatch
+    A0, B0 = synth.init_params(t.shape, w.ranks, R, mode="rating" if t.meta["rating"] else "normal", seed=1,
+                               mean_value=float(np.mean(v)))
+    ref = O.Model(t.shape, w.ranks, R, A0, B0)
+    worst = {"fp32": 0.0, "bf16": 0.0}
+    forms = [("fp32", {})] + ([("bf16", {"precision": 1})] if bf16 else [])
+    ctxs = {name: _gpu(B, t.shape, w.ranks, R, c, v, A0, B0, **o) for name, o in forms}
+    try:
+        for ep in range(epochs):
+            ref.epoch(c, v, M, 2, ep, lr, lr, lam, lam)
+            for name, g in ctxs.items():
+                g.epoch(lr, lr, lam, lam, M)
+            if ep + 1 not in check_after:
+                continue
+            for cc, vv in ((c, v), (tc, tv)):
+                r_o, m_o = ref.rmse_mae(cc, vv)
+                for name, g in ctxs.items():
+                    r_g, m_g = g.rmse(cc, vv)
+                    worst[name] = max(worst[name], abs(r_g - r_o), abs(m_g - m_o))
+    finally:
+        for g in ctxs.values():
+            g.close()
+    return worst, ref
+
+
+def test_epoch_rmse_parity_bench_shape_rating_10_epochs(B, synth):
+    w = synth.config2(scale=0.004)          # 396k training nonzeros, 97 minibatches of 4096 per epoch
+    tc, tv = w.tensor.split("test")
+    c, v = w.tensor.split("train")
+    A0, B0 = synth.init_params(w.tensor.shape, w.ranks, w.r_core, mode="rating", seed=1,
+                               mean_value=float(np.mean(v)))
+    start = O.Model(w.tensor.shape, w.ranks, w.r_core, A0, B0)
+    start.build_core()
+    worst, ref = _epoch_parity(B, synth, w, 10, 0.05, set(range(1, 11)), bf16=True)
+    assert worst["fp32"] <= 1e-3, worst
+    # the BF16 form against the FP64 oracle, same bar
+    assert worst["bf16"] <= 1e-3, worst
+    # the run trains: the test RMSE falls by more than the parity bar many times over
+    assert ref.rmse_mae(tc, tv)[0] < start.rmse_mae(tc, tv)[0] - 0.02
+
+
+def test_epoch_rmse_parity_bench_shape_4order(B, synth):
+    w = synth.config3(scale=0.004)          # 180k training nonzeros, 22 minibatches of 8192 per epoch
+    worst, _ = _epoch_parity(B, synth, w, 5, 0.5, {2, 5}, bf16=True)
+    assert worst["fp32"] <= 1e-3, worst
+    assert worst["bf16"] <= 1e-3, worst
+
+
+def test_params_after_8_minibatches_bench_shape(B, synth):
+    """Eight consecutive minibatches of 4096 at 152 CTAs from one state:
+    every factor and Kruskal matrix within the FP32 step tolerance (1e-5 of
+    the parameter scale) of the oracle after the same eight minibatches."""
+    w = synth.config2(scale=0.004)
+    t = w.tensor
+    c, v = t.split("train")
+    A0, B0 = synth.init_params(t.shape, w.ranks, w.r_core, mode="rating", seed=1, mean_value=float(np.mean(v)))
+    ref = O.Model(t.shape, w.ranks, w.r_core, A0, B0)
+    lr, lam = (0.05, 0.05), (1e-3, 1e-3)
+    with _gpu(B, t.shape, w.ranks, w.r_core, c, v, A0, B0) as g:
+        g.batches(lr[0], lr[1], lam[0], lam[1], 4096, 0, 8)
+        Ag, Bg, core, _ = g.get_params()
+    ref.epoch(c, v, 4096, 2, 0, lr[0], lr[1], lam[0], lam[1], 0, 0, 8)
+    for n in range(3):
+        assert float(np.abs(Ag[n] - ref.A[n]).max()) <= 1e-5 * float(np.abs(ref.A[n]).max())
+        assert float(np.abs(Bg[n] - ref.B[n]).max()) <= 1e-5 * float(np.abs(ref.B[n]).max())
+        # rows the eight minibatches never touched are bit-for-bit the start
+        touched = np.zeros(t.shape[n], bool)
+        ids = O.perm_range(c.shape[0], 2, 0, 0, 8 * 4096)
+        touched[c[ids, n]] = True
+        assert np.array_equal(Ag[n][~touched], A0[n][~touched])
+
+
+# ---------------------------------------------------------------------------
+# The library's declared limits: order STD_MAX_ORDER = 6, rank and R_core
+# STD_MAX_RANK = 32, core size STD_MAX_CORE = 16,384 entries.
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("shape,ranks,R,M,nnz", [
+    ((9, 8, 7, 6, 5, 4), (2, 3, 2, 2, 3, 2), 3, 64, 1500),     # N = 6
+    ((120, 40, 30), (32, 4, 4), 5, 256, 3000),                # J_1 = 32
+    ((60, 50, 40), (4, 4, 4), 32, 256, 3000),                 # R_core = 32
+    ((100, 90, 40), (32, 32, 16), 2, 128, 600),               # prod J = 16,384
+])
+def test_step_gradients_at_declared_limits(B, synth, shape, ranks, R, M, nnz):
+    t = synth.make_tensor(shape, nnz, [("uniform",)] * len(shape), tuple(min(j, 4) for j in ranks), 0.1, 0.0,
+                          seed=37)
+    _step_case(B, synth, t, ranks, R, M, batch=0)
