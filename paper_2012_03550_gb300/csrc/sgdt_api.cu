@@ -63,6 +63,7 @@ struct std_ctx {
   size_t sched_bytes = 0;
   int64_t sched_epoch = -1;
   int sched_M = 0;
+  int64_t sched_b0 = 0, sched_b1 = 0;   // minibatches the schedule buffer holds
   // epoch exchange words (tagged; see k_epoch)
   unsigned long long* part = nullptr;
   size_t part_words = 0;
@@ -96,6 +97,10 @@ struct std_ctx {
   int32_t cursor_M = 0;             // minibatch size of that epoch
   size_t allocated = 0;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr, evm = nullptr;
+  // per-segment timing of a timed call: before the sampler/tiler, between
+  // it and the update kernel, after the update kernel (3 events a segment)
+  std::vector<cudaEvent_t> seg_ev;
+  int seg_count = 0;
 };
 
 namespace {
@@ -148,17 +153,21 @@ int ensure_stage(std_ctx* c, size_t bytes) {
 
 int payload_floats(const Geometry& g) { return epoch_payload_floats(g); }
 
-int ensure_schedule(std_ctx* c, int M) {
-  if (c->sched_mem && c->sched_M == M && c->sched_epoch == c->epoch) return STD_OK;
+// Schedules minibatches [bs, be) of the current epoch at minibatch size M
+// (sampler and tiler) into the context's schedule buffer, unless it holds
+// them already.  Position t is stored at index t - bs * M (Schedule.b_first).
+int ensure_schedule_range(std_ctx* c, int M, int64_t bs, int64_t be) {
+  if (c->sched_mem && c->sched_M == M && c->sched_epoch == c->epoch && c->sched_b0 <= bs && be <= c->sched_b1)
+    return STD_OK;
   const int N = c->g.N;
-  const int64_t nb = (c->nnz + M - 1) / M;
-  const int64_t npad = nb * M;
+  const int64_t npad = (be - bs) * M;
   const size_t words = (size_t)npad * schedule_words_per_position(N);
   const size_t bytes = words * 4;
   if (bytes > c->sched_bytes) {
     dev_free(c, c->sched_mem, c->sched_bytes);
     c->sched_mem = nullptr;
     c->sched_bytes = 0;
+    c->sched_b0 = c->sched_b1 = 0;
     int rc = dev_alloc(c, &c->sched_mem, bytes, "epoch schedule");
     if (rc) return rc;
     c->sched_bytes = bytes;
@@ -175,12 +184,42 @@ int ensure_schedule(std_ctx* c, int M) {
   s.npad = npad;
   s.n = c->nnz;
   s.M = M;
+  s.b_first = bs;
   const Feistel f = make_feistel((uint64_t)c->nnz, c->opt.seed_sched, (uint64_t)c->epoch);
-  STD_CUDA(launch_schedule(c->g, c->coo, c->cs, f, s, 0, nb, c->stream), "sampler/tiler launch");
+  STD_CUDA(launch_schedule(c->g, c->coo, c->cs, f, s, bs, be, c->stream), "sampler/tiler launch");
   c->sched = s;
   c->sched_M = M;
   c->sched_epoch = c->epoch;
+  c->sched_b0 = bs;
+  c->sched_b1 = be;
   return STD_OK;
+}
+
+// The whole epoch's schedule (batched launches run whole epochs or long
+// stretches of one).
+int ensure_schedule(std_ctx* c, int M) {
+  const int64_t nb = (c->nnz + M - 1) / M;
+  return ensure_schedule_range(c, M, 0, nb);
+}
+
+// Minibatches per schedule segment of std_sgd_epoch / std_sgd_batches: about
+// 2^20 sampled positions (the schedule of one segment is ~100 MB for a 3-order
+// tensor, and the update kernel reads it back while it is still in L2), a
+// multiple of K in the K-snapshot form so that blocks never straddle segments.
+int64_t segment_batches(int M, int K) {
+  int64_t S = (1LL << 20) / M;
+  if (S < 1) S = 1;
+  if (K >= 2) S = S < K ? K : S / K * K;
+  return S;
+}
+
+cudaEvent_t seg_event(std_ctx* c, size_t i) {
+  while (c->seg_ev.size() <= i) {
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+    c->seg_ev.push_back(e);
+  }
+  return c->seg_ev[i];
 }
 
 int choose_ctas(std_ctx* c, int M, int* ctas, int* chunk_max, size_t* smem) {
@@ -358,94 +397,83 @@ int ensure_items(std_ctx* c, T** p, size_t* have, size_t items, const char* what
   return STD_OK;
 }
 
-// Minibatches [b0, b1) in the K-snapshot form (std_options.snapshot = K).
-int run_snapshot(std_ctx* c, float lr_a, float lr_b, float lam_a, float lam_b, int32_t M, int64_t b0, int64_t b1,
-                 bool probe, bool record_end) {
-  const int K = c->opt.snapshot;
-  int Gk = 0, chunk = 0;
-  size_t smem = 0;
-  int rc = choose_snap_ctas(c, M, K, &Gk, &chunk, &smem);
-  if (rc) return rc;
-  const int G = Gk * K;
+// Runs minibatches [b0, b1) of the current epoch, Algorithm 1's order or the
+// K-snapshot form (std_options.snapshot = K), segment after segment: the
+// sampler/tiler schedules a segment, then one cooperative launch runs it.
+// With `timed`, three events per segment are recorded (seg_ev).
+int run_batches(std_ctx* c, float lr_a, float lr_b, float lam_a, float lam_b, int32_t M, int64_t b0, int64_t b1,
+                bool probe, bool timed) {
+  const int K = c->opt.snapshot >= 2 ? c->opt.snapshot : 1;
   const int N = c->g.N;
-  int sumJR = 0;
-  for (int n = 0; n < N; ++n) sumJR += c->g.J[n] * c->g.R;
+  int G = 0, Gk = 0, chunk = 0;
+  size_t smem = 0;
+  int rc = STD_OK;
+  if (K >= 2) {
+    rc = choose_snap_ctas(c, M, K, &Gk, &chunk, &smem);
+    G = Gk * K;
+  } else {
+    rc = choose_ctas(c, M, &G, &chunk, &smem);
+  }
+  if (rc) return rc;
   rc = ensure_scratch(c, G, payload_floats(c->g), M * K);
-  if (!rc) rc = ensure_items(c, &c->snap_dB, &c->snap_dB_floats, (size_t)K * sumJR, "snapshot column changes");
-  if (!rc)
-    rc = ensure_items(c, &c->snap_drow, &c->snap_drow_floats, (size_t)K * N * M * c->g.Jmax, "snapshot row changes");
-  if (!rc) rc = ensure_items(c, &c->snap_list, &c->snap_list_items, (size_t)G * K * N * M, "snapshot row lists");
-  if (!rc) rc = ensure_items(c, &c->snap_count, &c->snap_count_items, (size_t)G * K, "snapshot list counts");
   if (rc) return rc;
-  uint32_t tag_base = 0;
-  rc = reserve_tags(c, b1 - b0, &tag_base);
-  if (rc) return rc;
-  EpochArgs a = epoch_args(c, lr_a, lr_b, lam_a, lam_b, b0, b1, chunk, tag_base);
+  if (K >= 2) {
+    int sumJR = 0;
+    for (int n = 0; n < N; ++n) sumJR += c->g.J[n] * c->g.R;
+    rc = ensure_items(c, &c->snap_dB, &c->snap_dB_floats, (size_t)K * sumJR, "snapshot column changes");
+    if (!rc)
+      rc = ensure_items(c, &c->snap_drow, &c->snap_drow_floats, (size_t)K * N * M * c->g.Jmax, "snapshot row changes");
+    if (!rc) rc = ensure_items(c, &c->snap_list, &c->snap_list_items, (size_t)G * K * N * M, "snapshot row lists");
+    if (!rc) rc = ensure_items(c, &c->snap_count, &c->snap_count_items, (size_t)G * K, "snapshot list counts");
+    if (rc) return rc;
+  }
+  float* pV = nullptr;
+  float* pF = nullptr;
   if (probe) {
     const size_t need = (size_t)N * c->g.R * kMaxJ + (size_t)N * M * kMaxJ;
     rc = ensure_items(c, &c->probe_mem, &c->probe_floats, need, "gradient probe");
     if (rc) return rc;
     STD_CUDA(cudaMemsetAsync(c->probe_mem, 0, need * 4, c->stream), "probe clear");
-    a.probe_batch = b0;
-    a.probeV = c->probe_mem;
-    a.probeF = c->probe_mem + (size_t)N * c->g.R * kMaxJ;
-  }
-  a.snap_k = K;
-  a.snap_gk = Gk;
-  a.snap_dB = c->snap_dB;
-  a.snap_drow = c->snap_drow;
-  a.snap_list = c->snap_list;
-  a.snap_count = c->snap_count;
-  STD_CUDA(cudaMemsetAsync(c->snap_count, 0, (size_t)G * K * sizeof(int), c->stream), "snapshot counts");
-  STD_CUDA(cudaMemsetAsync(c->bar, 0, sizeof(unsigned long long), c->stream), "barrier clear");
-  if (record_end) STD_CUDA(cudaEventRecord(c->evm, c->stream), "event");
-  if (b1 > b0) STD_CUDA(launch_epoch_snap(a, G, smem, c->stream), "snapshot kernel launch");
-  if (record_end) STD_CUDA(cudaEventRecord(c->ev1, c->stream), "event");
-  return read_err(c, "snapshot kernel");
-}
-
-// Runs minibatches [b0, b1) of the current schedule.  With record_end, ev1
-// is recorded on the stream right after the kernel (the caller records ev0).
-int run_batches(std_ctx* c, float lr_a, float lr_b, float lam_a, float lam_b, int32_t M, int64_t b0, int64_t b1,
-                bool probe, bool record_end) {
-  int rc = ensure_schedule(c, M);
-  if (rc) return rc;
-  if (c->opt.snapshot >= 2) return run_snapshot(c, lr_a, lr_b, lam_a, lam_b, M, b0, b1, probe, record_end);
-  int G = 0, chunk = 0;
-  size_t smem = 0;
-  rc = choose_ctas(c, M, &G, &chunk, &smem);
-  if (rc) return rc;
-  const int payload = payload_floats(c->g);
-  rc = ensure_scratch(c, G, payload, M);
-  if (rc) return rc;
-  uint32_t tag_base = 0;
-  rc = reserve_tags(c, b1 - b0, &tag_base);
-  if (rc) return rc;
-  float* pV = nullptr;
-  float* pF = nullptr;
-  if (probe) {
-    const size_t need = (size_t)c->g.N * c->g.R * kMaxJ + (size_t)c->g.N * M * kMaxJ;
-    if (need > c->probe_floats) {
-      dev_free(c, c->probe_mem, c->probe_floats * 4);
-      c->probe_mem = nullptr;
-      c->probe_floats = 0;
-      rc = dev_alloc(c, (void**)&c->probe_mem, need * 4, "gradient probe");
-      if (rc) return rc;
-      c->probe_floats = need;
-    }
-    STD_CUDA(cudaMemsetAsync(c->probe_mem, 0, need * 4, c->stream), "probe clear");
     pV = c->probe_mem;
-    pF = c->probe_mem + (size_t)c->g.N * c->g.R * kMaxJ;
+    pF = c->probe_mem + (size_t)N * c->g.R * kMaxJ;
   }
-  EpochArgs a = epoch_args(c, lr_a, lr_b, lam_a, lam_b, b0, b1, chunk, tag_base);
-  a.probe_batch = probe ? b0 : -1;
-  a.probeV = pV;
-  a.probeF = pF;
-  STD_CUDA(cudaMemsetAsync(c->bar, 0, sizeof(unsigned long long), c->stream), "barrier clear");
-  if (record_end) STD_CUDA(cudaEventRecord(c->evm, c->stream), "event");
-  if (b1 > b0) STD_CUDA(launch_epoch(a, G, smem, c->stream), "epoch kernel launch");
-  if (record_end) STD_CUDA(cudaEventRecord(c->ev1, c->stream), "event");
-  return read_err(c, "epoch kernel");
+  const int64_t S = segment_batches(M, K);
+  c->seg_count = 0;
+  for (int64_t sb = b0; sb < b1; sb += S) {
+    const int64_t se = b1 - sb < S ? b1 : sb + S;
+    const size_t ei = 3 * (size_t)c->seg_count;
+    if (timed) {
+      cudaEvent_t e0 = seg_event(c, ei), e1 = seg_event(c, ei + 1), e2 = seg_event(c, ei + 2);
+      if (!e0 || !e1 || !e2) return set_error(STD_ECUDA, "event create");
+      STD_CUDA(cudaEventRecord(e0, c->stream), "event");
+    }
+    rc = ensure_schedule_range(c, M, sb, se);
+    if (rc) return rc;
+    if (timed) STD_CUDA(cudaEventRecord(c->seg_ev[ei + 1], c->stream), "event");
+    uint32_t tag_base = 0;
+    rc = reserve_tags(c, se - sb, &tag_base);
+    if (rc) return rc;
+    EpochArgs a = epoch_args(c, lr_a, lr_b, lam_a, lam_b, sb, se, chunk, tag_base);
+    a.probe_batch = probe && sb == b0 ? b0 : -1;
+    a.probeV = pV;
+    a.probeF = pF;
+    STD_CUDA(cudaMemsetAsync(c->bar, 0, sizeof(unsigned long long), c->stream), "barrier clear");
+    if (K >= 2) {
+      a.snap_k = K;
+      a.snap_gk = Gk;
+      a.snap_dB = c->snap_dB;
+      a.snap_drow = c->snap_drow;
+      a.snap_list = c->snap_list;
+      a.snap_count = c->snap_count;
+      STD_CUDA(cudaMemsetAsync(c->snap_count, 0, (size_t)G * K * sizeof(int), c->stream), "snapshot counts");
+      STD_CUDA(launch_epoch_snap(a, G, smem, c->stream), "snapshot kernel launch");
+    } else {
+      STD_CUDA(launch_epoch(a, G, smem, c->stream), "epoch kernel launch");
+    }
+    if (timed) STD_CUDA(cudaEventRecord(c->seg_ev[ei + 2], c->stream), "event");
+    c->seg_count += 1;
+  }
+  return read_err(c, K >= 2 ? "snapshot kernel" : "epoch kernel");
 }
 
 const int32_t* stage_coords(std_ctx* c, const int32_t* coords, const float* values, int64_t k,
@@ -515,6 +543,7 @@ int std_destroy(std_ctx* c) {
   if (c->ev0) cudaEventDestroy(c->ev0);
   if (c->ev1) cudaEventDestroy(c->ev1);
   if (c->evm) cudaEventDestroy(c->evm);
+  for (cudaEvent_t e : c->seg_ev) cudaEventDestroy(e);
   delete c;
   return STD_OK;
 }
@@ -658,15 +687,19 @@ int std_sgd_epoch(std_ctx* c, float lr_a, float lr_b, float lambda_a, float lamb
   if (c->cursor != 0)
     return set_error(STD_EINVAL, "an epoch is in progress on this context (batched steps); finish it with std_batch_step");
   const int64_t nb = (c->nnz + minibatch - 1) / minibatch;
-  // the epoch time covers the sampler/tiler and the update kernel
-  STD_CUDA(cudaEventRecord(c->ev0, c->stream), "event");
-  rc = ensure_schedule(c, minibatch);
-  if (!rc) rc = run_batches(c, lr_a, lr_b, lambda_a, lambda_b, minibatch, 0, nb, false, true);
+  // the epoch time covers the sampler/tiler and the update kernel of every segment
+  rc = run_batches(c, lr_a, lr_b, lambda_a, lambda_b, minibatch, 0, nb, false, true);
   if (rc) return rc;
   float ms = 0.f, ms_sched = 0.f, ms_upd = 0.f;
-  STD_CUDA(cudaEventElapsedTime(&ms, c->ev0, c->ev1), "event time");
-  STD_CUDA(cudaEventElapsedTime(&ms_sched, c->ev0, c->evm), "event time");
-  STD_CUDA(cudaEventElapsedTime(&ms_upd, c->evm, c->ev1), "event time");
+  if (c->seg_count > 0)
+    STD_CUDA(cudaEventElapsedTime(&ms, c->seg_ev[0], c->seg_ev[3 * (size_t)c->seg_count - 1]), "event time");
+  for (int i = 0; i < c->seg_count; ++i) {
+    float a = 0.f, b = 0.f;
+    STD_CUDA(cudaEventElapsedTime(&a, c->seg_ev[3 * (size_t)i], c->seg_ev[3 * (size_t)i + 1]), "event time");
+    STD_CUDA(cudaEventElapsedTime(&b, c->seg_ev[3 * (size_t)i + 1], c->seg_ev[3 * (size_t)i + 2]), "event time");
+    ms_sched += a;
+    ms_upd += b;
+  }
   if (out) {
     out->seconds = ms * 1e-3;
     out->sched_seconds = ms_sched * 1e-3;
@@ -694,13 +727,17 @@ int std_sgd_batches(std_ctx* c, float lr_a, float lr_b, float lambda_a, float la
   const int N = c->g.N, R = c->g.R, M = minibatch;
   const int64_t t0 = batch_begin * (int64_t)M;
   const int m = (int)((c->nnz - t0) < M ? (c->nnz - t0) : M);
+  // the probed minibatch's run bounds (its segment may have been replaced)
+  rc = ensure_schedule_range(c, M, batch_begin, batch_begin + 1);
+  if (rc) return rc;
+  const int64_t ts = t0 - c->sched.b_first * (int64_t)M;
   std::vector<float> hv((size_t)N * R * kMaxJ), hf((size_t)N * M * kMaxJ);
   std::vector<uint32_t> seg((size_t)m);
   STD_CUDA(cudaMemcpy(hv.data(), c->probe_mem, hv.size() * 4, cudaMemcpyDeviceToHost), "probe copy");
   STD_CUDA(cudaMemcpy(hf.data(), c->probe_mem + hv.size(), hf.size() * 4, cudaMemcpyDeviceToHost), "probe copy");
   if (probe->core_V) std::memcpy(probe->core_V, hv.data(), hv.size() * 4);
   for (int n = 0; n < N; ++n) {
-    STD_CUDA(cudaMemcpy(seg.data(), c->sched.seg + (size_t)n * c->sched.npad + t0, (size_t)m * 4,
+    STD_CUDA(cudaMemcpy(seg.data(), c->sched.seg + (size_t)n * c->sched.npad + ts, (size_t)m * 4,
                         cudaMemcpyDeviceToHost), "segment copy");
     int64_t u = 0;
     for (int q = 0; q < m; ++q) {
@@ -726,7 +763,8 @@ int std_schedule(std_ctx* c, int32_t minibatch, int64_t batch_begin, int64_t bat
   const int64_t nb = (c->nnz + minibatch - 1) / minibatch;
   if (batch_begin < 0 || batch_end > nb || batch_begin > batch_end)
     return set_error(STD_EINVAL, "batch range outside the epoch");
-  int rc = ensure_schedule(c, minibatch);
+  if (batch_end <= batch_begin) return STD_OK;
+  int rc = ensure_schedule_range(c, minibatch, batch_begin, batch_end);
   if (rc) return rc;
   const int64_t t0 = batch_begin * (int64_t)minibatch;
   int64_t t1 = batch_end * (int64_t)minibatch;
@@ -734,16 +772,17 @@ int std_schedule(std_ctx* c, int32_t minibatch, int64_t batch_begin, int64_t bat
   const int64_t cnt = t1 - t0;
   if (cnt <= 0) return STD_OK;
   const int N = c->g.N;
+  const int64_t ts = t0 - c->sched.b_first * (int64_t)minibatch;   // storage index of position t0
   if (sample_ids)
-    STD_CUDA(cudaMemcpy(sample_ids, c->sched.sid + t0, (size_t)cnt * 4, cudaMemcpyDefault), "schedule copy");
+    STD_CUDA(cudaMemcpy(sample_ids, c->sched.sid + ts, (size_t)cnt * 4, cudaMemcpyDefault), "schedule copy");
   std::vector<uint32_t> seg;
   for (int n = 0; n < N; ++n) {
     if (order)
-      STD_CUDA(cudaMemcpy(order + (size_t)n * cnt, c->sched.pos + (size_t)n * c->sched.npad + t0, (size_t)cnt * 4,
+      STD_CUDA(cudaMemcpy(order + (size_t)n * cnt, c->sched.pos + (size_t)n * c->sched.npad + ts, (size_t)cnt * 4,
                           cudaMemcpyDefault), "schedule copy");
     if (seg_start || seg_end) {
       seg.resize((size_t)cnt);
-      STD_CUDA(cudaMemcpy(seg.data(), c->sched.seg + (size_t)n * c->sched.npad + t0, (size_t)cnt * 4,
+      STD_CUDA(cudaMemcpy(seg.data(), c->sched.seg + (size_t)n * c->sched.npad + ts, (size_t)cnt * 4,
                           cudaMemcpyDeviceToHost), "schedule copy");
       for (int64_t q = 0; q < cnt; ++q) {
         if (seg_start) seg_start[(size_t)n * cnt + q] = (int32_t)(seg[q] & 0xffffu);

@@ -66,7 +66,6 @@ constexpr int kRightBudget = 16384;  // floats of precomputed right Gram operand
 constexpr int kSBudget = 32768;      // floats of Kronecker rows materialised at once (FP32 form)
 constexpr int kMaxSmemBytes = 227 * 1024;
 constexpr int kDigitTable = 4096;    // core entries whose packed digits are tabulated in shared memory
-constexpr int kVecItems = kMaxN * (kMaxJ / 2);   // 16-byte loads per sample of one row gather, at most
 
 __host__ __device__ inline int pad4(int x) { return (x + 3) & ~3; }
 
@@ -115,6 +114,17 @@ __host__ __device__ inline int unpacked_payload(int Jn, int R) {
   return pad4(R * Jn) + (R * (R - 1) / 2) * Jn * pad4(Jn);
 }
 
+// Thread tiles (one left column x 4 right columns) of the core-phase Gram
+// partial of a mode, and the sample slices each tile is split into.
+constexpr int kGramSplitChunk = 48;
+__host__ __device__ inline int gram_tiles(int Jn, int R) {
+  return R * (pad4(Jn) >> 2) + (R * (R - 1) / 2) * (pad4(Jn * (Jn + 1) / 2) >> 2);
+}
+__host__ __device__ inline int gram_slices(int ntile) {
+  const int q = kEpochThreads / ntile;
+  return q < 1 ? 1 : (q > 3 ? 3 : q);
+}
+
 // Width of a sample's Gram operand rows: left = [w_r w_r' (pairs) | e w_r],
 // right = [a_j a_j' (upper triangle, padded to 4) | a_j (padded to 4)].
 __host__ __device__ inline int left_width(const Geometry& g) { return g.R * (g.R - 1) / 2 + g.R; }
@@ -143,9 +153,9 @@ __host__ __device__ inline int fp32_row_stride(int Pn) {
 }
 
 struct SmemLayout {
-  int B, VB, Bs, G, GT, GTh, Sh, S, ldig, cdig, vtab, trij, sc[2], rows, master, p, left, right, red, D, q,
-      head, fown, pbuf, total_words;
-  int lw, rw, sfloats, rpre, ldig_on;
+  int B, VB, Bs, G, GT, GTh, Sh, S, ldig, cdig, rowtab, trij, sc[2], rows, master, p, left, right, red, D, q,
+      head, fown, pbuf, gsp, total_words;
+  int lw, rw, sfloats, rpre, ldig_on, gsplit;
 };
 
 // Words of one phase's schedule chunk: coordinates [s][N], value, run
@@ -197,7 +207,7 @@ __host__ __device__ inline SmemLayout smem_layout_v(const Geometry& g, int chunk
   L.S = take(L.sfloats);
   L.ldig = take(L.ldig_on ? g.prodJ : 0);
   L.cdig = take(2 * sum_pn(g));
-  L.vtab = take(g.N * kVecItems);
+  L.rowtab = take(g.sumJ);
   L.trij = take(tri(g.Jmax));
   L.sc[0] = take(sched_chunk_words(g.N, chunk));
   L.sc[1] = take(sched_chunk_words(g.N, chunk));
@@ -212,6 +222,18 @@ __host__ __device__ inline SmemLayout smem_layout_v(const Geometry& g, int chunk
   L.head = take(chunk + 2);
   L.fown = take(32);
   L.pbuf = take(ctas * g.Jmax);
+  // large chunks: each Gram tile of the core phase is summed over up to 3
+  // sample slices by different threads, the slices' partials staged here
+  L.gsplit = chunk >= kGramSplitChunk ? 1 : 0;
+  int gneed = 0;
+  if (L.gsplit)
+    for (int n = 0; n < g.N; ++n) {
+      const int nt = gram_tiles(g.J[n], g.R);
+      const int nsl = gram_slices(nt);
+      const int need = nsl > 1 ? nsl * nt * 4 : 0;
+      gneed = need > gneed ? need : gneed;
+    }
+  L.gsp = take(gneed);
   L.total_words = off;
   return L;
 }
@@ -293,15 +315,6 @@ __device__ __forceinline__ ulonglong2 get_pair(const unsigned long long* p) {
 
 __device__ __forceinline__ uint32_t tag_of(unsigned long long w) { return (uint32_t)(w >> 32); }
 
-// 16 bytes from global memory through L2 only (the factor rows change every
-// minibatch, so L1 copies would go stale).
-__device__ __forceinline__ uint4 ldcg_v4(const void* p) {
-  uint4 v;
-  asm volatile("ld.global.cg.v4.u32 {%0, %1, %2, %3}, [%4];"
-               : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
-               : "l"(p));
-  return v;
-}
 __device__ __forceinline__ float val_of(unsigned long long w) { return __uint_as_float((uint32_t)w); }
 
 // Re-reads *p until it carries `tag` (short back-off after the first rounds,
@@ -399,35 +412,6 @@ __device__ __forceinline__ bool wait_pairs(const unsigned long long* const (&p)[
   }
 }
 
-// wait_pairs with a tag per pair; two[u] false: only the first word of pair u
-// is live (the second is row padding nobody writes).
-template <int K>
-__device__ __forceinline__ bool wait_pairs_tagged(const unsigned long long* const (&p)[K], ulonglong2 (&w)[K],
-                                                  const uint32_t (&tg)[K], const bool (&two)[K], const EpochArgs& a) {
-  unsigned long long t0 = 0;
-  unsigned spins = 0;
-#pragma unroll 1
-  while (true) {
-    bool done = true;
-#pragma unroll
-    for (int u = 0; u < K; ++u)
-      if (p[u] && (tag_of(w[u].x) != tg[u] || (two[u] && tag_of(w[u].y) != tg[u]))) {
-        done = false;
-        w[u] = get_pair(p[u]);
-      }
-    if (done) return true;
-    if (t0 == 0) t0 = globaltimer_ns();
-    if (++spins > 4) __nanosleep(32);
-    if ((spins & 15u) == 0u) {
-      if (ld_volatile_int(a.err) != 0) return false;
-      if (globaltimer_ns() - t0 > a.watchdog_ns) {
-        atomicCAS(a.err, 0, STD_ETIMEOUT);
-        return false;
-      }
-    }
-  }
-}
-
 // Barrier over the G CTAs that work on one tensor (all CTAs of a
 // single-tensor launch, or one group of a batched launch; co-resident in a
 // cooperative launch).  The counter only grows; barrier k completes when it
@@ -497,7 +481,7 @@ __device__ __forceinline__ Phase phase_of(const EpochArgs& a, int64_t b, int G, 
 __device__ __forceinline__ void prefetch_schedule(const EpochArgs& a, int N, int64_t b, int mode, int* buf,
                                                   int chunk_max, FastDiv fper, int G, int c) {
   const Phase ph = phase_of(a, b, G, c);
-  const size_t base = (size_t)(b * (int64_t)a.s.M + ph.lo);
+  const size_t base = (size_t)((b - a.s.b_first) * (int64_t)a.s.M + ph.lo);
   int* crd = buf;
   int* xs = buf + N * chunk_max;
   int* seg = xs + chunk_max;
@@ -655,8 +639,7 @@ __device__ __forceinline__ void epoch_body(const EpochArgs& a, const int G, cons
   // per-mode constants, indexed by the (runtime) mode
   __shared__ int mJ[kMaxN], mJoff[kMaxN], mBoff[kMaxN], mJp[kMaxN], mJb[kMaxN], mPn[kMaxN], mToff[kMaxN],
       mGs[kMaxN], mRoff[kMaxN];
-  __shared__ FastDiv mFna4[kMaxN], mFnq4[kMaxN], mFtJ[kMaxN], mFJ[kMaxN], mFper[kMaxN], mFv[kMaxN];
-  __shared__ int mVc[kMaxN];
+  __shared__ FastDiv mFna4[kMaxN], mFnq4[kMaxN], mFtJ[kMaxN], mFJ[kMaxN], mFper[kMaxN];
   __shared__ float* mA[kMaxN];
   __shared__ float* mvA[kMaxN];
   __shared__ unsigned short* mAb[kMaxN];
@@ -674,7 +657,7 @@ __device__ __forceinline__ void epoch_body(const EpochArgs& a, const int G, cons
   float* Sbuf = sm + L.S;
   uint32_t* ldig = reinterpret_cast<uint32_t*>(sm + L.ldig);
   unsigned long long* cdig = reinterpret_cast<unsigned long long*>(sm + L.cdig);
-  int* vtab = reinterpret_cast<int*>(sm + L.vtab);
+  int* rowtab = reinterpret_cast<int*>(sm + L.rowtab);
   int* trij = reinterpret_cast<int*>(sm + L.trij);
   int* scb[2] = {reinterpret_cast<int*>(sm + L.sc[0]), reinterpret_cast<int*>(sm + L.sc[1])};
   float* rows = sm + L.rows;
@@ -726,21 +709,12 @@ __device__ __forceinline__ void epoch_body(const EpochArgs& a, const int G, cons
       mFper[k] = make_fastdiv((uint32_t)(N + 2 + k));
     }
   }
-  // 16-byte loads per sample of the row gathers.  Phase 0 (core phase and
-  // factor mode 1): every mode's row from A, 4 FP32 (or 8 BF16) entries per
-  // load.  Phase p = 1..N-1 (factor mode p+1): rows of modes k < p from this
-  // minibatch's row slots as tagged word pairs, the others from A.  Entry:
-  // k | pair << 7 | j0 << 8.
-  if (tid < N) {
-    const int ph = tid;
-    int cntv = 0;
-    for (int k = 0; k < N; ++k) {
-      const bool pr = ph > 0 && k < ph;
-      const int step = pr ? 2 : (BF ? 8 : 4);
-      for (int j0 = 0; j0 < a.g.J[k]; j0 += step) vtab[ph * kVecItems + cntv++] = k | (pr ? 128 : 0) | (j0 << 8);
-    }
-    mVc[ph] = cntv;
-    mFv[ph] = make_fastdiv((uint32_t)cntv);
+  const FastDiv f_sumJ = make_fastdiv((uint32_t)sumJ);
+#pragma unroll 1
+  for (int jj = tid; jj < sumJ; jj += T) {
+    int k = 0, j = jj;
+    while (j >= mJ[k]) { j -= mJ[k]; ++k; }
+    rowtab[jj] = k | (j << 8);
   }
   __syncthreads();
   const FastDiv f_R = make_fastdiv((uint32_t)R);
@@ -880,45 +854,24 @@ __device__ __forceinline__ void epoch_body(const EpochArgs& a, const int G, cons
     // ------------------------------------------------------------------
     const int* crd = scb[buf];
     const float* xs = reinterpret_cast<const float*>(scb[buf] + N * chunk_max);
-    {
-      // every sample's N rows with 16-byte loads, four in flight per thread
-      const int nv = mVc[0], tot = cnt * nv;
-      const FastDiv fv = mFv[0];
 #pragma unroll 1
-      for (int i0 = tid; i0 < tot; i0 += 4 * T) {
-        uint4 x[4];
-        int dst[4], e[4];
+    for (int i0 = tid; i0 < cnt * sumJ; i0 += 2 * T) {
+      float v[2];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          const int i = i0 + u * T;
-          e[u] = -1;
-          if (i < tot) {
-            const int s = fdiv(i, fv);
-            e[u] = vtab[i - s * nv];
-            const int k = e[u] & 127, j0 = e[u] >> 8;
-            const unsigned row = (unsigned)crd[s * N + k];
-            dst[u] = s * sumJ + mJoff[k] + j0;
-            x[u] = BF ? ldcg_v4(mAb[k] + row * (unsigned)mJb[k] + j0) : ldcg_v4(mA[k] + row * (unsigned)mJp[k] + j0);
-          }
+      for (int u = 0; u < 2; ++u) {
+        const int i = i0 + u * T;
+        v[u] = 0.f;
+        if (i < cnt * sumJ) {
+          const int s = fdiv(i, f_sumJ), jj = i - s * sumJ;
+          const int k = rowtab[jj] & 0xff, j = rowtab[jj] >> 8;
+          const unsigned row = (unsigned)crd[s * N + k];
+          if (BF) v[u] = __uint_as_float((uint32_t)__ldcg(mAb[k] + row * (unsigned)mJb[k] + j) << 16);
+          else v[u] = __ldcg(mA[k] + row * (unsigned)mJp[k] + j);
         }
-#pragma unroll
-        for (int u = 0; u < 4; ++u)
-          if (e[u] >= 0) {
-            const int left = mJ[e[u] & 127] - (e[u] >> 8);
-            float* d = rows + dst[u];
-            if (BF) {
-              const uint32_t q[4] = {x[u].x, x[u].y, x[u].z, x[u].w};
-#pragma unroll
-              for (int h = 0; h < 8; ++h)
-                if (h < left) d[h] = __uint_as_float((h & 1) ? (q[h >> 1] & 0xffff0000u) : (q[h >> 1] << 16));
-            } else {
-              const uint32_t q[4] = {x[u].x, x[u].y, x[u].z, x[u].w};
-#pragma unroll
-              for (int h = 0; h < 4; ++h)
-                if (h < left) d[h] = __uint_as_float(q[h]);
-            }
-          }
       }
+#pragma unroll
+      for (int u = 0; u < 2; ++u)
+        if (i0 + u * T < cnt * sumJ) rows[i0 + u * T] = v[u];
     }
     __syncthreads();
     // lr_b = 0 leaves B unchanged: the core phase is skipped
@@ -1007,12 +960,17 @@ __device__ __forceinline__ void epoch_body(const EpochArgs& a, const int G, cons
         }
         __syncthreads();
         // Gram partial, thread tile = one left column x 4 right columns over
-        // the chunk, published as soon as it is summed
+        // the chunk (or over one of up to 3 sample slices, added in slice
+        // order), published as soon as it is summed
         {
           const float* rbase = right + mRoff[n];
           unsigned long long* dst = a.part + (unsigned)c * (unsigned)a.pstride;
+          const int nsl = L.gsplit ? gram_slices(ntile) : 1;
+          float4* gsp = reinterpret_cast<float4*>(sm + L.gsp);
+          const int cs = (cnt + nsl - 1) / nsl;
   #pragma unroll 1
-          for (int t = tid; t < ntile; t += T) {
+          for (int t0 = tid; t0 < nsl * ntile; t0 += T) {
+            const int sl = t0 / ntile, t = t0 - sl * ntile;
             int li, rc;
             if (t < R * na4) {
               const int r = fdiv(t, f_na4), jg = t - r * na4;
@@ -1028,9 +986,10 @@ __device__ __forceinline__ void epoch_body(const EpochArgs& a, const int G, cons
             float4 x0 = make_float4(0.f, 0.f, 0.f, 0.f), x1 = x0;
             const float* lp = left + li;
             const float* rp = rbase + rc;
-            int s = 0;
+            const int se = min(cnt, (sl + 1) * cs);
+            int s = sl * cs;
   #pragma unroll 1
-            for (; s + 1 < cnt; s += 2) {
+            for (; s + 1 < se; s += 2) {
               const float l0 = lp[s * lw], l1 = lp[(s + 1) * lw];
               const float4 r0 = *reinterpret_cast<const float4*>(rp + s * rw);
               const float4 r1 = *reinterpret_cast<const float4*>(rp + (s + 1) * rw);
@@ -1039,14 +998,35 @@ __device__ __forceinline__ void epoch_body(const EpochArgs& a, const int G, cons
               x1.x = fmaf(l1, r1.x, x1.x); x1.y = fmaf(l1, r1.y, x1.y);
               x1.z = fmaf(l1, r1.z, x1.z); x1.w = fmaf(l1, r1.w, x1.w);
             }
-            if (s < cnt) {
+            if (s < se) {
               const float l0 = lp[s * lw];
               const float4 r0 = *reinterpret_cast<const float4*>(rp + s * rw);
               x0.x = fmaf(l0, r0.x, x0.x); x0.y = fmaf(l0, r0.y, x0.y);
               x0.z = fmaf(l0, r0.z, x0.z); x0.w = fmaf(l0, r0.w, x0.w);
             }
-            put_pair(dst + obase, tag, x0.x + x1.x, x0.y + x1.y);
-            put_pair(dst + obase + 2, tag, x0.z + x1.z, x0.w + x1.w);
+            const float4 x = make_float4(x0.x + x1.x, x0.y + x1.y, x0.z + x1.z, x0.w + x1.w);
+            if (nsl == 1) {
+              put_pair(dst + obase, tag, x.x, x.y);
+              put_pair(dst + obase + 2, tag, x.z, x.w);
+            } else if (sl > 0) {
+              gsp[(sl - 1) * ntile + t] = x;
+            } else {
+              gsp[(nsl - 1) * ntile + t] = x;   // slice 0 parks its sum after the others
+            }
+          }
+          if (nsl > 1) {
+            __syncthreads();
+  #pragma unroll 1
+            for (int t = tid; t < ntile; t += T) {
+              float4 x = gsp[(nsl - 1) * ntile + t];
+  #pragma unroll 1
+              for (int q = 1; q < nsl; ++q) {
+                const float4 y = gsp[(q - 1) * ntile + t];
+                x.x += y.x; x.y += y.y; x.z += y.z; x.w += y.w;
+              }
+              put_pair(dst + 4 * t, tag, x.x, x.y);
+              put_pair(dst + 4 * t + 2, tag, x.z, x.w);
+            }
           }
         }
         // hop 1: CTA c sums its slice of the payload (word pairs) over all CTAs
@@ -1287,43 +1267,34 @@ __device__ __forceinline__ void epoch_body(const EpochArgs& a, const int G, cons
       const uint32_t* fseg = reinterpret_cast<const uint32_t*>(scb[buf] + (N + 1) * chunk_max);
       const int* fl = scb[buf] + (N + 2) * chunk_max;
       // rows: modes k < n as updated earlier in this minibatch (tagged slots,
-      // through the links, as 16-byte word pairs), modes k >= n from A
-      // (16-byte loads); G_(n) and the run heads are built while the first
-      // loads are in flight
-      const int nvf = n > 0 ? mVc[n] : 0;
-      const int total = cnt * nvf;
-      const FastDiv fvf = mFv[n];
-      const int* vt = vtab + n * kVecItems;
-      const unsigned mst = (unsigned)(Jmax + (Jmax & 1));   // row-slot stride: pairs stay 16-byte aligned
-      uint4 x4[4];
-      ulonglong2 w4[4];
-      const unsigned long long* p4[4];
-      uint32_t t4[4];
-      bool two4[4];
-      int e4[4], d4[4];
+      // through the links), modes k >= n from A; G_(n) and the run heads are
+      // built while the first loads are in flight
+      const int total = n > 0 ? cnt * sumJ : 0;
+      unsigned long long w2[2];
+      const unsigned long long* p2[2];
+      uint32_t t2[2];
+      float v2[2];
       int i0 = tid;
 #pragma unroll 1
-      for (bool first = true; i0 < total || first; i0 += 4 * T, first = false) {
+      for (bool first = true; i0 < total || first; i0 += 2 * T, first = false) {
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
+        for (int u = 0; u < 2; ++u) {
           const int i = i0 + u * T;
-          p4[u] = nullptr;
-          e4[u] = -1;
-          t4[u] = 0u;
-          two4[u] = false;
+          p2[u] = nullptr;
+          w2[u] = 0ULL;
+          t2[u] = 0u;
+          v2[u] = 0.f;
           if (i < total) {
-            const int s = fdiv(i, fvf);
-            e4[u] = vt[i - s * nvf];
-            const int k = e4[u] & 127, j0 = e4[u] >> 8;
-            d4[u] = s * sumJ + mJoff[k] + j0;
-            if (e4[u] & 128) {
-              p4[u] = a.mail + ((unsigned)k * (unsigned)M + (unsigned)fl[s * N + k]) * mst + j0;
-              w4[u] = get_pair(p4[u]);
-              t4[u] = tag0 + (uint32_t)k;
-              two4[u] = j0 + 1 < mJ[k];
+            const int s = fdiv(i, f_sumJ), jj = i - s * sumJ;
+            const int k = rowtab[jj] & 0xff, j = rowtab[jj] >> 8;
+            if (k < n) {
+              p2[u] = a.mail + ((unsigned)k * (unsigned)M + (unsigned)fl[s * N + k]) * (unsigned)(Jmax + (Jmax & 1)) + j;
+              w2[u] = get_word(p2[u]);
+              t2[u] = tag0 + (uint32_t)k;
             } else {
               const unsigned row = (unsigned)fcrd[s * N + k];
-              x4[u] = BF ? ldcg_v4(mAb[k] + row * (unsigned)mJb[k] + j0) : ldcg_v4(mA[k] + row * (unsigned)mJp[k] + j0);
+              if (BF) v2[u] = __uint_as_float((uint32_t)__ldcg(mAb[k] + row * (unsigned)mJb[k] + j) << 16);
+              else v2[u] = __ldcg(mA[k] + row * (unsigned)mJp[k] + j);
             }
           }
         }
@@ -1383,28 +1354,12 @@ __device__ __forceinline__ void epoch_body(const EpochArgs& a, const int G, cons
             }
           }
         }
-        if (ok) ok = wait_pairs_tagged<4>(p4, w4, t4, two4, a);
+        if (ok) ok = wait_all<2>(p2, w2, t2, a);
 #pragma unroll
-        for (int u = 0; u < 4; ++u)
-          if (e4[u] >= 0) {
-            float* d = rows + d4[u];
-            if (p4[u]) {
-              d[0] = BF ? bf16_round(val_of(w4[u].x)) : val_of(w4[u].x);
-              if (two4[u]) d[1] = BF ? bf16_round(val_of(w4[u].y)) : val_of(w4[u].y);
-            } else {
-              const int left = mJ[e4[u] & 127] - (e4[u] >> 8);
-              const uint32_t q[4] = {x4[u].x, x4[u].y, x4[u].z, x4[u].w};
-              if (BF) {
-#pragma unroll
-                for (int h = 0; h < 8; ++h)
-                  if (h < left) d[h] = __uint_as_float((h & 1) ? (q[h >> 1] & 0xffff0000u) : (q[h >> 1] << 16));
-              } else {
-#pragma unroll
-                for (int h = 0; h < 4; ++h)
-                  if (h < left) d[h] = __uint_as_float(q[h]);
-              }
-            }
-          }
+        for (int u = 0; u < 2; ++u) {
+          const int i = i0 + u * T;
+          if (i < total) rows[i] = p2[u] ? (BF ? bf16_round(val_of(w2[u])) : val_of(w2[u])) : v2[u];
+        }
       }
       if (!__syncthreads_and(ok)) return;
       const int nheads = s_nheads;
@@ -1551,19 +1506,31 @@ __device__ __forceinline__ void epoch_body(const EpochArgs& a, const int G, cons
           contract_fp32<1>(cnt, Jn, Pn, Pp, full_s, GT, Sbuf, rows, sumJ, mJoff[n], cdn, nm1, fx, qbuf, Jmax, tid, T);
       }
       __syncthreads();
-      // run sums in sorted order (warp per run piece, lane j), kept in the
-      // run head's row of qbuf; the piece of a run begun in an earlier chunk
-      // is published
+      // run sums (warp per run piece): the warp's 32 / J_n lane groups take
+      // every sub-th sample of the run (lane j of a group sums column j), then
+      // group 0 adds the groups' sums in group order; kept in the run head's
+      // row of qbuf; the piece of a run begun in an earlier chunk is published
+      {
+        const int nsub = 32 / Jn;
+        const int sub = lane / Jn, j = lane - sub * Jn;
 #pragma unroll 1
-      for (int h = warp; h < nheads; h += nwarps)
-        if (lane < Jn) {
+        for (int h = warp; h < nheads; h += nwarps) {
           const int s0 = head[h], s1 = head[h + 1];
           float F = 0.f;
+          if (sub < nsub)
 #pragma unroll 1
-          for (int s = s0; s < s1; ++s) F += qbuf[s * Jmax + lane];
-          qbuf[s0 * Jmax + lane] = F;
-          if ((int)(fseg[s0] & 0xffffu) < lo) put_word(a.piece + ((unsigned)n * G + c) * (unsigned)Jmax + lane, tag, F);
+            for (int s = s0 + sub; s < s1; s += nsub) F += qbuf[s * Jmax + j];
+#pragma unroll 1
+          for (int g = 1; g < nsub; ++g) {
+            const float o = __shfl_sync(0xffffffffu, F, (lane + g * Jn) & 31);
+            if (sub == 0) F += o;
+          }
+          if (lane < Jn) {
+            qbuf[s0 * Jmax + lane] = F;
+            if ((int)(fseg[s0] & 0xffffu) < lo) put_word(a.piece + ((unsigned)n * G + c) * (unsigned)Jmax + lane, tag, F);
+          }
         }
+      }
       // a run begun here that continues: the pieces of chunks c+1 .. c1,
       // polled in parallel
       const uint32_t seg_last = cnt > 0 ? fseg[head[nheads - 1]] : 0u;

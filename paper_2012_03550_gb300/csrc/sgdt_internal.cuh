@@ -99,7 +99,9 @@ struct Geometry {
 //                    the start of the mode-k run that holds the same sample
 //                    (sorted position in the mode-k copy of the minibatch)
 // and sid[t] the training-entry index pi_e(t).  rsp[k][t] (k < N - 1) is the
-// tiler's scratch: the mode-k run start of batch position t - bM.
+// tiler's scratch: the mode-k run start of batch position t - bM.  The arrays
+// hold the minibatches from b_first on: position t is stored at index
+// t - b_first * M (npad positions in all).
 struct Schedule {
   int32_t* crd;
   float* val;
@@ -111,6 +113,7 @@ struct Schedule {
   int64_t npad;
   int64_t n;
   int M;
+  int64_t b_first;
 };
 
 // Words per epoch position of a Schedule of order N.

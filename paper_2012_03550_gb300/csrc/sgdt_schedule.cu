@@ -32,12 +32,13 @@ k_schedule(Geometry g, const uint32_t* __restrict__ coo, int cs, Feistel f, Sche
 
   const int64_t b = b0 + blockIdx.x;
   const int64_t t0 = b * (int64_t)M;
+  const int64_t tb = s.b_first * (int64_t)M;   // storage index = position - tb
   const int m = (int)((s.n - t0) < (int64_t)M ? (s.n - t0) : (int64_t)M);
 
   for (int q = threadIdx.x; q < m; q += blockDim.x) {
     const uint64_t y = feistel_perm(f, (uint64_t)(t0 + q));
     sid[q] = (int32_t)y;
-    s.sid[t0 + q] = (int32_t)y;
+    s.sid[t0 + q - tb] = (int32_t)y;
   }
   __syncthreads();
 
@@ -86,17 +87,17 @@ k_schedule(Geometry g, const uint32_t* __restrict__ coo, int cs, Feistel f, Sche
       }
       const int end = lo;
       const uint32_t* e = coo + (size_t)sid[pos] * cs;
-      const size_t t = (size_t)(t0 + q);
+      const size_t t = (size_t)(t0 + q - tb);
       for (int k = 0; k < g.N; ++k) s.crd[((size_t)n * g.N + k) * s.npad + t] = (int32_t)e[k];
       s.val[(size_t)n * s.npad + t] = __uint_as_float(e[g.N]);
       s.pos[(size_t)n * s.npad + t] = pos;
       s.seg[(size_t)n * s.npad + t] = (uint32_t)start | ((uint32_t)end << 16);
-      if (n + 1 < g.N) s.rsp[(size_t)n * s.npad + (size_t)(t0 + pos)] = start;
+      if (n + 1 < g.N) s.rsp[(size_t)n * s.npad + (size_t)(t0 + pos - tb)] = start;
       // modes k < n were sorted in earlier passes of this CTA, which wrote
       // rsp[k]; the pass-ending __syncthreads orders those writes before
       // these reads
       for (int k = 0; k < n; ++k)
-        s.link[(size_t)(n * (n - 1) / 2 + k) * s.npad + t] = s.rsp[(size_t)k * s.npad + (size_t)(t0 + pos)];
+        s.link[(size_t)(n * (n - 1) / 2 + k) * s.npad + t] = s.rsp[(size_t)k * s.npad + (size_t)(t0 + pos - tb)];
     }
     __syncthreads();
   }

@@ -608,3 +608,44 @@ def test_step_gradients_at_declared_limits(B, synth, shape, ranks, R, M, nnz):
     t = synth.make_tensor(shape, nnz, [("uniform",)] * len(shape), tuple(min(j, 4) for j in ranks), 0.1, 0.0,
                           seed=37)
     _step_case(B, synth, t, ranks, R, M, batch=0)
+
+
+def test_epoch_spanning_schedule_segments(B, synth):
+    """An epoch longer than one schedule segment (2^20 positions: 256
+    minibatches of 4096) is scheduled and run segment after segment: RMSE
+    parity with the oracle over two epochs, and the context holds one
+    segment's schedule instead of the epoch's."""
+    w = synth.config2(scale=0.011)          # 1.089M training nonzeros: 266 minibatches, two segments
+    t = w.tensor
+    c, v = t.split("train")
+    tc, tv = t.split("test")
+    assert c.shape[0] > (1 << 20)
+    A0, B0 = synth.init_params(t.shape, w.ranks, w.r_core, mode="rating", seed=1, mean_value=float(np.mean(v)))
+    ref = O.Model(t.shape, w.ranks, w.r_core, A0, B0)
+    worst = 0.0
+    with _gpu(B, t.shape, w.ranks, w.r_core, c, v, A0, B0) as g:
+        for ep in range(2):
+            st = g.epoch(w.lr, w.lr, w.lam, w.lam, 4096)
+            assert st["batches"] == (c.shape[0] + 4095) // 4096
+            ref.epoch(c, v, 4096, 2, ep, w.lr, w.lr, w.lam, w.lam)
+            for cc, vv in ((c, v), (tc, tv)):
+                r_g, m_g = g.rmse(cc, vv)
+                r_o, m_o = ref.rmse_mae(cc, vv)
+                worst = max(worst, abs(r_g - r_o), abs(m_g - m_o))
+    assert worst <= 1e-3, worst
+
+
+def test_epoch_holds_one_schedule_segment(B, synth):
+    """std_sgd_epoch keeps one segment's schedule (2^20 positions) on the
+    device; a batched-launch reservation needs the whole epoch's."""
+    w = synth.config2(scale=0.05)           # 4.95M training nonzeros: 1,209 minibatches, five segments
+    t = w.tensor
+    c, v = t.split("train")
+    with B.Tucker(t.shape, w.ranks, c, v, r_core=w.r_core) as g:
+        g.epoch(w.lr, w.lr, w.lam, w.lam, 4096)
+        held = g.device_bytes()
+        g.reserve(4096, 16)
+        whole = g.device_bytes()
+    nb = (c.shape[0] + 4095) // 4096
+    words = 24                                          # schedule words per position of a 3-order tensor
+    assert whole - held == (nb - 256) * 4096 * words * 4, (held, whole)
