@@ -155,7 +155,7 @@ __host__ __device__ inline int fp32_row_stride(int Pn) {
 struct SmemLayout {
   int B, VB, Bs, G, GT, GTh, Sh, S, ldig, cdig, rowtab, trij, sc[2], rows, master, p, left, right, red, D, q,
       head, fown, pbuf, gsp, total_words;
-  int lw, rw, sfloats, rpre, ldig_on, gsplit;
+  int lw, rw, sfloats, rpre, ldig_on, gsplit, srows;
 };
 
 // Words of one phase's schedule chunk: coordinates [s][N], value, run
@@ -163,9 +163,12 @@ struct SmemLayout {
 __host__ __device__ inline int sched_chunk_words(int N, int chunk) { return (2 * N + 2) * chunk; }
 
 // Layout variant v: 0 = right Gram operands of all modes precomputed once per
-// minibatch and all Kronecker rows materialised; 1 = right operands rebuilt
-// per mode; 2 = also Kronecker entries formed on the fly in the contraction.
-__host__ __device__ inline SmemLayout smem_layout_v(const Geometry& g, int chunk, int ctas, int precision, int v) {
+// minibatch; 1 = right operands rebuilt per mode.  srows: Kronecker rows
+// materialised at once (the factor-phase contraction walks the chunk in
+// pieces of srows samples); 0 = Kronecker entries formed on the fly in the
+// contraction (FP32 form only).
+__host__ __device__ inline SmemLayout smem_layout_v(const Geometry& g, int chunk, int ctas, int precision, int v,
+                                                    int srows) {
   SmemLayout L;
   int off = 0;
   auto take = [&](int words) {
@@ -186,7 +189,9 @@ __host__ __device__ inline SmemLayout smem_layout_v(const Geometry& g, int chunk
   L.rpre = (v == 0 && chunk * rwall <= kRightBudget) ? 1 : 0;
   L.rw = L.rpre ? rwall : rwmax;
   const int spmax = fp32_row_stride(Pmax);
-  L.sfloats = (bf || v == 2) ? 0 : (chunk * spmax < kSBudget ? chunk * spmax : kSBudget);
+  if (!bf && srows * spmax > kSBudget) srows = kSBudget / spmax;
+  L.srows = srows;
+  L.sfloats = bf ? 0 : srows * spmax;
   const int kpmax = bf16_row_stride(Pmax);
   // the unfolded core of one mode at a time: J_n rows of P_n (padded) columns
   int gt32 = 0, gt16 = 0;
@@ -203,7 +208,7 @@ __host__ __device__ inline SmemLayout smem_layout_v(const Geometry& g, int chunk
   L.G = take(g.prodJ);
   L.GT = take(bf ? 0 : gt32);
   L.GTh = take(bf ? gt16 : 0);
-  L.Sh = take(bf ? round_up(chunk, 16) * kpmax / 2 : 0);
+  L.Sh = take(bf ? round_up(srows, 16) * kpmax / 2 : 0);
   L.S = take(L.sfloats);
   L.ldig = take(L.ldig_on ? g.prodJ : 0);
   L.cdig = take(2 * sum_pn(g));
@@ -240,9 +245,12 @@ __host__ __device__ inline SmemLayout smem_layout_v(const Geometry& g, int chunk
 
 // The first variant whose shared memory fits a CTA.
 __host__ __device__ inline SmemLayout smem_layout(const Geometry& g, int chunk, int ctas, int precision) {
-  SmemLayout L = smem_layout_v(g, chunk, ctas, precision, 0);
-  if (L.total_words * 4 > kMaxSmemBytes) L = smem_layout_v(g, chunk, ctas, precision, 1);
-  if (L.total_words * 4 > kMaxSmemBytes) L = smem_layout_v(g, chunk, ctas, precision, 2);
+  SmemLayout L = smem_layout_v(g, chunk, ctas, precision, 0, chunk);
+  if (L.total_words * 4 > kMaxSmemBytes) L = smem_layout_v(g, chunk, ctas, precision, 1, chunk);
+  // fewer Kronecker rows at a time (multiples of 16), then none (FP32)
+  for (int sr = (chunk / 2 + 15) / 16 * 16; sr >= 16 && L.total_words * 4 > kMaxSmemBytes; sr = sr / 2 / 16 * 16)
+    L = smem_layout_v(g, chunk, ctas, precision, 1, sr);
+  if (L.total_words * 4 > kMaxSmemBytes && precision != 1) L = smem_layout_v(g, chunk, ctas, precision, 1, 0);
   return L;
 }
 
@@ -1377,7 +1385,7 @@ __device__ __forceinline__ void epoch_body(const EpochArgs& a, const int G, cons
       // Kronecker rows S_s (Eq. 10), warp per sample, lanes over columns
       const int nm1 = N - 1;
       const bool kru = a.contraction == 1;
-      const bool full_s = BF || cnt * Pp <= L.sfloats;
+      const bool full_s = BF || L.srows > 0;
       if (kru) {
         // Kruskal form of the same contraction (Eq. 4 in Eq. 11):
         // E_s = G_(n) S_s^T = B(n) w_s, w_s[r] = prod_{k != n} <a_k(s), b(k)_r>;
@@ -1414,96 +1422,111 @@ __device__ __forceinline__ void epoch_body(const EpochArgs& a, const int G, cons
           for (int off = 16; off > 0; off >>= 1) part += __shfl_xor_sync(0xffffffffu, part, off);
           if (lane < Jn) qbuf[s * Jmax + lane] = (part - fx[s]) * E;
         }
-      } else if (BF) {
-        // (the K extent P_n rounded up to 16 is all the tiles read)
-        const int KP = bf16_row_stride(Pn);
-        const int Kext = round_up(Pn, 16);
-#pragma unroll 1
-        for (int s = warp; s < round_up(cnt, 16); s += nwarps) {
-          const float* rs = rows + s * sumJ;
-#pragma unroll 1
-          for (int cc = lane; cc < Kext; cc += 64) {
-            const int c2 = cc + 32;
-            const float v0 = (s < cnt && cc < Pn) ? kron_entry(rs, cdn[cc], nm1) : 0.f;
-            const float v1 = (s < cnt && c2 < Pn) ? kron_entry(rs, cdn[c2], nm1) : 0.f;
-            Sh[s * KP + cc] = __float2bfloat16_rn(v0);
-            if (c2 < Kext) Sh[s * KP + c2] = __float2bfloat16_rn(v1);
-          }
-        }
-      } else if (full_s) {
-#pragma unroll 1
-        for (int s = warp; s < cnt; s += nwarps) {
-          const float* rs = rows + s * sumJ;
-#pragma unroll 1
-          for (int cc = lane; cc < Pp; cc += 64) {
-            const int c2 = cc + 32;
-            const float v0 = cc < Pn ? kron_entry(rs, cdn[cc], nm1) : 0.f;
-            const float v1 = c2 < Pn ? kron_entry(rs, cdn[c2], nm1) : 0.f;
-            Sbuf[s * Pp + cc] = v0;
-            if (c2 < Pp) Sbuf[s * Pp + c2] = v1;
-          }
-        }
       }
-      __syncthreads();
       if (kru) {
-        // E_s and the contributions were formed above
-      } else if (BF) {
-        // Tensor-core contraction: E (samples x J_n) = S (samples x P_n) .
-        // G_(n)^T with BF16 operands and FP32 accumulation, mma.sync
-        // m16n8k16 tiles (one warp per 16 x 8 output tile, full K).
-        const int KP = bf16_row_stride(Pn);
-        const int mt = round_up(cnt, 16) >> 4, ntl = (Jn + 7) >> 3, ksteps = round_up(Pn, 16) >> 4;
-        const int gq = lane >> 2, tq = lane & 3;
-#pragma unroll 1
-        for (int w = warp; w < mt * ntl; w += nwarps) {
-          const int mi = w / ntl, ni = w - mi * ntl;
-          const uint32_t* A0 = reinterpret_cast<const uint32_t*>(Sh + (mi * 16 + gq) * KP);
-          const uint32_t* A1 = reinterpret_cast<const uint32_t*>(Sh + (mi * 16 + gq + 8) * KP);
-          const uint32_t* Bq = reinterpret_cast<const uint32_t*>(GTh + (ni * 8 + gq) * KP);
-          float d[4] = {0.f, 0.f, 0.f, 0.f};
-#pragma unroll 1
-          for (int ks = 0; ks < ksteps; ++ks) {
-            const int kw = ks * 8 + tq;
-            mma_bf16_16816(d, A0[kw], A1[kw], A0[kw + 4], A1[kw + 4], Bq[kw], Bq[kw + 4]);
-          }
-          const int s0 = mi * 16 + gq, j0 = ni * 8 + 2 * tq;
-          if (s0 < cnt) {
-            if (j0 < Jn) qbuf[s0 * Jmax + j0] = d[0];
-            if (j0 + 1 < Jn) qbuf[s0 * Jmax + j0 + 1] = d[1];
-          }
-          if (s0 + 8 < cnt) {
-            if (j0 < Jn) qbuf[(s0 + 8) * Jmax + j0] = d[2];
-            if (j0 + 1 < Jn) qbuf[(s0 + 8) * Jmax + j0 + 1] = d[3];
-          }
-        }
-        __syncthreads();
-        // residual e_s = a_n . E_s - x_s (8 lanes per sample), contributions in place
-#pragma unroll 1
-        for (int base = 0; base < cnt * 8; base += T) {
-          const int t8 = base + tid, s = t8 >> 3, l = t8 & 7;
-          const bool live = s < cnt;
-          float part = 0.f;
-          if (live) {
-            const float* an = rows + s * sumJ + mJoff[n];
-#pragma unroll 1
-            for (int j = l; j < Jn; j += 8) part = fmaf(an[j], qbuf[s * Jmax + j], part);
-          }
-          part += __shfl_xor_sync(0xffffffffu, part, 4);
-          part += __shfl_xor_sync(0xffffffffu, part, 2);
-          part += __shfl_xor_sync(0xffffffffu, part, 1);
-          if (live) {
-            const float e = part - fx[s];
-#pragma unroll 1
-            for (int j = l; j < Jn; j += 8) qbuf[s * Jmax + j] *= e;
-          }
-        }
+        __syncthreads();   // E_s and the contributions were formed above
       } else {
-        // four samples per thread when that still fills half the block
-        const int JL = pow2_at_least(Jn);
-        if (((cnt + 3) >> 2) * JL >= (T >> 1))
-          contract_fp32<4>(cnt, Jn, Pn, Pp, full_s, GT, Sbuf, rows, sumJ, mJoff[n], cdn, nm1, fx, qbuf, Jmax, tid, T);
-        else
-          contract_fp32<1>(cnt, Jn, Pn, Pp, full_s, GT, Sbuf, rows, sumJ, mJoff[n], cdn, nm1, fx, qbuf, Jmax, tid, T);
+        // the chunk in pieces of srows samples (one piece when they all fit):
+        // Kronecker rows of the piece, then its contraction
+        const int piece = full_s ? (L.srows < cnt ? L.srows : cnt) : cnt;
+#pragma unroll 1
+        for (int sa = 0; sa < cnt || sa == 0; sa += (piece > 0 ? piece : 1)) {
+          const int pc = cnt - sa < piece ? cnt - sa : piece;
+          const float* prow = rows + sa * sumJ;
+          const float* pfx = fx + sa;
+          float* pq = qbuf + sa * Jmax;
+          if (sa > 0) __syncthreads();   // the previous piece's tiles are no longer read
+          if (BF) {
+            // (the K extent P_n rounded up to 16 is all the tiles read)
+            const int KP = bf16_row_stride(Pn);
+            const int Kext = round_up(Pn, 16);
+#pragma unroll 1
+            for (int s = warp; s < round_up(pc, 16); s += nwarps) {
+              const float* rs = prow + s * sumJ;
+#pragma unroll 1
+              for (int cc = lane; cc < Kext; cc += 64) {
+                const int c2 = cc + 32;
+                const float v0 = (s < pc && cc < Pn) ? kron_entry(rs, cdn[cc], nm1) : 0.f;
+                const float v1 = (s < pc && c2 < Pn) ? kron_entry(rs, cdn[c2], nm1) : 0.f;
+                Sh[s * KP + cc] = __float2bfloat16_rn(v0);
+                if (c2 < Kext) Sh[s * KP + c2] = __float2bfloat16_rn(v1);
+              }
+            }
+          } else if (full_s) {
+#pragma unroll 1
+            for (int s = warp; s < pc; s += nwarps) {
+              const float* rs = prow + s * sumJ;
+#pragma unroll 1
+              for (int cc = lane; cc < Pp; cc += 64) {
+                const int c2 = cc + 32;
+                const float v0 = cc < Pn ? kron_entry(rs, cdn[cc], nm1) : 0.f;
+                const float v1 = c2 < Pn ? kron_entry(rs, cdn[c2], nm1) : 0.f;
+                Sbuf[s * Pp + cc] = v0;
+                if (c2 < Pp) Sbuf[s * Pp + c2] = v1;
+              }
+            }
+          }
+          __syncthreads();
+          if (BF) {
+            // Tensor-core contraction: E (samples x J_n) = S (samples x P_n) .
+            // G_(n)^T with BF16 operands and FP32 accumulation, mma.sync
+            // m16n8k16 tiles (one warp per 16 x 8 output tile, full K).
+            const int KP = bf16_row_stride(Pn);
+            const int mt = round_up(pc, 16) >> 4, ntl = (Jn + 7) >> 3, ksteps = round_up(Pn, 16) >> 4;
+            const int gq = lane >> 2, tq = lane & 3;
+#pragma unroll 1
+            for (int w = warp; w < mt * ntl; w += nwarps) {
+              const int mi = w / ntl, ni = w - mi * ntl;
+              const uint32_t* A0 = reinterpret_cast<const uint32_t*>(Sh + (mi * 16 + gq) * KP);
+              const uint32_t* A1 = reinterpret_cast<const uint32_t*>(Sh + (mi * 16 + gq + 8) * KP);
+              const uint32_t* Bq = reinterpret_cast<const uint32_t*>(GTh + (ni * 8 + gq) * KP);
+              float d[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll 1
+              for (int ks = 0; ks < ksteps; ++ks) {
+                const int kw = ks * 8 + tq;
+                mma_bf16_16816(d, A0[kw], A1[kw], A0[kw + 4], A1[kw + 4], Bq[kw], Bq[kw + 4]);
+              }
+              const int s0 = mi * 16 + gq, j0 = ni * 8 + 2 * tq;
+              if (s0 < pc) {
+                if (j0 < Jn) pq[s0 * Jmax + j0] = d[0];
+                if (j0 + 1 < Jn) pq[s0 * Jmax + j0 + 1] = d[1];
+              }
+              if (s0 + 8 < pc) {
+                if (j0 < Jn) pq[(s0 + 8) * Jmax + j0] = d[2];
+                if (j0 + 1 < Jn) pq[(s0 + 8) * Jmax + j0 + 1] = d[3];
+              }
+            }
+            __syncthreads();
+            // residual e_s = a_n . E_s - x_s (8 lanes per sample), contributions in place
+#pragma unroll 1
+            for (int base = 0; base < pc * 8; base += T) {
+              const int t8 = base + tid, s = t8 >> 3, l = t8 & 7;
+              const bool live = s < pc;
+              float part = 0.f;
+              if (live) {
+                const float* an = prow + s * sumJ + mJoff[n];
+#pragma unroll 1
+                for (int j = l; j < Jn; j += 8) part = fmaf(an[j], pq[s * Jmax + j], part);
+              }
+              part += __shfl_xor_sync(0xffffffffu, part, 4);
+              part += __shfl_xor_sync(0xffffffffu, part, 2);
+              part += __shfl_xor_sync(0xffffffffu, part, 1);
+              if (live) {
+                const float e = part - pfx[s];
+#pragma unroll 1
+                for (int j = l; j < Jn; j += 8) pq[s * Jmax + j] *= e;
+              }
+            }
+          } else {
+            // four samples per thread when that still fills half the block
+            const int JL = pow2_at_least(Jn);
+            if (((pc + 3) >> 2) * JL >= (T >> 1))
+              contract_fp32<4>(pc, Jn, Pn, Pp, full_s, GT, Sbuf, prow, sumJ, mJoff[n], cdn, nm1, pfx, pq, Jmax, tid, T);
+            else
+              contract_fp32<1>(pc, Jn, Pn, Pp, full_s, GT, Sbuf, prow, sumJ, mJoff[n], cdn, nm1, pfx, pq, Jmax, tid, T);
+          }
+          if (pc <= 0) break;
+        }
       }
       __syncthreads();
       // run sums (warp per run piece): the warp's 32 / J_n lane groups take
