@@ -415,6 +415,16 @@ int run_batches(std_ctx* c, float lr_a, float lr_b, float lam_a, float lam_b, in
     rc = choose_ctas(c, M, &G, &chunk, &smem);
   }
   if (rc) return rc;
+  // groups of 2..16 CTAs run as one thread block cluster (same results as the
+  // cooperative form, exchanges through cluster barriers and shared memory)
+  bool cl = false;
+  if (K < 2 && epoch_cluster_size_ok(G)) {
+    const size_t smc = epoch_smem_bytes_cl(c->g, chunk, G, c->opt.precision);
+    if (smc <= 227 * 1024 && epoch_cl_max_clusters(c->opt.precision, false, smc, G) >= 1) {
+      cl = true;
+      smem = smc;
+    }
+  }
   rc = ensure_scratch(c, G, payload_floats(c->g), M * K);
   if (rc) return rc;
   if (K >= 2) {
@@ -467,6 +477,8 @@ int run_batches(std_ctx* c, float lr_a, float lr_b, float lam_a, float lam_b, in
       a.snap_count = c->snap_count;
       STD_CUDA(cudaMemsetAsync(c->snap_count, 0, (size_t)G * K * sizeof(int), c->stream), "snapshot counts");
       STD_CUDA(launch_epoch_snap(a, G, smem, c->stream), "snapshot kernel launch");
+    } else if (cl) {
+      STD_CUDA(launch_epoch_cl(a, G, smem, c->stream), "cluster epoch kernel launch");
     } else {
       STD_CUDA(launch_epoch(a, G, smem, c->stream), "epoch kernel launch");
     }
@@ -991,6 +1003,7 @@ struct std_batch {
   int* d_order = nullptr;
   int* d_first = nullptr;
   int* d_gstart = nullptr;
+  int* d_gstart_cl = nullptr;   // cluster form: each size class's group starts, from 0
   size_t cap_items = 0, cap_groups = 0;
   // pinned host staging of the launch arguments (fixed addresses, so that a
   // captured graph copies their current contents at every replay)
@@ -998,7 +1011,11 @@ struct std_batch {
   int* h_order = nullptr;
   int* h_first = nullptr;
   int* h_gstart = nullptr;
+  int* h_gstart_cl = nullptr;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr, evm = nullptr;
+  // cluster form: one launch per group size, on forked streams of the capture
+  cudaStream_t fork[8] = {};
+  cudaEvent_t ev_fork = nullptr, ev_join[8] = {};
   // the launch sequence (barrier resets, argument uploads, the cooperative
   // kernel) captured as a CUDA graph and replayed while its shape holds
   cudaStream_t cap_stream = nullptr;
@@ -1006,6 +1023,7 @@ struct std_batch {
   std::vector<std_ctx*> gkey_ctxs;
   int gkey_ctas = 0, gkey_groups = 0;
   size_t gkey_smem = 0;
+  std::vector<std::pair<int, int>> gkey_classes;   // cluster form: (size, groups) per launch; empty = cooperative
   const void* gkey_items = nullptr;
   bool replayed = false;   // the last launch replayed the graph
 };
@@ -1014,10 +1032,11 @@ namespace {
 
 // Smallest chunk a CTA of the batched kernel handles for tensor c at group
 // size G, or 0 when the shape does not fit a CTA.
-size_t batch_smem(std_ctx* c, int M, int G) {
+size_t batch_smem(std_ctx* c, int M, int G, bool cl = false) {
   const int chunk = (M + G - 1) / G;
   if (chunk > epoch_chunk_cap(c->g)) return 0;
-  const size_t sm = epoch_smem_bytes(c->g, chunk, G, c->opt.precision);
+  const size_t sm = cl ? epoch_smem_bytes_cl(c->g, chunk, G, c->opt.precision)
+                       : epoch_smem_bytes(c->g, chunk, G, c->opt.precision);
   return sm > 227 * 1024 ? 0 : sm;
 }
 
@@ -1040,10 +1059,14 @@ int batch_launch(std_batch* bt, float lr_a, float lr_b, float lam_a, float lam_b
     cudaFree(bt->d_order);
     cudaFree(bt->d_first);
     cudaFree(bt->d_gstart);
+    cudaFree(bt->d_gstart_cl);
     cudaFreeHost(bt->h_items);
     cudaFreeHost(bt->h_order);
     cudaFreeHost(bt->h_first);
     cudaFreeHost(bt->h_gstart);
+    cudaFreeHost(bt->h_gstart_cl);
+    bt->d_gstart_cl = nullptr;
+    bt->h_gstart_cl = nullptr;
     bt->d_items = nullptr;
     bt->d_order = nullptr;
     bt->d_first = nullptr;
@@ -1062,12 +1085,15 @@ int batch_launch(std_batch* bt, float lr_a, float lr_b, float lam_a, float lam_b
     STD_CUDA(cudaMallocHost((void**)&bt->h_order, ci * sizeof(int)), "batch order (host)");
     STD_CUDA(cudaMallocHost((void**)&bt->h_first, cg * sizeof(int)), "batch groups (host)");
     STD_CUDA(cudaMallocHost((void**)&bt->h_gstart, cg * sizeof(int)), "batch group starts (host)");
+    STD_CUDA(cudaMalloc((void**)&bt->d_gstart_cl, (cg + 8) * sizeof(int)), "batch cluster group starts");
+    STD_CUDA(cudaMallocHost((void**)&bt->h_gstart_cl, (cg + 8) * sizeof(int)), "batch cluster group starts (host)");
     bt->cap_items = ci;
     bt->cap_groups = cg;
   }
   // work estimates and the base-size shared memory (a larger group has
   // smaller chunks, so the base size bounds every tensor's need)
   std::vector<int64_t> w(T), e0v(T), e1v(T);
+  size_t smem_cl = 0;
   for (int t = 0; t < T; ++t) {
     std_ctx* c = bt->ctxs[t];
     int rc = ensure_schedule(c, M);
@@ -1076,6 +1102,8 @@ int batch_launch(std_batch* bt, float lr_a, float lr_b, float lam_a, float lam_b
     const size_t sm = batch_smem(c, M, gown);
     if (sm == 0) return set_error(STD_EUNSUPPORTED, "a tensor of the batch does not fit a CTA at this group size");
     smem = sm > smem ? sm : smem;
+    const size_t smc = batch_smem(c, M, gown, true);
+    smem_cl = smc == 0 ? (size_t)-1 : (smc > smem_cl ? smc : smem_cl);
     const int64_t nb = (c->nnz + M - 1) / M;
     e0v[t] = range[t].first < nb ? range[t].first : nb;
     e1v[t] = range[t].second < nb ? range[t].second : nb;
@@ -1255,6 +1283,39 @@ int batch_launch(std_batch* bt, float lr_a, float lr_b, float lam_a, float lam_b
     if (dry) a.momentum = 0.f;
     bt->h_items[t] = a;
   }
+  // cluster form: every group one thread block cluster (2..16 CTAs, or a
+  // single CTA), one launch per group size; the groups are ordered by size so
+  // that each size's groups are consecutive.  Same results as the cooperative
+  // form, which takes over when a size is not a cluster size or clusters of
+  // it cannot be resident.
+  std::vector<std::pair<int, int>> classes;
+  {
+    bool ok = smem_cl <= (size_t)227 * 1024;
+    for (int q = 0; q < groups && ok; ++q) ok = gsize[q] == 1 || epoch_cluster_size_ok(gsize[q]);
+    if (ok) {
+      std::vector<int> idx(groups);
+      for (int q = 0; q < groups; ++q) idx[q] = q;
+      std::stable_sort(idx.begin(), idx.end(), [&](int x, int y) { return gsize[x] < gsize[y]; });
+      std::vector<std::vector<int>> l2(groups);
+      std::vector<int> g2(groups);
+      for (int q = 0; q < groups; ++q) {
+        l2[q] = lists[idx[q]];
+        g2[q] = gsize[idx[q]];
+      }
+      for (int q = 0; q < groups; ++q)
+        if (classes.empty() || classes.back().first != g2[q]) classes.push_back({g2[q], 1});
+        else classes.back().second += 1;
+      for (const auto& k : classes)
+        if (epoch_cl_max_clusters(bt->precision, true, smem_cl, k.first) < 1) ok = false;
+      if (ok && classes.size() <= 8) {
+        lists.swap(l2);
+        gsize.swap(g2);
+      } else {
+        classes.clear();
+      }
+    }
+  }
+  if (!classes.empty()) smem = smem_cl;
   int no = 0;
   bt->h_first[0] = 0;
   bt->h_gstart[0] = 0;
@@ -1263,13 +1324,22 @@ int batch_launch(std_batch* bt, float lr_a, float lr_b, float lam_a, float lam_b
     bt->h_first[q + 1] = no;
     bt->h_gstart[q + 1] = bt->h_gstart[q] + gsize[q];
   }
+  {
+    int at = 0, q0 = 0;
+    for (const auto& k : classes) {
+      for (int j = 0; j <= k.second; ++j) bt->h_gstart_cl[at + j] = j * k.first;
+      at += k.second + 1;
+      q0 += k.second;
+    }
+  }
   const int ctas = bt->h_gstart[groups];
   // (re)capture the launch sequence when its shape changed: the tensors (their
   // barrier words), the group size, the group count, the shared memory and
   // the argument buffers; otherwise replay it (the copies read the pinned
   // staging, so the new ranges, order and flags reach the device)
   const bool same = bt->gexec && bt->gkey_ctxs == bt->ctxs && bt->gkey_ctas == ctas && bt->gkey_groups == groups &&
-                    bt->gkey_smem == smem && bt->gkey_items == (const void*)bt->d_items;
+                    bt->gkey_smem == smem && bt->gkey_items == (const void*)bt->d_items &&
+                    bt->gkey_classes == classes;
   bt->replayed = same;
   if (!same) {
     if (bt->gexec) cudaGraphExecDestroy(bt->gexec);
@@ -1289,7 +1359,10 @@ int batch_launch(std_batch* bt, float lr_a, float lr_b, float lam_a, float lam_b
     if (e == cudaSuccess)
       e = cudaMemcpyAsync(bt->d_gstart, bt->h_gstart, (size_t)(groups + 1) * sizeof(int), cudaMemcpyHostToDevice,
                           cs);
-    if (e == cudaSuccess) {
+    if (e == cudaSuccess && !classes.empty())
+      e = cudaMemcpyAsync(bt->d_gstart_cl, bt->h_gstart_cl, (size_t)(groups + classes.size()) * sizeof(int),
+                          cudaMemcpyHostToDevice, cs);
+    if (e == cudaSuccess && classes.empty()) {
       MultiArgs m{};
       m.items = bt->d_items;
       m.order = bt->d_order;
@@ -1297,6 +1370,30 @@ int batch_launch(std_batch* bt, float lr_a, float lr_b, float lam_a, float lam_b
       m.gstart = bt->d_gstart;
       m.groups = groups;
       e = launch_epoch_multi(m, bt->precision, ctas, smem, cs);
+    } else if (e == cudaSuccess) {
+      // one cluster launch per group size, the sizes in parallel branches
+      if (!bt->ev_fork) e = cudaEventCreateWithFlags(&bt->ev_fork, cudaEventDisableTiming);
+      for (size_t k = 1; k < classes.size() && e == cudaSuccess; ++k) {
+        if (!bt->fork[k]) e = cudaStreamCreateWithFlags(&bt->fork[k], cudaStreamNonBlocking);
+        if (e == cudaSuccess && !bt->ev_join[k]) e = cudaEventCreateWithFlags(&bt->ev_join[k], cudaEventDisableTiming);
+      }
+      if (e == cudaSuccess) e = cudaEventRecord(bt->ev_fork, cs);
+      int q0 = 0, at = 0;
+      for (size_t k = 0; k < classes.size() && e == cudaSuccess; ++k) {
+        cudaStream_t sk = k == 0 ? cs : bt->fork[k];
+        if (k > 0) e = cudaStreamWaitEvent(sk, bt->ev_fork, 0);
+        MultiArgs m{};
+        m.items = bt->d_items;
+        m.order = bt->d_order;
+        m.first = bt->d_first + q0;
+        m.gstart = bt->d_gstart_cl + at;
+        m.groups = classes[k].second;
+        if (e == cudaSuccess) e = launch_epoch_multi_cl(m, bt->precision, classes[k].first, smem, sk);
+        if (e == cudaSuccess && k > 0) e = cudaEventRecord(bt->ev_join[k], sk);
+        q0 += classes[k].second;
+        at += classes[k].second + 1;
+      }
+      for (size_t k = 1; k < classes.size() && e == cudaSuccess; ++k) e = cudaStreamWaitEvent(cs, bt->ev_join[k], 0);
     }
     cudaGraph_t graph = nullptr;
     const cudaError_t e2 = cudaStreamEndCapture(cs, &graph);
@@ -1312,6 +1409,7 @@ int batch_launch(std_batch* bt, float lr_a, float lr_b, float lam_a, float lam_b
     bt->gkey_groups = groups;
     bt->gkey_smem = smem;
     bt->gkey_items = bt->d_items;
+    bt->gkey_classes = classes;
   }
   STD_CUDA(cudaEventRecord(bt->evm, bt->stream), "event");
   STD_CUDA(cudaGraphLaunch(bt->gexec, bt->stream), "batched graph launch");
@@ -1377,10 +1475,17 @@ int std_batch_destroy(std_batch* bt) {
   cudaFree(bt->d_order);
   cudaFree(bt->d_first);
   cudaFree(bt->d_gstart);
+  cudaFree(bt->d_gstart_cl);
   cudaFreeHost(bt->h_items);
   cudaFreeHost(bt->h_order);
   cudaFreeHost(bt->h_first);
   cudaFreeHost(bt->h_gstart);
+  cudaFreeHost(bt->h_gstart_cl);
+  for (int k = 0; k < 8; ++k) {
+    if (bt->fork[k]) cudaStreamDestroy(bt->fork[k]);
+    if (bt->ev_join[k]) cudaEventDestroy(bt->ev_join[k]);
+  }
+  if (bt->ev_fork) cudaEventDestroy(bt->ev_fork);
   if (bt->ev0) cudaEventDestroy(bt->ev0);
   if (bt->ev1) cudaEventDestroy(bt->ev1);
   if (bt->evm) cudaEventDestroy(bt->evm);

@@ -54,6 +54,7 @@
 // row is also published, tagged, under its run start; later modes of the
 // same minibatch (which need the rows of modes k < n as updated, Gauss-Seidel
 // order) poll those slots, found through the tiler's links.
+#include <cooperative_groups.h>
 #include <cuda_bf16.h>
 
 #include "sgdt_internal.cuh"
@@ -154,7 +155,7 @@ __host__ __device__ inline int fp32_row_stride(int Pn) {
 
 struct SmemLayout {
   int B, VB, Bs, G, GT, GTh, Sh, S, ldig, cdig, rowtab, trij, sc[2], rows, master, p, left, right, red, D, q,
-      head, fown, pbuf, gsp, total_words;
+      head, fown, pbuf, gsp, cred, total_words;
   int lw, rw, sfloats, rpre, ldig_on, gsplit, srows;
 };
 
@@ -168,7 +169,7 @@ __host__ __device__ inline int sched_chunk_words(int N, int chunk) { return (2 *
 // pieces of srows samples); 0 = Kronecker entries formed on the fly in the
 // contraction (FP32 form only).
 __host__ __device__ inline SmemLayout smem_layout_v(const Geometry& g, int chunk, int ctas, int precision, int v,
-                                                    int srows) {
+                                                    int srows, int cl) {
   SmemLayout L;
   int off = 0;
   auto take = [&](int words) {
@@ -239,18 +240,21 @@ __host__ __device__ inline SmemLayout smem_layout_v(const Geometry& g, int chunk
       gneed = need > gneed ? need : gneed;
     }
   L.gsp = take(gneed);
+  // cluster form: this CTA's core-phase Gram partial, two copies (mode parity),
+  // read by the other CTAs of the cluster through distributed shared memory
+  L.cred = take(cl ? 2 * pad4(payload_max(g)) : 0);
   L.total_words = off;
   return L;
 }
 
 // The first variant whose shared memory fits a CTA.
-__host__ __device__ inline SmemLayout smem_layout(const Geometry& g, int chunk, int ctas, int precision) {
-  SmemLayout L = smem_layout_v(g, chunk, ctas, precision, 0, chunk);
-  if (L.total_words * 4 > kMaxSmemBytes) L = smem_layout_v(g, chunk, ctas, precision, 1, chunk);
+__host__ __device__ inline SmemLayout smem_layout(const Geometry& g, int chunk, int ctas, int precision, int cl = 0) {
+  SmemLayout L = smem_layout_v(g, chunk, ctas, precision, 0, chunk, cl);
+  if (L.total_words * 4 > kMaxSmemBytes) L = smem_layout_v(g, chunk, ctas, precision, 1, chunk, cl);
   // fewer Kronecker rows at a time (multiples of 16), then none (FP32)
   for (int sr = (chunk / 2 + 15) / 16 * 16; sr >= 16 && L.total_words * 4 > kMaxSmemBytes; sr = sr / 2 / 16 * 16)
-    L = smem_layout_v(g, chunk, ctas, precision, 1, sr);
-  if (L.total_words * 4 > kMaxSmemBytes && precision != 1) L = smem_layout_v(g, chunk, ctas, precision, 1, 0);
+    L = smem_layout_v(g, chunk, ctas, precision, 1, sr, cl);
+  if (L.total_words * 4 > kMaxSmemBytes && precision != 1) L = smem_layout_v(g, chunk, ctas, precision, 1, 0, cl);
   return L;
 }
 
@@ -639,9 +643,19 @@ __device__ __forceinline__ void right_row(float* dst, const float* an, int Jn, i
 
 }  // namespace
 
+// Barrier over the CTAs of this thread block cluster (release/acquire at
+// cluster scope: global and shared memory written before it are visible to
+// every CTA of the cluster after it).
+__device__ __forceinline__ void cluster_sync_all() { cooperative_groups::this_cluster().sync(); }
+
 // The epoch of one tensor on the G CTAs c = 0..G-1 that own it.  SNAP: the
 // K-snapshot form, G CTAs per group and a.snap_k groups (see k_epoch_snap).
-template <bool BF, bool SNAP>
+// CL: the G CTAs are one thread block cluster (G <= 16, see k_epoch_cl): the
+// core-phase reduction reads the other CTAs' partials from their shared
+// memory and adds them in the same order as the two-hop exchange (so both
+// forms give the same bits), and every other exchange keeps its tagged words
+// but is preceded by a cluster barrier instead of being polled for.
+template <bool BF, bool SNAP, bool CL>
 __device__ __forceinline__ void epoch_body(const EpochArgs& a, const int G, const int c) {
   extern __shared__ __align__(16) float sm[];
   // per-mode constants, indexed by the (runtime) mode
@@ -654,7 +668,9 @@ __device__ __forceinline__ void epoch_body(const EpochArgs& a, const int G, cons
   __shared__ int s_nheads;
   const int N = a.g.N, R = a.g.R;
   const int chunk_max = a.chunk_max;
-  const SmemLayout L = smem_layout(a.g, chunk_max, G, BF ? 1 : 0);
+  const SmemLayout L = smem_layout(a.g, chunk_max, G, BF ? 1 : 0, CL ? 1 : 0);
+  float* credsm = sm + L.cred;
+  int cpar = 0;   // parity of the core mode (cluster form: which partial buffer)
   float* Bsm = sm + L.B;
   float* VBsm = sm + L.VB;   // Kruskal-column velocities (momentum)
   float* Bsnap = sm + L.Bs;  // K-snapshot form: B at the start of the block (then the combined B)
@@ -717,6 +733,7 @@ __device__ __forceinline__ void epoch_body(const EpochArgs& a, const int G, cons
       mFper[k] = make_fastdiv((uint32_t)(N + 2 + k));
     }
   }
+  __syncthreads();   // thread 0's per-mode tables, read by every thread below
   const FastDiv f_sumJ = make_fastdiv((uint32_t)sumJ);
 #pragma unroll 1
   for (int jj = tid; jj < sumJ; jj += T) {
@@ -810,25 +827,50 @@ __device__ __forceinline__ void epoch_body(const EpochArgs& a, const int G, cons
       Bsm[i] = v;
     }
     // the rows this CTA owns, minibatch after minibatch (a row's changes
-    // from different minibatches are added in order)
+    // from different minibatches are added in order; within one minibatch
+    // the entries are distinct rows).  A warp takes 32 / Jmax entries per
+    // pass, lane group g entry g, lane j column j, two passes' loads in flight
+    {
+      const int gpw = 32 / Jmax;
+      const int sub = lane / Jmax, jj = lane - sub * Jmax;
 #pragma unroll 1
-    for (int k = 0; k < kq; ++k) {
-      const int cnt_k = __ldcg(a.snap_count + a.snap_cta * stride + k);
-      const int2* lst = a.snap_list + ((size_t)a.snap_cta * stride + k) * (size_t)(N * M);
+      for (int k = 0; k < kq; ++k) {
+        const int cnt_k = __ldcg(a.snap_count + a.snap_cta * stride + k);
+        const int2* lst = a.snap_list + ((size_t)a.snap_cta * stride + k) * (size_t)(N * M);
 #pragma unroll 1
-      for (int e = warp; e < cnt_k; e += nwarps) {
-        const int2 en = __ldcg(lst + e);
-        const int n = en.y >> 16, st = en.y & 0xffff;
-        const unsigned row = (unsigned)en.x;
-        if (lane < mJ[n]) {
-          const float d = __ldcg(a.snap_drow + (((size_t)k * N + n) * M + st) * Jmax + lane);
-          float* ap = mA[n] + row * (unsigned)mJp[n] + lane;
-          const float nv = __fadd_rn(__ldcg(ap), d);
-          __stcg(ap, nv);
-          if (BF) __stcg(mAb[n] + row * (unsigned)mJb[n] + lane, __bfloat16_as_ushort(__float2bfloat16_rn(nv)));
+        for (int e0 = warp * 2 * gpw; e0 < cnt_k; e0 += nwarps * 2 * gpw) {
+          float d[2], av[2];
+          float* ap[2];
+          int nn[2];
+          unsigned rw[2];
+          bool live[2];
+#pragma unroll
+          for (int u = 0; u < 2; ++u) {
+            const int e = e0 + u * gpw + sub;
+            live[u] = sub < gpw && e < cnt_k;
+            if (live[u]) {
+              const int2 en = __ldcg(lst + e);
+              nn[u] = en.y >> 16;
+              rw[u] = (unsigned)en.x;
+              live[u] = jj < mJ[nn[u]];
+              if (live[u]) {
+                d[u] = __ldcg(a.snap_drow + (((size_t)k * N + nn[u]) * M + (en.y & 0xffff)) * Jmax + jj);
+                ap[u] = mA[nn[u]] + rw[u] * (unsigned)mJp[nn[u]] + jj;
+                av[u] = __ldcg(ap[u]);
+              }
+            }
+          }
+#pragma unroll
+          for (int u = 0; u < 2; ++u)
+            if (live[u]) {
+              const float nv = __fadd_rn(av[u], d[u]);
+              __stcg(ap[u], nv);
+              if (BF)
+                __stcg(mAb[nn[u]] + rw[u] * (unsigned)mJb[nn[u]] + jj, __bfloat16_as_ushort(__float2bfloat16_rn(nv)));
+            }
         }
+        __syncthreads();
       }
-      __syncthreads();
     }
     if (tid < stride) a.snap_count[a.snap_cta * stride + tid] = 0;
     return grid_barrier(a, generation, Gtot);
@@ -849,7 +891,11 @@ __device__ __forceinline__ void epoch_body(const EpochArgs& a, const int G, cons
     const uint32_t tag0 = a.tag_base + (uint32_t)((b - a.b0) * 8);
 
     // every row update of the previous minibatch is visible after this
-    if (!SNAP && b > a.b0 && !grid_barrier(a, generation, G)) return;
+    if (CL) {
+      if (b > a.b0) cluster_sync_all();
+    } else if (!SNAP && b > a.b0 && !grid_barrier(a, generation, G)) {
+      return;
+    }
     cp_async_wait_all();
     __syncthreads();
     // factor mode 2's chunk arrives while the core phase runs
@@ -1014,8 +1060,12 @@ __device__ __forceinline__ void epoch_body(const EpochArgs& a, const int G, cons
             }
             const float4 x = make_float4(x0.x + x1.x, x0.y + x1.y, x0.z + x1.z, x0.w + x1.w);
             if (nsl == 1) {
-              put_pair(dst + obase, tag, x.x, x.y);
-              put_pair(dst + obase + 2, tag, x.z, x.w);
+              if (CL) {
+                *reinterpret_cast<float4*>(credsm + (cpar & 1) * pad4(payload_max(a.g)) + obase) = x;
+              } else {
+                put_pair(dst + obase, tag, x.x, x.y);
+                put_pair(dst + obase + 2, tag, x.z, x.w);
+              }
             } else if (sl > 0) {
               gsp[(sl - 1) * ntile + t] = x;
             } else {
@@ -1032,17 +1082,61 @@ __device__ __forceinline__ void epoch_body(const EpochArgs& a, const int G, cons
                 const float4 y = gsp[(q - 1) * ntile + t];
                 x.x += y.x; x.y += y.y; x.z += y.z; x.w += y.w;
               }
-              put_pair(dst + 4 * t, tag, x.x, x.y);
-              put_pair(dst + 4 * t + 2, tag, x.z, x.w);
+              if (CL) {
+                *reinterpret_cast<float4*>(credsm + (cpar & 1) * pad4(payload_max(a.g)) + 4 * t) = x;
+              } else {
+                put_pair(dst + 4 * t, tag, x.x, x.y);
+                put_pair(dst + 4 * t + 2, tag, x.z, x.w);
+              }
             }
           }
         }
+        // payload word o of the reduced Gram into shared memory: g as R x J_n,
+        // each block C_{r r'} unpacked to full rows of stride pad4(J_n)
+        auto put_red = [&](int o, float v) {
+          if (o < Kx) {
+            const int r = fdiv(o >> 2, f_na4), j = o - r * Jq;
+            if (j < Jn) redsm[r * Jn + j] = v;
+          } else {
+            const int t = o - Kx;
+            const int q = fdiv(t >> 2, f_nq4), jj = t - q * tJp;
+            if (jj < tJ) {
+              const int ja = trij[jj] & 0xff, jb = trij[jj] >> 8;
+              float* blk = redsm + Kq + q * Jn * Jq;
+              blk[ja * Jq + jb] = v;
+              blk[jb * Jq + ja] = v;
+            }
+          }
+        };
+        bool ok = true;
+        if (CL) {
+          // every CTA sums the cluster's partials itself, word by word, in the
+          // order of the two-hop exchange's butterfly over GL = G rounded up
+          // to a power of two lanes (missing CTAs contribute +0)
+          cluster_sync_all();
+          cooperative_groups::cluster_group cg_cl = cooperative_groups::this_cluster();
+          const int GL = pow2_at_least(G);
+          const float* mine = credsm + (cpar & 1) * pad4(payload_max(a.g));
+  #pragma unroll 1
+          for (int o = tid; o < P; o += T) {
+            float t16[16];
+  #pragma unroll
+            for (int q = 0; q < 16; ++q)
+              t16[q] = (q < G) ? *cg_cl.map_shared_rank(mine + o, (unsigned)q) : 0.f;
+  #pragma unroll
+            for (int off = 8; off > 0; off >>= 1)
+              if (off < GL)
+  #pragma unroll
+                for (int q = 0; q < 8; ++q)
+                  if (q < off) t16[q] = t16[q] + t16[q + off];
+            put_red(o, t16[0]);
+          }
+        } else {
         // hop 1: CTA c sums its slice of the payload (word pairs) over all CTAs
         // (in CTA order within each lane, then a fixed butterfly across the
         // GL lanes of the pair) and pushes each sum into every CTA's copy of
         // the payload; with fewer than 32 CTAs a warp takes 32 / GL pairs at once
         // (a separate loop: the full-warp form is faster when every lane has a CTA)
-        bool ok = true;
         {
           const int P2 = P >> 1;
           const int per = (P2 + G - 1) / G;
@@ -1112,24 +1206,11 @@ __device__ __forceinline__ void epoch_body(const EpochArgs& a, const int G, cons
             w1[0] = get_pair(p1[0]);
             if (ok) ok = wait_pairs<1>(p1, w1, tag, a);
   #pragma unroll
-            for (int u = 0; u < 2; ++u) {
-              const int o = 2 * o2 + u;
-              const float v = val_of(u == 0 ? w1[0].x : w1[0].y);
-              if (o < Kx) {
-                const int r = fdiv(o >> 2, f_na4), j = o - r * Jq;
-                if (j < Jn) redsm[r * Jn + j] = v;
-              } else {
-                const int t = o - Kx;
-                const int q = fdiv(t >> 2, f_nq4), jj = t - q * tJp;
-                if (jj < tJ) {
-                  const int ja = trij[jj] & 0xff, jb = trij[jj] >> 8;
-                  float* blk = redsm + Kq + q * Jn * Jq;
-                  blk[ja * Jq + jb] = v;
-                  blk[jb * Jq + ja] = v;
-                }
-              }
-            }
+            for (int u = 0; u < 2; ++u) put_red(2 * o2 + u, val_of(u == 0 ? w1[0].x : w1[0].y));
           }
+        }
+        }
+        {
           // zero padding columns of the unpacked blocks
           if (Jq > Jn)
   #pragma unroll 1
@@ -1137,7 +1218,7 @@ __device__ __forceinline__ void epoch_body(const EpochArgs& a, const int G, cons
   #pragma unroll 1
               for (int j = Jn; j < Jq; ++j) redsm[Kq + i * Jq + j] = 0.f;
         }
-        if (!__syncthreads_and(ok)) return;
+        if (!__syncthreads_and(ok) && !CL) return;
         // Cyclic SGD over the columns of B(n) (Algorithm 1's loop over r) as a block forward
         // substitution: warp w keeps V_w (lane j) and V_{w+16}; at step r the
         // owner of column r moves it, and every later V_r'' gains C_{r'' r}
@@ -1228,6 +1309,7 @@ __device__ __forceinline__ void epoch_body(const EpochArgs& a, const int G, cons
           pbuf[s * NR + n * R + r] = acc0 + acc1;
         }
         __syncthreads();
+        ++cpar;
       }
     }
 
@@ -1263,6 +1345,7 @@ __device__ __forceinline__ void epoch_body(const EpochArgs& a, const int G, cons
       if (n > 0) {
         cp_async_wait_all();
         __syncthreads();
+        if (CL) cluster_sync_all();   // the previous mode's row slots
         buf ^= 1;
         // the next phase's chunk: mode n+1 of this minibatch, or mode 1 of the next
         const int64_t nb = (n + 1 < N) ? b : b + stride;
@@ -1369,7 +1452,7 @@ __device__ __forceinline__ void epoch_body(const EpochArgs& a, const int G, cons
           if (i < total) rows[i] = p2[u] ? (BF ? bf16_round(val_of(w2[u])) : val_of(w2[u])) : v2[u];
         }
       }
-      if (!__syncthreads_and(ok)) return;
+      if (!__syncthreads_and(ok) && !CL) return;
       const int nheads = s_nheads;
       // BF16 form: the FP32 master rows, fetched only for the runs this CTA
       // updates (run heads that start in this chunk), while the contraction runs
@@ -1554,6 +1637,7 @@ __device__ __forceinline__ void epoch_body(const EpochArgs& a, const int G, cons
           }
         }
       }
+      if (CL) cluster_sync_all();   // every chunk's run pieces
       // a run begun here that continues: the pieces of chunks c+1 .. c1,
       // polled in parallel
       const uint32_t seg_last = cnt > 0 ? fseg[head[nheads - 1]] : 0u;
@@ -1567,7 +1651,7 @@ __device__ __forceinline__ void epoch_body(const EpochArgs& a, const int G, cons
         pieces_sm[i] = val_of(settle(p, get_word(p), tag, ok, a));
       }
       if (BF) cp_async_wait_all();
-      if (!__syncthreads_and(ok)) return;
+      if (!__syncthreads_and(ok) && !CL) return;
       // the factor-row update of every run that starts in this chunk (pieces of
       // a continuing run added in chunk order), warp per run, lane j
 #pragma unroll 1
@@ -1639,13 +1723,23 @@ __device__ __forceinline__ void epoch_body(const EpochArgs& a, const int G, cons
       a.core[lin] = acc;
     }
   }
+  // no CTA leaves (or starts its next tensor) while another may still read
+  // its shared memory
+  if (CL) cluster_sync_all();
 }
 
 // One tensor on the whole grid.
 template <bool BF>
 __global__ void __launch_bounds__(kEpochThreads, 1)
 k_epoch(EpochArgs a) {
-  epoch_body<BF, false>(a, gridDim.x, blockIdx.x);
+  epoch_body<BF, false, false>(a, gridDim.x, blockIdx.x);
+}
+
+// One tensor on one thread block cluster of gridDim.x <= 16 CTAs.
+template <bool BF>
+__global__ void __launch_bounds__(kEpochThreads, 1)
+k_epoch_cl(EpochArgs a) {
+  epoch_body<BF, false, true>(a, gridDim.x, (int)cooperative_groups::this_cluster().block_rank());
 }
 
 // K-snapshot form (a labelled variant of Algorithm 1's minibatch order): the
@@ -1675,14 +1769,14 @@ k_epoch_snap(EpochArgs a) {
     s_a.mail = a.mail + (size_t)grp * a.s.M * a.g.N * (a.g.Jmax + (a.g.Jmax & 1));
   }
   __syncthreads();
-  epoch_body<BF, true>(s_a, a.snap_gk, c);
+  epoch_body<BF, true, false>(s_a, a.snap_gk, c);
 }
 
 // Many independent tensors in one persistent launch: the grid is split into
 // groups of CTAs [m.gstart[q], m.gstart[q+1]); group q runs the epochs of the
 // tensors m.order[m.first[q] .. m.first[q+1]) one after the other, each on
 // its own arguments (copied into shared memory) and exchange buffers.
-template <bool BF>
+template <bool BF, bool CL>
 __global__ void __launch_bounds__(kEpochThreads, 1)
 k_epoch_multi(MultiArgs m) {
   __shared__ __align__(16) EpochArgs s_a;
@@ -1697,7 +1791,7 @@ k_epoch_multi(MultiArgs m) {
 #pragma unroll 1
     for (int i = threadIdx.x; i < (int)(sizeof(EpochArgs) / 4); i += blockDim.x) dst[i] = src[i];
     __syncthreads();
-    epoch_body<BF, false>(s_a, G, c);
+    epoch_body<BF, false, CL>(s_a, G, c);
     __syncthreads();
   }
 }
@@ -1718,8 +1812,13 @@ const void* kernel_for(int precision) {
   return precision == 1 ? (const void*)k_epoch<true> : (const void*)k_epoch<false>;
 }
 
-const void* multi_kernel_for(int precision) {
-  return precision == 1 ? (const void*)k_epoch_multi<true> : (const void*)k_epoch_multi<false>;
+const void* multi_kernel_for(int precision, bool cl = false) {
+  if (cl) return precision == 1 ? (const void*)k_epoch_multi<true, true> : (const void*)k_epoch_multi<false, true>;
+  return precision == 1 ? (const void*)k_epoch_multi<true, false> : (const void*)k_epoch_multi<false, false>;
+}
+
+const void* cl_kernel_for(int precision) {
+  return precision == 1 ? (const void*)k_epoch_cl<true> : (const void*)k_epoch_cl<false>;
 }
 
 const void* snap_kernel_for(int precision) {
@@ -1816,8 +1915,77 @@ cudaError_t launch_epoch_multi(const MultiArgs& m, int precision, int ctas, size
   attr[0].val.cooperative = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  if (precision == 1) return cudaLaunchKernelEx(&cfg, k_epoch_multi<true>, m);
-  return cudaLaunchKernelEx(&cfg, k_epoch_multi<false>, m);
+  if (precision == 1) return cudaLaunchKernelEx(&cfg, k_epoch_multi<true, false>, m);
+  return cudaLaunchKernelEx(&cfg, k_epoch_multi<false, false>, m);
+}
+
+// ---------------------------------------------------------------------------
+// Cluster form (groups of 2..16 CTAs as one thread block cluster).
+// ---------------------------------------------------------------------------
+namespace {
+
+cudaError_t cl_attrs(const void* fn, size_t smem, int csize) {
+  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e == cudaSuccess && csize > 8) e = cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+  return e;
+}
+
+cudaLaunchConfig_t cl_config(int ctas, int csize, size_t smem, cudaStream_t st, cudaLaunchAttribute* attr) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(ctas);
+  cfg.blockDim = dim3(kEpochThreads);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = csize;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cfg;
+}
+
+}  // namespace
+
+bool epoch_cluster_size_ok(int csize) { return csize == 2 || csize == 4 || csize == 8 || csize == 16; }
+
+size_t epoch_smem_bytes_cl(const Geometry& g, int chunk_max, int ctas, int precision) {
+  return (size_t)smem_layout(g, chunk_max, ctas, precision, 1).total_words * sizeof(float);
+}
+
+// Clusters of csize CTAs that can be resident at once (0: none).
+int epoch_cl_max_clusters(int precision, bool multi, size_t smem, int csize) {
+  const void* fn = multi ? multi_kernel_for(precision, true) : cl_kernel_for(precision);
+  if (cl_attrs(fn, smem, csize) != cudaSuccess) return 0;
+  cudaLaunchAttribute attr[1];
+  cudaLaunchConfig_t cfg = cl_config(csize, csize, smem, nullptr, attr);
+  int n = 0;
+  if (cudaOccupancyMaxActiveClusters(&n, fn, &cfg) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return n;
+}
+
+cudaError_t launch_epoch_cl(const EpochArgs& a, int ctas, size_t smem, cudaStream_t st) {
+  cudaError_t e = cl_attrs(cl_kernel_for(a.precision), smem, ctas);
+  if (e != cudaSuccess) return e;
+  cudaLaunchAttribute attr[1];
+  cudaLaunchConfig_t cfg = cl_config(ctas, ctas, smem, st, attr);
+  if (a.precision == 1) return cudaLaunchKernelEx(&cfg, k_epoch_cl<true>, a);
+  return cudaLaunchKernelEx(&cfg, k_epoch_cl<false>, a);
+}
+
+// Groups of csize CTAs, each one cluster; gstart[q] = q * csize.  Not
+// cooperative: clusters are independent, and a cluster's CTAs are resident
+// together by construction.
+cudaError_t launch_epoch_multi_cl(const MultiArgs& m, int precision, int csize, size_t smem, cudaStream_t st) {
+  cudaError_t e = cl_attrs(multi_kernel_for(precision, true), smem, csize);
+  if (e != cudaSuccess) return e;
+  cudaLaunchAttribute attr[1];
+  cudaLaunchConfig_t cfg = cl_config(m.groups * csize, csize, smem, st, attr);
+  if (precision == 1) return cudaLaunchKernelEx(&cfg, k_epoch_multi<true, true>, m);
+  return cudaLaunchKernelEx(&cfg, k_epoch_multi<false, true>, m);
 }
 
 }  // namespace sgdt

@@ -212,6 +212,14 @@ cudaError_t launch_wait_probe(unsigned long long watchdog_ns, int* err, const un
 cudaError_t epoch_multi_setup(int precision, size_t smem);
 int epoch_multi_max_ctas(int precision, size_t smem);
 cudaError_t launch_epoch_multi(const MultiArgs& m, int precision, int ctas, size_t smem, cudaStream_t st);
+// Cluster form of the update kernels: one tensor's group of 2, 4, 8 or 16
+// CTAs as one thread block cluster (same results bit for bit as the
+// cooperative form with that many CTAs).
+bool epoch_cluster_size_ok(int csize);
+size_t epoch_smem_bytes_cl(const Geometry& g, int chunk_max, int ctas, int precision);
+int epoch_cl_max_clusters(int precision, bool multi, size_t smem, int csize);
+cudaError_t launch_epoch_cl(const EpochArgs& a, int ctas, size_t smem, cudaStream_t st);
+cudaError_t launch_epoch_multi_cl(const MultiArgs& m, int precision, int csize, size_t smem, cudaStream_t st);
 cudaError_t launch_init_params(const Geometry& g, float* const* A, float* B, int mode, double mu,
                                double sigma, uint64_t seed, cudaStream_t st);
 cudaError_t launch_check_coords(const Geometry& g, const int32_t* coords, int64_t k, int* err,

@@ -149,3 +149,29 @@ def test_batch_member_tracks_oracle(B, synth):
     assert worst <= 1e-3, worst
     for m in batched:
         m[1].close()
+
+
+@pytest.mark.parametrize("group", [2, 4, 8, 16])
+def test_cluster_form_equals_cooperative_form(B, synth, group):
+    """A group of 2..16 CTAs runs as one thread block cluster (exchanges through
+    cluster barriers and shared memory); the cooperative form (tagged words
+    through L2) runs when any group of the launch is larger.  Both add the
+    same numbers in the same order, so they agree bit for bit: members at
+    `group` CTAs beside one 32-CTA group (cooperative form) against their runs
+    alone at `group` CTAs (cluster form)."""
+    M, lr, lam = 256, 0.1, 1e-3
+    batched = _members(B, synth)
+    alone = _members(B, synth, ctas=group)
+    sizes = [group] * (len(SPECS) - 1) + [32]
+    with B.Batch([m[1] for m in batched], ctas_per_tensor=group) as bt:
+        bt.set_groups(sizes)
+        for _ in range(2):
+            bt.epoch(lr, lr, lam, lam, M)
+        assert bt.groups() == sizes
+    for m in alone[:-1]:
+        for _ in range(2):
+            m[1].epoch(lr, lr, lam, lam, M)
+    for a, b in zip(batched[:-1], alone[:-1]):
+        assert _params_equal(a[1], b[1])
+    for m in batched + alone:
+        m[1].close()
