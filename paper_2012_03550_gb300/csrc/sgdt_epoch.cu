@@ -601,14 +601,29 @@ __device__ __forceinline__ void contract_fp32(int cnt, int Jn, int Pn, int Pp, b
 #pragma unroll
         for (int q = 0; q < SG; ++q) e[q] += f[q];
       } else {
+        // entries formed on the fly, added in exactly the order of the
+        // materialised form (even 4-column groups into e, odd ones into f,
+        // padding columns as zeros), so the result does not depend on which
+        // form the shared-memory budget allowed
+        const int nv = Pp >> 2;
 #pragma unroll
         for (int q = 0; q < SG; ++q)
           if (s0 + q < cnt) {
             const float* rs = rows + (s0 + q) * sumJ;
-            float acc = 0.f;
+            float acc = 0.f, acc2 = 0.f;
 #pragma unroll 1
-            for (int cc = 0; cc < Pn; ++cc) acc = fmaf(kron_entry(rs, cdn[cc], nm1), gv[cc], acc);
-            e[q] = acc;
+            for (int v = 0; v < nv; ++v) {
+              float a4 = v & 1 ? acc2 : acc;
+#pragma unroll
+              for (int h = 0; h < 4; ++h) {
+                const int cc = 4 * v + h;
+                const float x = cc < Pn ? kron_entry(rs, cdn[cc], nm1) : 0.f;
+                a4 = fmaf(x, gv[cc], a4);
+              }
+              if (v & 1) acc2 = a4;
+              else acc = a4;
+            }
+            e[q] = acc + acc2;
           }
       }
     }
