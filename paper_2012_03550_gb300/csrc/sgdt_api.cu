@@ -1305,9 +1305,16 @@ int batch_launch(std_batch* bt, float lr_a, float lr_b, float lam_a, float lam_b
       for (int q = 0; q < groups; ++q)
         if (classes.empty() || classes.back().first != g2[q]) classes.push_back({g2[q], 1});
         else classes.back().second += 1;
-      for (const auto& k : classes)
-        if (epoch_cl_max_clusters(bt->precision, true, smem_cl, k.first) < 1) ok = false;
-      if (ok && classes.size() <= 8) {
+      // only one size, and no more groups than clusters of it can be resident
+      // at once: a cluster must fit inside one GPC, so fewer groups of a size
+      // run side by side than CTAs would allow, and groups that wait for a
+      // free slot would stretch the launch (measured on the batched workload:
+      // 692 ms in the cluster form against 421 ms cooperative with groups of
+      // 4 and 8)
+      if (classes.size() != 1 || epoch_cl_max_clusters(bt->precision, true, smem_cl, classes[0].first) <
+                                     classes[0].second)
+        ok = false;
+      if (ok) {
         lists.swap(l2);
         gsize.swap(g2);
       } else {
