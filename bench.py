@@ -113,8 +113,10 @@ def _workload(scale):
 # by the sha256 prefix of the kernel source the capture ran.  The figure is
 # reported only while the source is unchanged.
 PROFILED_TRAFFIC = {
-    "fp32": {"sha256_prefix": "f35cbcdd49677b2e", "dram_bytes_per_nnz": 75.55,
-             "capture": "ncu --set full, rating tensor at 2% scale (1.98M training nonzeros), one launch"},
+    "fp32": {"sha256_prefix": "b5b7e612cf7786a8", "dram_bytes_per_nnz": 76.28,
+             "capture": "ncu --set full, rating tensor at 2% scale, first segment launch (1,048,576 nonzeros)"},
+    "snapshot8": {"sha256_prefix": "b5b7e612cf7786a8", "dram_bytes_per_nnz": 82.08,
+                  "capture": "ncu --set full, K = 8, rating tensor at 2% scale, first segment launch"},
 }
 
 
@@ -450,6 +452,8 @@ def run_gpu(a):
             ach = n_train * _bytes_per_nnz(N, J) / (r["kernel_ms"] * 1e-3) / 1e9
             r["roofline_frac"] = ach / peak_s
             r["achieved_gbs"] = ach
+            tpk, _ = _profiled_traffic_per_nnz(f"snapshot{K}")
+            r["traffic"] = tpk * n_train if tpk is not None else None
             snap[f"K{K}"] = r
     del dc, dv
 

@@ -203,11 +203,12 @@ int ensure_schedule(std_ctx* c, int M) {
 }
 
 // Minibatches per schedule segment of std_sgd_epoch / std_sgd_batches: about
-// 2^20 sampled positions (the schedule of one segment is ~100 MB for a 3-order
-// tensor, and the update kernel reads it back while it is still in L2), a
-// multiple of K in the K-snapshot form so that blocks never straddle segments.
+// 2^22 sampled positions (the schedule of one segment is ~400 MB for a 3-order
+// tensor instead of the epoch's; a segment of 1,024 minibatches of 4,096 keeps
+// the sampler/tiler's one-CTA-per-minibatch launch several CTAs deep per SM),
+// a multiple of K in the K-snapshot form so that blocks never straddle segments.
 int64_t segment_batches(int M, int K) {
-  int64_t S = (1LL << 20) / M;
+  int64_t S = (1LL << 22) / M;
   if (S < 1) S = 1;
   if (K >= 2) S = S < K ? K : S / K * K;
   return S;
