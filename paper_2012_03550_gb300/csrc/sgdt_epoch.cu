@@ -118,6 +118,9 @@ __host__ __device__ inline int unpacked_payload(int Jn, int R) {
 // Thread tiles (one left column x 4 right columns) of the core-phase Gram
 // partial of a mode, and the sample slices each tile is split into.
 constexpr int kGramSplitChunk = 48;
+// K-snapshot chunks of at least this many samples form their left Gram
+// operand rows with one thread per sample (a 16-lane group per sample below)
+constexpr int kThreadPerSampleChunk = 96;
 __host__ __device__ inline int gram_tiles(int Jn, int R) {
   return R * (pad4(Jn) >> 2) + (R * (R - 1) / 2) * (pad4(Jn * (Jn + 1) / 2) >> 2);
 }
@@ -681,6 +684,8 @@ __device__ __forceinline__ void epoch_body(const EpochArgs& a, const int G, cons
   __shared__ float* mvA[kMaxN];
   __shared__ unsigned short* mAb[kMaxN];
   __shared__ int s_nheads;
+  __shared__ FastDiv mFrw[kMaxN];
+  __shared__ int s_soff[65];   // K-snapshot form: offsets of the row lists (K <= 64)
   const int N = a.g.N, R = a.g.R;
   const int chunk_max = a.chunk_max;
   const SmemLayout L = smem_layout(a.g, chunk_max, G, BF ? 1 : 0, CL ? 1 : 0);
@@ -746,6 +751,7 @@ __device__ __forceinline__ void epoch_body(const EpochArgs& a, const int G, cons
       mFtJ[k] = make_fastdiv((uint32_t)tri(Jk));
       mFJ[k] = make_fastdiv((uint32_t)Jk);
       mFper[k] = make_fastdiv((uint32_t)(N + 2 + k));
+      mFrw[k] = make_fastdiv((uint32_t)right_width(Jk));
     }
   }
   __syncthreads();   // thread 0's per-mode tables, read by every thread below
@@ -759,6 +765,7 @@ __device__ __forceinline__ void epoch_body(const EpochArgs& a, const int G, cons
   __syncthreads();
   const FastDiv f_R = make_fastdiv((uint32_t)R);
   const FastDiv f_NR = make_fastdiv((uint32_t)(N * R));
+  const FastDiv f_Jmax = make_fastdiv((uint32_t)Jmax);
   int sumJR = 0;
   for (int n = 0; n < N; ++n) sumJR += mJ[n] * R;
 #pragma unroll 1
@@ -832,20 +839,117 @@ __device__ __forceinline__ void epoch_body(const EpochArgs& a, const int G, cons
     if (!grid_barrier(a, generation, Gtot)) return false;
     const int64_t bs = a.b0 + blk * stride;
     const int kq = (int)((a.b1 - bs) < (int64_t)stride ? (a.b1 - bs) : (int64_t)stride);
+    // column changes, loaded eight minibatches at a time and added in order
 #pragma unroll 1
     for (int i = tid; i < sumJR; i += T) {
       float v = Bsnap[i];
       if (a.lr_b != 0.f)
 #pragma unroll 1
-        for (int k = 0; k < kq; ++k) v = __fadd_rn(v, __ldcg(a.snap_dB + (size_t)k * sumJR + i));
+        for (int k0 = 0; k0 < kq; k0 += 8) {
+          float dv[8];
+#pragma unroll
+          for (int u = 0; u < 8; ++u) dv[u] = k0 + u < kq ? __ldcg(a.snap_dB + (size_t)(k0 + u) * sumJR + i) : 0.f;
+#pragma unroll
+          for (int u = 0; u < 8; ++u)
+            if (k0 + u < kq) v = __fadd_rn(v, dv[u]);
+        }
       Bsnap[i] = v;
       Bsm[i] = v;
     }
-    // the rows this CTA owns, minibatch after minibatch (a row's changes
-    // from different minibatches are added in order; within one minibatch
-    // the entries are distinct rows).  A warp takes 32 / Jmax entries per
-    // pass, lane group g entry g, lane j column j, two passes' loads in flight
-    {
+    // sizes of the kq lists of rows this CTA owns, and their offsets
+    if (warp == 0) {
+      const int* cp = a.snap_count + a.snap_cta * stride;
+      const int c0 = lane < kq ? __ldcg(cp + lane) : 0;
+      const int c1 = lane + 32 < kq ? __ldcg(cp + lane + 32) : 0;
+      int x0 = c0, x1 = c1;
+#pragma unroll
+      for (int off = 1; off < 32; off <<= 1) {
+        const int y0 = __shfl_up_sync(0xffffffffu, x0, off), y1 = __shfl_up_sync(0xffffffffu, x1, off);
+        if (lane >= off) {
+          x0 += y0;
+          x1 += y1;
+        }
+      }
+      const int t0 = __shfl_sync(0xffffffffu, x0, 31);
+      x1 += t0;
+      if (lane < kq) s_soff[lane] = x0 - c0;
+      if (lane + 32 < kq) s_soff[lane + 32] = x1 - c1;
+      if (lane == 31) s_soff[kq] = x1;
+    }
+    __syncthreads();
+    const int total = s_soff[kq];
+    // staging area: the buffers of one minibatch's phases (rows .. q), free here
+    const int cap = (L.head - L.rows) / (3 + Jmax);
+    if (total <= cap) {
+      // every list entry and its row change, all minibatches' loads at once;
+      // then the rows minibatch after minibatch (a row's changes from
+      // different minibatches are added in order; within one minibatch the
+      // entries are distinct rows), two elements per thread in flight
+      int2* se = reinterpret_cast<int2*>(sm + L.rows);
+      int* sk = reinterpret_cast<int*>(se + cap);
+      float* sd = reinterpret_cast<float*>(sk + cap);
+#pragma unroll 1
+      for (int t = tid; t < total; t += T) {
+        int lo = 0, hi = kq - 1;   // the list holding entry t
+        while (lo < hi) {
+          const int mid = (lo + hi + 1) >> 1;
+          if (s_soff[mid] <= t) lo = mid;
+          else hi = mid - 1;
+        }
+        se[t] = __ldcg(a.snap_list + ((size_t)a.snap_cta * stride + lo) * (size_t)(N * M) + (t - s_soff[lo]));
+        sk[t] = lo;
+      }
+      __syncthreads();
+#pragma unroll 1
+      for (int i = tid; i < total * Jmax; i += T) {
+        const int t = fdiv(i, f_Jmax), jj = i - t * Jmax;
+        const int2 en = se[t];
+        const int nn = en.y >> 16;
+        if (jj < mJ[nn]) sd[i] = __ldcg(a.snap_drow + (((size_t)sk[t] * N + nn) * M + (en.y & 0xffff)) * Jmax + jj);
+      }
+      __syncthreads();
+#pragma unroll 1
+      for (int k = 0; k < kq; ++k) {
+        const int i1 = s_soff[k + 1] * Jmax;
+#pragma unroll 1
+        for (int i0 = s_soff[k] * Jmax + tid; i0 < i1; i0 += 2 * T) {
+          float av[2];
+          float* ap[2];
+          int nn[2], jv[2];
+          unsigned rw[2];
+          bool live[2];
+#pragma unroll
+          for (int u = 0; u < 2; ++u) {
+            const int i = i0 + u * T;
+            live[u] = false;
+            if (i < i1) {
+              const int t = fdiv(i, f_Jmax);
+              const int2 en = se[t];
+              jv[u] = i - t * Jmax;
+              nn[u] = en.y >> 16;
+              rw[u] = (unsigned)en.x;
+              live[u] = jv[u] < mJ[nn[u]];
+              if (live[u]) {
+                ap[u] = mA[nn[u]] + rw[u] * (unsigned)mJp[nn[u]] + jv[u];
+                av[u] = __ldcg(ap[u]);
+              }
+            }
+          }
+#pragma unroll
+          for (int u = 0; u < 2; ++u)
+            if (live[u]) {
+              const float nv = __fadd_rn(av[u], sd[i0 + u * T]);
+              __stcg(ap[u], nv);
+              if (BF)
+                __stcg(mAb[nn[u]] + rw[u] * (unsigned)mJb[nn[u]] + jv[u], __bfloat16_as_ushort(__float2bfloat16_rn(nv)));
+            }
+        }
+        __syncthreads();
+      }
+    } else {
+      // lists larger than the staging area: list after list.  A warp takes
+      // 32 / Jmax entries per pass, lane group g entry g, lane j column j,
+      // two passes' loads in flight
       const int gpw = 32 / Jmax;
       const int sub = lane / Jmax, jj = lane - sub * Jmax;
 #pragma unroll 1
@@ -990,16 +1094,20 @@ __device__ __forceinline__ void epoch_body(const EpochArgs& a, const int G, cons
         const int nq4 = tJp >> 2, na4 = Jq >> 2;
         const int ntile = R * na4 + npairs * nq4;
         const FastDiv f_na4 = mFna4[n], f_nq4 = mFnq4[n];
-        // left Gram operand rows, one sample per 16-lane group (R <= 16) or
-        // per warp: lane r forms w_r, the residual e_s (group sum), e_s w_r and
-        // w_r w_r' (r' < r); right operand rows of this mode unless built above
+        // left Gram operand rows: w_r = prod_{k != n} p[s][k][r], the residual
+        // e_s = sum_r w_r p[s][n][r] - x_s, e_s w_r and w_r w_r' (r' < r); one
+        // sample per 16-lane group (R <= 16) or per warp, lane r forming w_r
+        // and the residual a group sum, except in the large chunks of the
+        // K-snapshot form, one sample per thread.  Then the right operand rows
+        // of this mode unless built above.
         {
+          const bool per_thread = SNAP && cnt >= kThreadPerSampleChunk;
           const int gl = R <= 16 ? 16 : 32;
           const int gpw = 32 / gl;
           const int sub = lane / gl, gla = lane - sub * gl;
           const int gbase = sub * gl;
   #pragma unroll 1
-          for (int s0 = warp * gpw; s0 < cnt; s0 += nwarps * gpw) {
+          for (int s0 = warp * gpw; s0 < (per_thread ? 0 : cnt); s0 += nwarps * gpw) {
             const int s = s0 + sub;
             const bool live = (s < cnt) && (gla < R);
             float w = 0.f, contrib = 0.f;
@@ -1022,10 +1130,49 @@ __device__ __forceinline__ void epoch_body(const EpochArgs& a, const int G, cons
             }
             if (live) lrow[npairs + gla] = (contrib - xs[s]) * w;
           }
-          if (!L.rpre)
+          if (per_thread)
   #pragma unroll 1
-            for (int s = warp; s < cnt; s += nwarps)
-              right_row(right + s * rw, rows + s * sumJ + mJoff[n], Jn, tJ, tJp, right_width(Jn), trij, lane);
+            for (int s = tid; s < cnt; s += T) {
+              const float* ps = pbuf + s * NR;
+              float* lrow = left + s * lw;
+              float contrib = 0.f;
+  #pragma unroll 1
+              for (int r = 0; r < R; ++r) {
+                float w = 1.f;
+  #pragma unroll 1
+                for (int k = 0; k < N; ++k)
+                  if (k != n) w *= ps[k * R + r];
+                contrib = fmaf(w, ps[n * R + r], contrib);
+                lrow[npairs + r] = w;
+              }
+              const float e = contrib - xs[s];
+  #pragma unroll 1
+              for (int r = 1; r < R; ++r) {
+                const float wr = lrow[npairs + r];
+  #pragma unroll 1
+                for (int rp = 0; rp < r; ++rp) lrow[r * (r - 1) / 2 + rp] = wr * lrow[npairs + rp];
+              }
+  #pragma unroll 1
+              for (int r = 0; r < R; ++r) lrow[npairs + r] *= e;
+            }
+          if (!L.rpre) {
+            // thread per (sample, entry) of the right rows
+            const int rwn = right_width(Jn);
+            const FastDiv frw = mFrw[n];
+  #pragma unroll 1
+            for (int i = tid; i < cnt * rwn; i += T) {
+              const int s = fdiv(i, frw), qq = i - s * rwn;
+              const float* an = rows + s * sumJ + mJoff[n];
+              float v = 0.f;
+              if (qq < tJ) {
+                const int t = trij[qq];
+                v = an[t & 0xff] * an[t >> 8];
+              } else if (qq >= tJp && qq < tJp + Jn) {
+                v = an[qq - tJp];
+              }
+              right[s * rw + qq] = v;
+            }
+          }
         }
         __syncthreads();
         // Gram partial, thread tile = one left column x 4 right columns over
@@ -1290,8 +1437,9 @@ __device__ __forceinline__ void epoch_body(const EpochArgs& a, const int G, cons
                   if (r2 > r && r2 < R) {
                     const float4* C4 = reinterpret_cast<const float4*>(Cv + ((r2 * (r2 - 1) / 2 + r) * Jn + lane) * Jq);
                     float s0 = 0.f, s1 = 0.f;
-  #pragma unroll 1
-                    for (int v = 0; v < nv4; ++v) {
+  #pragma unroll   // (unrolled: the loads of C_{r'' r} issue together)
+                    for (int v = 0; v < kMaxJ / 4; ++v) {
+                      if (v >= nv4) break;
                       const float4 cv = C4[v], dv = D4[v];
                       s0 = fmaf(cv.x, dv.x, s0);
                       s1 = fmaf(cv.y, dv.y, s1);
@@ -1616,10 +1764,14 @@ __device__ __forceinline__ void epoch_body(const EpochArgs& a, const int G, cons
               }
             }
           } else {
-            // four samples per thread when that still fills half the block
+            // four samples per thread when that still fills half the block,
+            // else two when that fills a quarter (each sample's sums are
+            // formed in the same order whatever the grouping)
             const int JL = pow2_at_least(Jn);
             if (((pc + 3) >> 2) * JL >= (T >> 1))
               contract_fp32<4>(pc, Jn, Pn, Pp, full_s, GT, Sbuf, prow, sumJ, mJoff[n], cdn, nm1, pfx, pq, Jmax, tid, T);
+            else if (((pc + 1) >> 1) * JL >= (T >> 2))
+              contract_fp32<2>(pc, Jn, Pn, Pp, full_s, GT, Sbuf, prow, sumJ, mJoff[n], cdn, nm1, pfx, pq, Jmax, tid, T);
             else
               contract_fp32<1>(pc, Jn, Pn, Pp, full_s, GT, Sbuf, prow, sumJ, mJoff[n], cdn, nm1, pfx, pq, Jmax, tid, T);
           }
