@@ -473,6 +473,8 @@ __device__ __forceinline__ void cp_async4(void* smem, const void* gmem) {
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+// Waits for this thread's cp.async groups but the most recent one.
+__device__ __forceinline__ void cp_async_wait_but_last() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
 
 struct Phase {
   int m, chunk, lo, hi, cnt;
@@ -531,6 +533,7 @@ __device__ __forceinline__ void mma_bf16_16816(float* d, uint32_t a0, uint32_t a
 // (8-bit element offsets into the sample's concatenated rows).
 __device__ __forceinline__ float kron_entry(const float* rs, unsigned long long packed, int nm1) {
   float v = rs[(int)(packed & 0xffu)];
+  if (nm1 == 2) return v * rs[(int)((packed >> 8) & 0xffu)];   // 3-way tensors
 #pragma unroll 1
   for (int k = 1; k < nm1; ++k) v *= rs[(int)((packed >> (8 * k)) & 0xffu)];
   return v;
@@ -684,7 +687,7 @@ __device__ __forceinline__ void epoch_body(const EpochArgs& a, const int G, cons
   __shared__ float* mvA[kMaxN];
   __shared__ unsigned short* mAb[kMaxN];
   __shared__ int s_nheads;
-  __shared__ FastDiv mFrw[kMaxN];
+  __shared__ FastDiv mFrw[kMaxN], mFjo[kMaxN], mFtail[kMaxN];
   __shared__ int s_soff[65];   // K-snapshot form: offsets of the row lists (K <= 64)
   const int N = a.g.N, R = a.g.R;
   const int chunk_max = a.chunk_max;
@@ -752,6 +755,8 @@ __device__ __forceinline__ void epoch_body(const EpochArgs& a, const int G, cons
       mFJ[k] = make_fastdiv((uint32_t)Jk);
       mFper[k] = make_fastdiv((uint32_t)(N + 2 + k));
       mFrw[k] = make_fastdiv((uint32_t)right_width(Jk));
+      mFjo[k] = make_fastdiv((uint32_t)(a.g.joff[k] > 0 ? a.g.joff[k] : 1));
+      mFtail[k] = make_fastdiv((uint32_t)(a.g.sumJ - a.g.joff[k]));
     }
   }
   __syncthreads();   // thread 0's per-mode tables, read by every thread below
@@ -1017,6 +1022,18 @@ __device__ __forceinline__ void epoch_body(const EpochArgs& a, const int G, cons
     }
     cp_async_wait_all();
     __syncthreads();
+    // FP32: the chunk's factor rows copied straight into shared memory, all
+    // in flight at once (one cp.async group, committed before the prefetch)
+    if (!BF) {
+      const int* crd0 = scb[buf];
+#pragma unroll 1
+      for (int i = tid; i < cnt * sumJ; i += T) {
+        const int s = fdiv(i, f_sumJ), jj = i - s * sumJ;
+        const int k = rowtab[jj] & 0xff, j = rowtab[jj] >> 8;
+        cp_async4(rows + i, mA[k] + (unsigned)crd0[s * N + k] * (unsigned)mJp[k] + j);
+      }
+      cp_async_commit();
+    }
     // factor mode 2's chunk arrives while the core phase runs
     prefetch_schedule(a, N, b, 1, scb[buf ^ 1], chunk_max, mFper[1], G, c);
     cp_async_commit();
@@ -1027,11 +1044,13 @@ __device__ __forceinline__ void epoch_body(const EpochArgs& a, const int G, cons
     // ------------------------------------------------------------------
     const int* crd = scb[buf];
     const float* xs = reinterpret_cast<const float*>(scb[buf] + N * chunk_max);
+    constexpr int UC = SNAP ? 4 : 2;   // row loads in flight per thread (K-snapshot chunks are larger)
+    if (!BF) cp_async_wait_but_last();   // the rows, not the prefetch
 #pragma unroll 1
-    for (int i0 = tid; i0 < cnt * sumJ; i0 += 2 * T) {
-      float v[2];
+    for (int i0 = tid; i0 < (BF ? cnt * sumJ : 0); i0 += UC * T) {
+      float v[UC];
 #pragma unroll
-      for (int u = 0; u < 2; ++u) {
+      for (int u = 0; u < UC; ++u) {
         const int i = i0 + u * T;
         v[u] = 0.f;
         if (i < cnt * sumJ) {
@@ -1043,7 +1062,7 @@ __device__ __forceinline__ void epoch_body(const EpochArgs& a, const int G, cons
         }
       }
 #pragma unroll
-      for (int u = 0; u < 2; ++u)
+      for (int u = 0; u < UC; ++u)
         if (i0 + u * T < cnt * sumJ) rows[i0 + u * T] = v[u];
     }
     __syncthreads();
@@ -1510,6 +1529,20 @@ __device__ __forceinline__ void epoch_body(const EpochArgs& a, const int G, cons
         __syncthreads();
         if (CL) cluster_sync_all();   // the previous mode's row slots
         buf ^= 1;
+        // FP32: rows of modes k >= n from A straight into shared memory (one
+        // cp.async group, committed before the prefetch)
+        if (!BF) {
+          const int* fc = scb[buf];
+          const int tailJ = sumJ - mJoff[n];
+          const FastDiv ft = mFtail[n];
+#pragma unroll 1
+          for (int i = tid; i < cnt * tailJ; i += T) {
+            const int s = fdiv(i, ft), jj = mJoff[n] + (i - s * tailJ);
+            const int k = rowtab[jj] & 0xff, j = rowtab[jj] >> 8;
+            cp_async4(rows + s * sumJ + jj, mA[k] + (unsigned)fc[s * N + k] * (unsigned)mJp[k] + j);
+          }
+          cp_async_commit();
+        }
         // the next phase's chunk: mode n+1 of this minibatch, or mode 1 of the next
         const int64_t nb = (n + 1 < N) ? b : b + stride;
         const int nmode = (n + 1 < N) ? n + 1 : 0;
@@ -1523,23 +1556,28 @@ __device__ __forceinline__ void epoch_body(const EpochArgs& a, const int G, cons
       // rows: modes k < n as updated earlier in this minibatch (tagged slots,
       // through the links), modes k >= n from A; G_(n) and the run heads are
       // built while the first loads are in flight
-      const int total = n > 0 ? cnt * sumJ : 0;
-      unsigned long long w2[2];
-      const unsigned long long* p2[2];
-      uint32_t t2[2];
-      float v2[2];
+      // FP32: only the rows of modes k < n (the first joff[n] entries of a
+      // sample's rows) go through this loop
+      const int width = BF ? sumJ : mJoff[n];
+      const FastDiv fw = BF ? f_sumJ : mFjo[n];
+      const int total = n > 0 ? cnt * width : 0;
+      constexpr int UG = SNAP ? 4 : 2;   // row loads in flight per thread
+      unsigned long long w2[UG];
+      const unsigned long long* p2[UG];
+      uint32_t t2[UG];
+      float v2[UG];
       int i0 = tid;
 #pragma unroll 1
-      for (bool first = true; i0 < total || first; i0 += 2 * T, first = false) {
+      for (bool first = true; i0 < total || first; i0 += UG * T, first = false) {
 #pragma unroll
-        for (int u = 0; u < 2; ++u) {
+        for (int u = 0; u < UG; ++u) {
           const int i = i0 + u * T;
           p2[u] = nullptr;
           w2[u] = 0ULL;
           t2[u] = 0u;
           v2[u] = 0.f;
           if (i < total) {
-            const int s = fdiv(i, f_sumJ), jj = i - s * sumJ;
+            const int s = fdiv(i, fw), jj = i - s * width;
             const int k = rowtab[jj] & 0xff, j = rowtab[jj] >> 8;
             if (k < n) {
               p2[u] = a.mail + ((unsigned)k * (unsigned)M + (unsigned)fl[s * N + k]) * (unsigned)(Jmax + (Jmax & 1)) + j;
@@ -1608,13 +1646,17 @@ __device__ __forceinline__ void epoch_body(const EpochArgs& a, const int G, cons
             }
           }
         }
-        if (ok) ok = wait_all<2>(p2, w2, t2, a);
+        if (ok) ok = wait_all<UG>(p2, w2, t2, a);
 #pragma unroll
-        for (int u = 0; u < 2; ++u) {
+        for (int u = 0; u < UG; ++u) {
           const int i = i0 + u * T;
-          if (i < total) rows[i] = p2[u] ? (BF ? bf16_round(val_of(w2[u])) : val_of(w2[u])) : v2[u];
+          if (i < total) {
+            const int s = fdiv(i, fw);
+            rows[s * sumJ + (i - s * width)] = p2[u] ? (BF ? bf16_round(val_of(w2[u])) : val_of(w2[u])) : v2[u];
+          }
         }
       }
+      if (!BF && n > 0) cp_async_wait_but_last();   // the rows of modes >= n, not the prefetch
       if (!__syncthreads_and(ok) && !CL) return;
       const int nheads = s_nheads;
       // BF16 form: the FP32 master rows, fetched only for the runs this CTA
