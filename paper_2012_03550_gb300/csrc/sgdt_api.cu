@@ -1025,6 +1025,7 @@ struct std_batch {
   int gkey_ctas = 0, gkey_groups = 0;
   size_t gkey_smem = 0;
   std::vector<std::pair<int, int>> gkey_classes;   // cluster form: (size, groups) per launch; empty = cooperative
+  bool gkey_plain = false;                         // the captured launches use the specialised kernels
   const void* gkey_items = nullptr;
   bool replayed = false;   // the last launch replayed the graph
 };
@@ -1271,6 +1272,7 @@ int batch_launch(std_batch* bt, float lr_a, float lr_b, float lam_a, float lam_b
     }
   }
   bt->last_g = gt;
+  bool plain = true;   // every tensor with the default options: the specialised kernels
   for (int t = 0; t < T; ++t) {
     std_ctx* c = bt->ctxs[t];
     int rc = ensure_scratch(c, gt[t], payload_floats(c->g), M);
@@ -1283,6 +1285,7 @@ int batch_launch(std_batch* bt, float lr_a, float lr_b, float lam_a, float lam_b
     a.dry = dry ? 1 : 0;
     if (dry) a.momentum = 0.f;
     bt->h_items[t] = a;
+    plain = plain && epoch_args_plain(a);
   }
   // cluster form: every group one thread block cluster (2..16 CTAs, or a
   // single CTA), one launch per group size; the groups are ordered by size so
@@ -1347,7 +1350,7 @@ int batch_launch(std_batch* bt, float lr_a, float lr_b, float lam_a, float lam_b
   // staging, so the new ranges, order and flags reach the device)
   const bool same = bt->gexec && bt->gkey_ctxs == bt->ctxs && bt->gkey_ctas == ctas && bt->gkey_groups == groups &&
                     bt->gkey_smem == smem && bt->gkey_items == (const void*)bt->d_items &&
-                    bt->gkey_classes == classes;
+                    bt->gkey_classes == classes && bt->gkey_plain == plain;
   bt->replayed = same;
   if (!same) {
     if (bt->gexec) cudaGraphExecDestroy(bt->gexec);
@@ -1377,6 +1380,7 @@ int batch_launch(std_batch* bt, float lr_a, float lr_b, float lam_a, float lam_b
       m.first = bt->d_first;
       m.gstart = bt->d_gstart;
       m.groups = groups;
+      m.plain = plain ? 1 : 0;
       e = launch_epoch_multi(m, bt->precision, ctas, smem, cs);
     } else if (e == cudaSuccess) {
       // one cluster launch per group size, the sizes in parallel branches
@@ -1396,6 +1400,7 @@ int batch_launch(std_batch* bt, float lr_a, float lr_b, float lam_a, float lam_b
         m.first = bt->d_first + q0;
         m.gstart = bt->d_gstart_cl + at;
         m.groups = classes[k].second;
+        m.plain = plain ? 1 : 0;
         if (e == cudaSuccess) e = launch_epoch_multi_cl(m, bt->precision, classes[k].first, smem, sk);
         if (e == cudaSuccess && k > 0) e = cudaEventRecord(bt->ev_join[k], sk);
         q0 += classes[k].second;
@@ -1418,6 +1423,7 @@ int batch_launch(std_batch* bt, float lr_a, float lr_b, float lam_a, float lam_b
     bt->gkey_smem = smem;
     bt->gkey_items = bt->d_items;
     bt->gkey_classes = classes;
+    bt->gkey_plain = plain;
   }
   STD_CUDA(cudaEventRecord(bt->evm, bt->stream), "event");
   STD_CUDA(cudaGraphLaunch(bt->gexec, bt->stream), "batched graph launch");

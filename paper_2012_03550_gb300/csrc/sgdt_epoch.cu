@@ -676,7 +676,9 @@ __device__ __forceinline__ void cluster_sync_all() { cooperative_groups::this_cl
 // memory and adds them in the same order as the two-hop exchange (so both
 // forms give the same bits), and every other exchange keeps its tagged words
 // but is preceded by a cluster barrier instead of being polled for.
-template <bool BF, bool SNAP, bool CL>
+// PLAIN: the default options only (no momentum, no probe, the 1/M
+// normaliser), whose code then leaves out the other options' branches.
+template <bool BF, bool SNAP, bool CL, bool PLAIN>
 __device__ __forceinline__ void epoch_body(const EpochArgs& a, const int G, const int c) {
   extern __shared__ __align__(16) float sm[];
   // per-mode constants, indexed by the (runtime) mode
@@ -1427,7 +1429,7 @@ __device__ __forceinline__ void epoch_body(const EpochArgs& a, const int G, cons
                   const float bo = ra == r ? boa : bob;
                   const float gb = V * invm + a.lam_b * bo;
                   float step = gb;
-                  if (a.momentum != 0.f) {
+                  if (!PLAIN && a.momentum != 0.f) {
                     float* vb = VBsm + mBoff[n] + lane * R + r;
                     step = a.momentum * *vb + gb;
                     *vb = step;
@@ -1443,7 +1445,7 @@ __device__ __forceinline__ void epoch_body(const EpochArgs& a, const int G, cons
                   }
                   d = bn - bo;
                   Bn[lane * R + r] = bn;
-                  if (probe && c == 0 && a.probeV) a.probeV[((unsigned)n * R + r) * kMaxJ + lane] = V;
+                  if (!PLAIN && probe && c == 0 && a.probeV) a.probeV[((unsigned)n * R + r) * kMaxJ + lane] = V;
                 }
                 D[lane] = d;
               }
@@ -1874,12 +1876,12 @@ __device__ __forceinline__ void epoch_body(const EpochArgs& a, const int G, cons
             if (en >= hi)
 #pragma unroll 1
               for (int i = lane; i < npc; i += Jn) F += pieces_sm[i];
-            const float denom = a.norm_mode == 1 ? (float)(en - st + 1) : fm;
+            const float denom = (!PLAIN && a.norm_mode == 1) ? (float)(en - st + 1) : fm;
             const unsigned row = (unsigned)fcrd[s0 * N + n];
             const float av = BF ? master[h * Jmax + lane] : rows[s0 * sumJ + mJoff[n] + lane];
             const float ga = F / denom + a.lam_a * av;
             float step = ga;
-            if (a.momentum != 0.f) {
+            if (!PLAIN && a.momentum != 0.f) {
               float* vp = mvA[n] + row * (unsigned)mJp[n] + lane;
               step = a.momentum * __ldcg(vp) + ga;
               if (!a.dry) __stcg(vp, step);
@@ -1906,7 +1908,7 @@ __device__ __forceinline__ void epoch_body(const EpochArgs& a, const int G, cons
             }
             if (n + 1 < N)
               put_word(a.mail + ((unsigned)n * (unsigned)M + st) * (unsigned)(Jmax + (Jmax & 1)) + lane, tag, nv);
-            if (probe && a.probeF) a.probeF[((unsigned)n * M + st) * kMaxJ + lane] = F;
+            if (!PLAIN && probe && a.probeF) a.probeF[((unsigned)n * M + st) * kMaxJ + lane] = F;
           }
         }
     }
@@ -1938,17 +1940,17 @@ __device__ __forceinline__ void epoch_body(const EpochArgs& a, const int G, cons
 }
 
 // One tensor on the whole grid.
-template <bool BF>
+template <bool BF, bool PLAIN>
 __global__ void __launch_bounds__(kEpochThreads, 1)
 k_epoch(EpochArgs a) {
-  epoch_body<BF, false, false>(a, gridDim.x, blockIdx.x);
+  epoch_body<BF, false, false, PLAIN>(a, gridDim.x, blockIdx.x);
 }
 
 // One tensor on one thread block cluster of gridDim.x <= 16 CTAs.
-template <bool BF>
+template <bool BF, bool PLAIN>
 __global__ void __launch_bounds__(kEpochThreads, 1)
 k_epoch_cl(EpochArgs a) {
-  epoch_body<BF, false, true>(a, gridDim.x, (int)cooperative_groups::this_cluster().block_rank());
+  epoch_body<BF, false, true, PLAIN>(a, gridDim.x, (int)cooperative_groups::this_cluster().block_rank());
 }
 
 // K-snapshot form (a labelled variant of Algorithm 1's minibatch order): the
@@ -1961,7 +1963,7 @@ k_epoch_cl(EpochArgs a) {
 // minibatch order, each row by the one CTA its index hashes to, so the result
 // does not depend on timing.  One chain of dependent phases per block instead
 // of per minibatch.
-template <bool BF>
+template <bool BF, bool PLAIN>
 __global__ void __launch_bounds__(kEpochThreads, 1)
 k_epoch_snap(EpochArgs a) {
   __shared__ __align__(16) EpochArgs s_a;
@@ -1978,14 +1980,14 @@ k_epoch_snap(EpochArgs a) {
     s_a.mail = a.mail + (size_t)grp * a.s.M * a.g.N * (a.g.Jmax + (a.g.Jmax & 1));
   }
   __syncthreads();
-  epoch_body<BF, true, false>(s_a, a.snap_gk, c);
+  epoch_body<BF, true, false, PLAIN>(s_a, a.snap_gk, c);
 }
 
 // Many independent tensors in one persistent launch: the grid is split into
 // groups of CTAs [m.gstart[q], m.gstart[q+1]); group q runs the epochs of the
 // tensors m.order[m.first[q] .. m.first[q+1]) one after the other, each on
 // its own arguments (copied into shared memory) and exchange buffers.
-template <bool BF, bool CL>
+template <bool BF, bool CL, bool PLAIN>
 __global__ void __launch_bounds__(kEpochThreads, 1)
 k_epoch_multi(MultiArgs m) {
   __shared__ __align__(16) EpochArgs s_a;
@@ -2000,11 +2002,24 @@ k_epoch_multi(MultiArgs m) {
 #pragma unroll 1
     for (int i = threadIdx.x; i < (int)(sizeof(EpochArgs) / 4); i += blockDim.x) dst[i] = src[i];
     __syncthreads();
-    epoch_body<BF, false, CL>(s_a, G, c);
+    epoch_body<BF, false, CL, PLAIN>(s_a, G, c);
     __syncthreads();
   }
 }
 
+#ifdef SGDT_EPOCH_PLAIN_TU
+// This translation unit: the kernels specialised for the default options.
+const void* epoch_plain_kernel(int kind, int precision) {
+  const bool bf = precision == 1;
+  switch (kind) {
+    case 0: return bf ? (const void*)k_epoch<true, true> : (const void*)k_epoch<false, true>;
+    case 1: return bf ? (const void*)k_epoch_cl<true, true> : (const void*)k_epoch_cl<false, true>;
+    case 2: return bf ? (const void*)k_epoch_snap<true, true> : (const void*)k_epoch_snap<false, true>;
+    case 3: return bf ? (const void*)k_epoch_multi<true, false, true> : (const void*)k_epoch_multi<false, false, true>;
+    default: return bf ? (const void*)k_epoch_multi<true, true, true> : (const void*)k_epoch_multi<false, true, true>;
+  }
+}
+#else
 // One thread waits, through the epoch kernel's bounded wait, for a tag that
 // nothing writes: the watchdog must expire and record STD_ETIMEOUT in *err.
 __global__ void k_wait_probe(EpochArgs a, const unsigned long long* word) {
@@ -2015,23 +2030,41 @@ __global__ void k_wait_probe(EpochArgs a, const unsigned long long* word) {
   (void)wait_all<1>(p, w, tg, a);
 }
 
+bool epoch_args_plain(const EpochArgs& a) {
+  return a.momentum == 0.f && a.norm_mode == 0 && (a.probe_batch < a.b0 || a.probe_batch >= a.b1);
+}
+
 namespace {
 
-const void* kernel_for(int precision) {
-  return precision == 1 ? (const void*)k_epoch<true> : (const void*)k_epoch<false>;
+// The kernel of each form: the general one (every option) or the one
+// specialised for the default options (compiled in its own translation unit).
+const void* kernel_for(int precision, bool plain = false) {
+  if (plain) return epoch_plain_kernel(0, precision);
+  return precision == 1 ? (const void*)k_epoch<true, false> : (const void*)k_epoch<false, false>;
 }
 
-const void* multi_kernel_for(int precision, bool cl = false) {
-  if (cl) return precision == 1 ? (const void*)k_epoch_multi<true, true> : (const void*)k_epoch_multi<false, true>;
-  return precision == 1 ? (const void*)k_epoch_multi<true, false> : (const void*)k_epoch_multi<false, false>;
+const void* multi_kernel_for(int precision, bool cl = false, bool plain = false) {
+  if (plain) return epoch_plain_kernel(cl ? 4 : 3, precision);
+  if (cl)
+    return precision == 1 ? (const void*)k_epoch_multi<true, true, false> : (const void*)k_epoch_multi<false, true, false>;
+  return precision == 1 ? (const void*)k_epoch_multi<true, false, false> : (const void*)k_epoch_multi<false, false, false>;
 }
 
-const void* cl_kernel_for(int precision) {
-  return precision == 1 ? (const void*)k_epoch_cl<true> : (const void*)k_epoch_cl<false>;
+const void* cl_kernel_for(int precision, bool plain = false) {
+  if (plain) return epoch_plain_kernel(1, precision);
+  return precision == 1 ? (const void*)k_epoch_cl<true, false> : (const void*)k_epoch_cl<false, false>;
 }
 
-const void* snap_kernel_for(int precision) {
-  return precision == 1 ? (const void*)k_epoch_snap<true> : (const void*)k_epoch_snap<false>;
+const void* snap_kernel_for(int precision, bool plain = false) {
+  if (plain) return epoch_plain_kernel(2, precision);
+  return precision == 1 ? (const void*)k_epoch_snap<true, false> : (const void*)k_epoch_snap<false, false>;
+}
+
+// Blocks of one kernel resident per SM at this shared memory.
+int blocks_per_sm(const void* fn, size_t smem) {
+  int per = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fn, kEpochThreads, smem) != cudaSuccess) return 0;
+  return per;
 }
 
 }  // namespace
@@ -2051,42 +2084,52 @@ size_t epoch_smem_bytes(const Geometry& g, int chunk_max, int ctas, int precisio
   return (size_t)smem_layout(g, chunk_max, ctas, precision).total_words * sizeof(float);
 }
 
+// Attributes and occupancy cover both kernels of a form (general and
+// specialised), so either can be launched on the same layout.
 cudaError_t epoch_kernel_setup(int precision, size_t smem) {
-  return cudaFuncSetAttribute(kernel_for(precision), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = cudaFuncSetAttribute(kernel_for(precision), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(kernel_for(precision, true), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  return e;
 }
 
 int epoch_max_ctas(int precision, size_t smem) {
-  const void* fn = kernel_for(precision);
-  int dev = 0, sms = 0, per = 0;
+  int dev = 0, sms = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return 0;
   if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fn, kEpochThreads, smem) != cudaSuccess) return 0;
-  return per * sms;
+  const int p0 = blocks_per_sm(kernel_for(precision), smem), p1 = blocks_per_sm(kernel_for(precision, true), smem);
+  return (p0 < p1 ? p0 : p1) * sms;
 }
 
 cudaError_t launch_epoch(const EpochArgs& a, int ctas, size_t smem, cudaStream_t st) {
   EpochArgs copy = a;
   void* args[] = {&copy};
-  return cudaLaunchCooperativeKernel(kernel_for(a.precision), dim3(ctas), dim3(kEpochThreads), args, smem, st);
+  return cudaLaunchCooperativeKernel(kernel_for(a.precision, epoch_args_plain(a)), dim3(ctas), dim3(kEpochThreads),
+                                     args, smem, st);
 }
 
 cudaError_t epoch_snap_setup(int precision, size_t smem) {
-  return cudaFuncSetAttribute(snap_kernel_for(precision), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e =
+      cudaFuncSetAttribute(snap_kernel_for(precision), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(snap_kernel_for(precision, true), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  return e;
 }
 
 int epoch_snap_max_ctas(int precision, size_t smem) {
-  const void* fn = snap_kernel_for(precision);
-  int dev = 0, sms = 0, per = 0;
+  int dev = 0, sms = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return 0;
   if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fn, kEpochThreads, smem) != cudaSuccess) return 0;
-  return per * sms;
+  const int p0 = blocks_per_sm(snap_kernel_for(precision), smem);
+  const int p1 = blocks_per_sm(snap_kernel_for(precision, true), smem);
+  return (p0 < p1 ? p0 : p1) * sms;
 }
 
 cudaError_t launch_epoch_snap(const EpochArgs& a, int ctas, size_t smem, cudaStream_t st) {
   EpochArgs copy = a;
   void* args[] = {&copy};
-  return cudaLaunchCooperativeKernel(snap_kernel_for(a.precision), dim3(ctas), dim3(kEpochThreads), args, smem, st);
+  return cudaLaunchCooperativeKernel(snap_kernel_for(a.precision, epoch_args_plain(a)), dim3(ctas),
+                                     dim3(kEpochThreads), args, smem, st);
 }
 
 cudaError_t launch_wait_probe(unsigned long long watchdog_ns, int* err, const unsigned long long* word,
@@ -2099,16 +2142,21 @@ cudaError_t launch_wait_probe(unsigned long long watchdog_ns, int* err, const un
 }
 
 cudaError_t epoch_multi_setup(int precision, size_t smem) {
-  return cudaFuncSetAttribute(multi_kernel_for(precision), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e =
+      cudaFuncSetAttribute(multi_kernel_for(precision), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(multi_kernel_for(precision, false, true), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem);
+  return e;
 }
 
 int epoch_multi_max_ctas(int precision, size_t smem) {
-  const void* fn = multi_kernel_for(precision);
-  int dev = 0, sms = 0, per = 0;
+  int dev = 0, sms = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return 0;
   if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fn, kEpochThreads, smem) != cudaSuccess) return 0;
-  return per * sms;
+  const int p0 = blocks_per_sm(multi_kernel_for(precision), smem);
+  const int p1 = blocks_per_sm(multi_kernel_for(precision, false, true), smem);
+  return (p0 < p1 ? p0 : p1) * sms;
 }
 
 // Cooperative launch through the launch-attribute form, which stream capture
@@ -2124,8 +2172,9 @@ cudaError_t launch_epoch_multi(const MultiArgs& m, int precision, int ctas, size
   attr[0].val.cooperative = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  if (precision == 1) return cudaLaunchKernelEx(&cfg, k_epoch_multi<true, false>, m);
-  return cudaLaunchKernelEx(&cfg, k_epoch_multi<false, false>, m);
+  MultiArgs copy = m;
+  void* args[] = {&copy};
+  return cudaLaunchKernelExC(&cfg, multi_kernel_for(precision, false, m.plain != 0), args);
 }
 
 // ---------------------------------------------------------------------------
@@ -2162,39 +2211,49 @@ size_t epoch_smem_bytes_cl(const Geometry& g, int chunk_max, int ctas, int preci
   return (size_t)smem_layout(g, chunk_max, ctas, precision, 1).total_words * sizeof(float);
 }
 
-// Clusters of csize CTAs that can be resident at once (0: none).
+// Clusters of csize CTAs that can be resident at once (0: none), for both
+// kernels of the form.
 int epoch_cl_max_clusters(int precision, bool multi, size_t smem, int csize) {
-  const void* fn = multi ? multi_kernel_for(precision, true) : cl_kernel_for(precision);
-  if (cl_attrs(fn, smem, csize) != cudaSuccess) return 0;
-  cudaLaunchAttribute attr[1];
-  cudaLaunchConfig_t cfg = cl_config(csize, csize, smem, nullptr, attr);
-  int n = 0;
-  if (cudaOccupancyMaxActiveClusters(&n, fn, &cfg) != cudaSuccess) {
-    cudaGetLastError();
-    return 0;
+  int best = -1;
+  for (int plain = 0; plain < 2; ++plain) {
+    const void* fn = multi ? multi_kernel_for(precision, true, plain != 0) : cl_kernel_for(precision, plain != 0);
+    if (cl_attrs(fn, smem, csize) != cudaSuccess) return 0;
+    cudaLaunchAttribute attr[1];
+    cudaLaunchConfig_t cfg = cl_config(csize, csize, smem, nullptr, attr);
+    int n = 0;
+    if (cudaOccupancyMaxActiveClusters(&n, fn, &cfg) != cudaSuccess) {
+      cudaGetLastError();
+      return 0;
+    }
+    best = best < 0 || n < best ? n : best;
   }
-  return n;
+  return best;
 }
 
 cudaError_t launch_epoch_cl(const EpochArgs& a, int ctas, size_t smem, cudaStream_t st) {
-  cudaError_t e = cl_attrs(cl_kernel_for(a.precision), smem, ctas);
+  const void* fn = cl_kernel_for(a.precision, epoch_args_plain(a));
+  cudaError_t e = cl_attrs(fn, smem, ctas);
   if (e != cudaSuccess) return e;
   cudaLaunchAttribute attr[1];
   cudaLaunchConfig_t cfg = cl_config(ctas, ctas, smem, st, attr);
-  if (a.precision == 1) return cudaLaunchKernelEx(&cfg, k_epoch_cl<true>, a);
-  return cudaLaunchKernelEx(&cfg, k_epoch_cl<false>, a);
+  EpochArgs copy = a;
+  void* args[] = {&copy};
+  return cudaLaunchKernelExC(&cfg, fn, args);
 }
 
 // Groups of csize CTAs, each one cluster; gstart[q] = q * csize.  Not
 // cooperative: clusters are independent, and a cluster's CTAs are resident
 // together by construction.
 cudaError_t launch_epoch_multi_cl(const MultiArgs& m, int precision, int csize, size_t smem, cudaStream_t st) {
-  cudaError_t e = cl_attrs(multi_kernel_for(precision, true), smem, csize);
+  const void* fn = multi_kernel_for(precision, true, m.plain != 0);
+  cudaError_t e = cl_attrs(fn, smem, csize);
   if (e != cudaSuccess) return e;
   cudaLaunchAttribute attr[1];
   cudaLaunchConfig_t cfg = cl_config(m.groups * csize, csize, smem, st, attr);
-  if (precision == 1) return cudaLaunchKernelEx(&cfg, k_epoch_multi<true, true>, m);
-  return cudaLaunchKernelEx(&cfg, k_epoch_multi<false, true>, m);
+  MultiArgs copy = m;
+  void* args[] = {&copy};
+  return cudaLaunchKernelExC(&cfg, fn, args);
 }
+#endif  // SGDT_EPOCH_PLAIN_TU
 
 }  // namespace sgdt

@@ -173,6 +173,7 @@ struct MultiArgs {
   const int* first;    // group q runs order[first[q] .. first[q+1])
   const int* gstart;   // group q owns CTAs [gstart[q], gstart[q+1])
   int groups;
+  int plain;           // every tensor runs with the default options (see epoch_args_plain)
 };
 
 // Factor-matrix pointers passed to kernels by value.
@@ -194,6 +195,12 @@ struct PredictItem {
 };
 
 // Launchers (host side, defined in the .cu files).
+// The default options (no momentum, no probe minibatch in [b0, b1), the 1/M
+// normaliser): the launchers then use the update kernels specialised for them.
+bool epoch_args_plain(const EpochArgs& a);
+// Those kernels (compiled in their own translation unit): kind 0 k_epoch,
+// 1 k_epoch_cl, 2 k_epoch_snap, 3 k_epoch_multi, 4 its cluster form.
+const void* epoch_plain_kernel(int kind, int precision);
 cudaError_t launch_schedule(const Geometry& g, const uint32_t* coo, int cs, const Feistel& f,
                             const Schedule& s, int64_t b0, int64_t b1, cudaStream_t st);
 int epoch_payload_floats(const Geometry& g);   // largest core-phase Gram payload over the modes

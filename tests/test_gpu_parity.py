@@ -593,6 +593,26 @@ def test_params_after_8_minibatches_bench_shape(B, synth):
         assert np.array_equal(Ag[n][~touched], A0[n][~touched])
 
 
+@pytest.mark.parametrize("precision,M", [(0, 4096), (1, 4096), (0, 256)])
+def test_default_option_kernels_equal_general_kernels(B, synth, precision, M):
+    """With the default options the launchers run update kernels compiled
+    without the momentum, probe and row-count-normaliser branches; a probe on
+    the first minibatch makes the same launch take the general kernel.  Both
+    must leave the same bits (152 CTAs at M = 4096; a 16-CTA cluster at 256)."""
+    w = synth.config2(scale=0.004)
+    t = w.tensor
+    c, v = t.split("train")
+    A0, B0 = synth.init_params(t.shape, w.ranks, w.r_core, mode="rating", seed=1, mean_value=float(np.mean(v)))
+    out = []
+    for probe in (False, True):
+        with _gpu(B, t.shape, w.ranks, w.r_core, c, v, A0, B0, precision=precision) as g:
+            g.batches(0.05, 0.05, 1e-3, 1e-3, M, 0, 6, probe=probe)
+            Ag, Bg, core, _ = g.get_params()
+            out.append(list(Ag) + list(Bg) + [core])
+    for x, y in zip(out[0], out[1]):
+        assert np.array_equal(x, y)
+
+
 # ---------------------------------------------------------------------------
 # The library's declared limits: order STD_MAX_ORDER = 6, rank and R_core
 # STD_MAX_RANK = 32, core size STD_MAX_CORE = 16,384 entries.
