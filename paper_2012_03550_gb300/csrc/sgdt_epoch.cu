@@ -885,16 +885,32 @@ __device__ __forceinline__ void epoch_body(const EpochArgs& a, const int G, cons
     }
     __syncthreads();
     const int total = s_soff[kq];
-    // staging area: the buffers of one minibatch's phases (rows .. q), free here
-    const int cap = (L.head - L.rows) / (3 + Jmax);
-    if (total <= cap) {
-      // every list entry and its row change, all minibatches' loads at once;
-      // then the rows minibatch after minibatch (a row's changes from
-      // different minibatches are added in order; within one minibatch the
-      // entries are distinct rows), two elements per thread in flight
-      int2* se = reinterpret_cast<int2*>(sm + L.rows);
-      int* sk = reinterpret_cast<int*>(se + cap);
-      float* sd = reinterpret_cast<float*>(sk + cap);
+    // staging area: the buffers of one minibatch's phases (rows .. q), free
+    // here: a hash table of the rows (open addressing, H >= 2 total slots),
+    // then per entry its list entry, minibatch, previous entry of the same
+    // row, "last of its row" flag, row change and row value
+    int H = 64;
+    while (H < 2 * total) H <<= 1;
+    const int span = L.head - L.rows;
+    if ((long long)3 * H + (long long)total * (5 + 2 * Jmax) <= span) {
+      // Every list entry and its row change, and the row as A holds it, all
+      // loads in flight at once.  Then, minibatch after minibatch in shared
+      // memory, each entry finds the previous entry of its row (hash table)
+      // and takes that entry's value, or A's, plus its change: a row touched
+      // by several minibatches gets its changes in minibatch order (within
+      // one minibatch the entries are distinct rows).  Finally the last
+      // value of every row goes to A.
+      unsigned long long* hkey = reinterpret_cast<unsigned long long*>(sm + L.rows);
+      int* hidx = reinterpret_cast<int*>(hkey + H);
+      int2* se = reinterpret_cast<int2*>(hidx + H);
+      int* sk = reinterpret_cast<int*>(se + total);
+      int* prv = sk + total;
+      int* lastf = prv + total;
+      float* sd = reinterpret_cast<float*>(lastf + total);   // [total][Jmax] change, then value
+      float* sa = sd + (size_t)total * Jmax;                  // [total][Jmax] the row in A
+      const int hbits = 31 - __clz(H);
+#pragma unroll 1
+      for (int i = tid; i < H; i += T) hkey[i] = ~0ULL;
 #pragma unroll 1
       for (int t = tid; t < total; t += T) {
         int lo = 0, hi = kq - 1;   // the list holding entry t
@@ -908,51 +924,78 @@ __device__ __forceinline__ void epoch_body(const EpochArgs& a, const int G, cons
       }
       __syncthreads();
 #pragma unroll 1
-      for (int i = tid; i < total * Jmax; i += T) {
-        const int t = fdiv(i, f_Jmax), jj = i - t * Jmax;
-        const int2 en = se[t];
-        const int nn = en.y >> 16;
-        if (jj < mJ[nn]) sd[i] = __ldcg(a.snap_drow + (((size_t)sk[t] * N + nn) * M + (en.y & 0xffff)) * Jmax + jj);
+      for (int i0 = tid; i0 < total * Jmax; i0 += 2 * T) {
+        float dv[2], av[2];
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+          const int i = i0 + u * T;
+          dv[u] = 0.f;
+          av[u] = 0.f;
+          if (i < total * Jmax) {
+            const int t = fdiv(i, f_Jmax), jj = i - t * Jmax;
+            const int2 en = se[t];
+            const int nn = en.y >> 16;
+            if (jj < mJ[nn]) {
+              dv[u] = __ldcg(a.snap_drow + (((size_t)sk[t] * N + nn) * M + (en.y & 0xffff)) * Jmax + jj);
+              av[u] = __ldcg(mA[nn] + (unsigned)en.x * (unsigned)mJp[nn] + jj);
+            }
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < 2; ++u)
+          if (i0 + u * T < total * Jmax) {
+            sd[i0 + u * T] = dv[u];
+            sa[i0 + u * T] = av[u];
+          }
       }
       __syncthreads();
 #pragma unroll 1
       for (int k = 0; k < kq; ++k) {
-        const int i1 = s_soff[k + 1] * Jmax;
+        const int t0 = s_soff[k], t1 = s_soff[k + 1];
 #pragma unroll 1
-        for (int i0 = s_soff[k] * Jmax + tid; i0 < i1; i0 += 2 * T) {
-          float av[2];
-          float* ap[2];
-          int nn[2], jv[2];
-          unsigned rw[2];
-          bool live[2];
-#pragma unroll
-          for (int u = 0; u < 2; ++u) {
-            const int i = i0 + u * T;
-            live[u] = false;
-            if (i < i1) {
-              const int t = fdiv(i, f_Jmax);
-              const int2 en = se[t];
-              jv[u] = i - t * Jmax;
-              nn[u] = en.y >> 16;
-              rw[u] = (unsigned)en.x;
-              live[u] = jv[u] < mJ[nn[u]];
-              if (live[u]) {
-                ap[u] = mA[nn[u]] + rw[u] * (unsigned)mJp[nn[u]] + jv[u];
-                av[u] = __ldcg(ap[u]);
-              }
+        for (int t = t0 + tid; t < t1; t += T) {
+          const int2 en = se[t];
+          const unsigned long long key = ((unsigned long long)(en.y >> 16) << 32) | (unsigned)en.x;
+          int h = (int)((key * 0x9E3779B97F4A7C15ULL) >> (64 - hbits));
+          int p = -1;
+#pragma unroll 1
+          for (int tries = 0; tries < H; ++tries) {
+            const unsigned long long old = atomicCAS(hkey + h, ~0ULL, key);
+            if (old == ~0ULL) break;   // new row
+            if (old == key) {          // seen in an earlier minibatch
+              p = hidx[h];
+              break;
             }
+            h = (h + 1) & (H - 1);
           }
-#pragma unroll
-          for (int u = 0; u < 2; ++u)
-            if (live[u]) {
-              const float nv = __fadd_rn(av[u], sd[i0 + u * T]);
-              __stcg(ap[u], nv);
-              if (BF)
-                __stcg(mAb[nn[u]] + rw[u] * (unsigned)mJb[nn[u]] + jv[u], __bfloat16_as_ushort(__float2bfloat16_rn(nv)));
-            }
+          hidx[h] = t;
+          prv[t] = p;
+          lastf[t] = 1;
+          if (p >= 0) lastf[p] = 0;
+        }
+        __syncthreads();
+#pragma unroll 1
+        for (int i = t0 * Jmax + tid; i < t1 * Jmax; i += T) {
+          const int t = fdiv(i, f_Jmax), jj = i - t * Jmax;
+          const int p = prv[t];
+          const float base = p >= 0 ? sd[p * Jmax + jj] : sa[i];
+          sd[i] = __fadd_rn(base, sd[i]);
         }
         __syncthreads();
       }
+#pragma unroll 1
+      for (int i = tid; i < total * Jmax; i += T) {
+        const int t = fdiv(i, f_Jmax), jj = i - t * Jmax;
+        const int2 en = se[t];
+        const int nn = en.y >> 16;
+        if (lastf[t] && jj < mJ[nn]) {
+          const float nv = sd[i];
+          __stcg(mA[nn] + (unsigned)en.x * (unsigned)mJp[nn] + jj, nv);
+          if (BF)
+            __stcg(mAb[nn] + (unsigned)en.x * (unsigned)mJb[nn] + jj, __bfloat16_as_ushort(__float2bfloat16_rn(nv)));
+        }
+      }
+      __syncthreads();
     } else {
       // lists larger than the staging area: list after list.  A warp takes
       // 32 / Jmax entries per pass, lane group g entry g, lane j column j,
