@@ -98,6 +98,12 @@ typedef struct {
                              minibatch order.  K groups of CTAs run a block's minibatches at once.
                              Limits: K <= 64, K * ceil(M / 256) CTAs resident, momentum 0
                              (STD_EINVAL otherwise); batched launches refuse such contexts */
+    int32_t  tile;        /* register tile of the FP32 factor-phase contraction E_s = G-hat_(n) S_s^T
+                             (Eqs. 10-11): samples per thread sharing each unfolded-core load,
+                             1, 2 or 4; 0 = chosen from the chunk size (default).  Every sample's
+                             sums are formed in the same order whatever the tile, so results are
+                             the same bits.  Batched launches run every tensor with the batch's
+                             tile instead (std_batch_tile).  Other values: STD_EINVAL */
 } std_options;
 
 /* Fill *opt with the defaults listed above. */
@@ -300,6 +306,14 @@ int std_batch_set_groups(std_batch* batch, const int32_t* ctas_per_tensor);
  * the order of std_batch_create; 0 before the first launch).  A tensor's
  * result equals std_sgd_epoch's with that many CTAs. */
 int std_batch_groups(const std_batch* batch, int32_t* ctas_per_tensor);
+
+/* The FP32 contraction tile the batch runs with (std_options.tile: 0 = from
+ * each tensor's chunk size, else 1, 2 or 4 for every tensor).  With
+ * ctas_per_tensor = 0 the tuner picks it on the first step, after the group
+ * size, by timing each choice on the same dry run; results are the same bits
+ * whatever the tile.  Until then, and with fixed group sizes, it is 0.
+ * Errors: STD_EINVAL (NULL arguments). */
+int std_batch_tile(const std_batch* batch, int32_t* tile);
 
 /* std_batch_step without a limit: every tensor finishes its current epoch. */
 int std_batch_epoch(std_batch* batch, float lr_a, float lr_b, float lambda_a, float lambda_b,

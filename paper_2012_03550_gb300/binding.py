@@ -56,6 +56,7 @@ class std_options(ctypes.Structure):
         ("contraction", ctypes.c_int32),
         ("momentum", ctypes.c_float),
         ("snapshot", ctypes.c_int32),
+        ("tile", ctypes.c_int32),
     ]
 
 
@@ -123,6 +124,7 @@ SIGNATURES = {
     "std_device_bytes": (ctypes.c_int, [_P, _P]),
     "std_watchdog_probe": (ctypes.c_int, [ctypes.c_uint64, _P]),
     "std_batch_groups": (ctypes.c_int, [_P, _P]),
+    "std_batch_tile": (ctypes.c_int, [_P, _P]),
     "std_batch_set_groups": (ctypes.c_int, [_P, _P]),
     "std_predict_many": (ctypes.c_int, [ctypes.c_int32, _P, _P, _P, _P]),
     "std_batch_reset": (ctypes.c_int, [_P, ctypes.c_int32, _P]),
@@ -449,6 +451,12 @@ def std_batch_groups(batch, count):
     return [int(x) for x in out]
 
 
+def std_batch_tile(batch):
+    out = ctypes.c_int32()
+    _check(lib().std_batch_tile(batch, ctypes.byref(out)))
+    return int(out.value)
+
+
 def std_predict_many(ctxs, coords_list, outs):
     n = len(ctxs)
     carr = (ctypes.c_void_p * n)(*[c.value if isinstance(c, ctypes.c_void_p) else c for c in ctxs])
@@ -502,6 +510,9 @@ class Batch:
 
     def groups(self):
         return std_batch_groups(self.ptr, len(self.members))
+
+    def tile(self):
+        return std_batch_tile(self.ptr)
 
     def set_groups(self, sizes):
         std_batch_set_groups(self.ptr, sizes)

@@ -340,6 +340,7 @@ EpochArgs epoch_args(std_ctx* c, float lr_a, float lr_b, float lam_a, float lam_
   a.lam_b = lam_b;
   a.norm_mode = c->opt.norm_mode;
   a.contraction = c->opt.contraction;
+  a.tile_sg = c->opt.tile;
   a.momentum = c->opt.momentum;
   a.vB = c->vB;
   a.chunk_max = chunk;
@@ -581,6 +582,8 @@ int std_create(std_ctx** out, int32_t order, const int64_t* mode_sizes, const in
   if (opt.ctas < 0) return set_error(STD_EINVAL, "ctas must be >= 0");
   if (opt.contraction != 0 && opt.contraction != 1) return set_error(STD_EINVAL, "contraction must be 0 or 1");
   if (!(opt.momentum >= 0.f && opt.momentum < 1.f)) return set_error(STD_EINVAL, "momentum must be in [0, 1)");
+  if (opt.tile != 0 && opt.tile != 1 && opt.tile != 2 && opt.tile != 4)
+    return set_error(STD_EINVAL, "tile must be 0, 1, 2 or 4");
   if (opt.snapshot < 0) return set_error(STD_EINVAL, "snapshot must be >= 0");
   if (opt.snapshot > 64) return set_error(STD_EUNSUPPORTED, "snapshot exceeds 64 minibatches per block");
   if (opt.snapshot >= 2 && opt.momentum != 0.f)
@@ -995,6 +998,7 @@ struct std_batch {
   cudaStream_t stream = nullptr;
   int precision = 0;
   int group = 0;          // CTAs per tensor (the base size); 0 until tuned
+  int tile = 0;           // FP32 contraction tile of every tensor (0 = from its chunk size)
   bool tuned = false;
   bool promote = false;   // long tensors may get groups of 2^k x group CTAs
   std::vector<int> fixed_g; // per-tensor group sizes set by the caller (empty: none)
@@ -1282,6 +1286,7 @@ int batch_launch(std_batch* bt, float lr_a, float lr_b, float lam_a, float lam_b
     if (rc) return rc;
     EpochArgs a = epoch_args(c, lr_a, lr_b, lam_a, lam_b, e0v[t], e1v[t], (M + gt[t] - 1) / gt[t], tag_base);
     a.err = bt->err;
+    a.tile_sg = bt->tile;
     a.dry = dry ? 1 : 0;
     if (dry) a.momentum = 0.f;
     bt->h_items[t] = a;
@@ -1545,6 +1550,24 @@ int std_batch_step(std_batch* bt, float lr_a, float lr_b, float lambda_a, float 
     }
     if (best_g == 0) return set_error(STD_EUNSUPPORTED, "no group size fits every tensor of the batch");
     bt->group = best_g;
+    // then the FP32 contraction tile on the same trial (same bits whatever
+    // the tile; the per-chunk choice, 0, stays unless a fixed tile is faster)
+    if (bt->precision == 0) {
+      float best_t = -1.f;
+      int best_tile = 0;
+      for (int tile : {0, 1, 2, 4}) {
+        bt->tile = tile;
+        rc = batch_launch(bt, lr_a, lr_b, lambda_a, lambda_b, minibatch, trial, best_g, true, bt->promote);
+        if (rc) return rc;
+        float ms = 0.f;
+        STD_CUDA(cudaEventElapsedTime(&ms, bt->evm, bt->ev1), "event time");
+        if (best_t < 0.f || ms < best_t * 0.99f) {
+          best_t = ms;
+          best_tile = tile;
+        }
+      }
+      bt->tile = best_tile;
+    }
     bt->tuned = true;
   }
   STD_CUDA(cudaEventRecord(bt->ev0, bt->stream), "event");
@@ -1621,6 +1644,12 @@ int std_batch_set_groups(std_batch* bt, const int32_t* ctas_per_tensor) {
   bt->group = mn;
   bt->tuned = true;
   bt->promote = false;
+  return STD_OK;
+}
+
+int std_batch_tile(const std_batch* bt, int32_t* tile) {
+  if (!bt || !tile) return set_error(STD_EINVAL, "batch or output is NULL");
+  *tile = bt->tile;
   return STD_OK;
 }
 

@@ -1854,10 +1854,13 @@ __device__ __forceinline__ void epoch_body(const EpochArgs& a, const int G, cons
             // four samples per thread when that still fills half the block,
             // else two when that fills a quarter (each sample's sums are
             // formed in the same order whatever the grouping)
+            // (or the tile the caller or the batched tuner set)
             const int JL = pow2_at_least(Jn);
-            if (((pc + 3) >> 2) * JL >= (T >> 1))
+            const int sg = a.tile_sg > 0 ? a.tile_sg
+                                         : (((pc + 3) >> 2) * JL >= (T >> 1) ? 4 : (((pc + 1) >> 1) * JL >= (T >> 2) ? 2 : 1));
+            if (sg == 4)
               contract_fp32<4>(pc, Jn, Pn, Pp, full_s, GT, Sbuf, prow, sumJ, mJoff[n], cdn, nm1, pfx, pq, Jmax, tid, T);
-            else if (((pc + 1) >> 1) * JL >= (T >> 2))
+            else if (sg == 2)
               contract_fp32<2>(pc, Jn, Pn, Pp, full_s, GT, Sbuf, prow, sumJ, mJoff[n], cdn, nm1, pfx, pq, Jmax, tid, T);
             else
               contract_fp32<1>(pc, Jn, Pn, Pp, full_s, GT, Sbuf, prow, sumJ, mJoff[n], cdn, nm1, pfx, pq, Jmax, tid, T);

@@ -133,6 +133,7 @@ struct EpochArgs {
   float lr_a, lr_b, lam_a, lam_b;
   int norm_mode;
   int contraction;       // 0 Kronecker rows x unfolded core; 1 Kruskal form E = B(n) w
+  int tile_sg;          // FP32 contraction: samples per thread (1, 2, 4); 0 = from the chunk size
   float momentum;        // heavy-ball mu (0 = plain SGD)
   int dry;               // 1: compute everything, write no parameter (timing runs)
   float* vA[kMaxN];      // factor-row velocities, I_n x Jp_n (momentum != 0)

@@ -104,7 +104,7 @@ def test_create_rejects_bad_options_and_nnz(lib):
     val = np.zeros(1, np.float32)
     for field, value in [("precision", 2), ("norm_mode", 3), ("ptr_kind", 5), ("ctas", -1), ("init_mode", 9),
                          ("contraction", 2), ("momentum", 1.0), ("momentum", -0.1), ("momentum", float("nan")),
-                         ("snapshot", -1)]:
+                         ("snapshot", -1), ("tile", 3), ("tile", -1), ("tile", 8)]:
         o = lib.std_default_options()
         setattr(o, field, value)
         with pytest.raises(lib.StdError) as ei:
@@ -145,6 +145,8 @@ def test_null_context_is_rejected(lib):
         lib.std_batch_set_groups(None, [4])
     with pytest.raises(lib.StdError):
         lib.std_batch_groups(None, 1)
+    with pytest.raises(lib.StdError):
+        lib.std_batch_tile(None)
     with pytest.raises(lib.StdError):
         lib.std_predict_many([None], [np.zeros((1, 3), np.int32)], [np.zeros(1, np.float32)])
     lib.std_destroy(None)

@@ -86,6 +86,8 @@ def test_batch_tuner_writes_nothing_and_matches_alone(B, synth):
         st = bt.epoch(lr, lr, lam, lam, M)
         group = st["ctas_per_tensor"]
         sizes = bt.groups()
+        tile = bt.tile()
+    assert tile in (0, 1, 2, 4)   # the contraction tile the tuner kept (same bits whatever it is)
     assert group >= 1 and len(sizes) == len(SPECS)
     assert all(g >= group and g % group == 0 for g in sizes)
     for k, (a, g) in enumerate(zip(batched, sizes)):

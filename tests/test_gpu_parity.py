@@ -613,6 +613,27 @@ def test_default_option_kernels_equal_general_kernels(B, synth, precision, M):
         assert np.array_equal(x, y)
 
 
+@pytest.mark.parametrize("tile", [1, 2, 4])
+def test_contraction_tile_gives_the_same_bits(B, synth, tile):
+    """std_options.tile forces the FP32 contraction's samples per thread; each
+    sample's sums keep one order whatever the tile, so six minibatches of
+    4096 on 152 CTAs (27-sample chunks, where the library picks 2) and of 256
+    on 16 CTAs leave the same bits as the library's own choice."""
+    w = synth.config2(scale=0.004)
+    t = w.tensor
+    c, v = t.split("train")
+    A0, B0 = synth.init_params(t.shape, w.ranks, w.r_core, mode="rating", seed=1, mean_value=float(np.mean(v)))
+    for M in (4096, 256):
+        out = []
+        for tl in (0, tile):
+            with _gpu(B, t.shape, w.ranks, w.r_core, c, v, A0, B0, tile=tl) as g:
+                g.batches(0.05, 0.05, 1e-3, 1e-3, M, 0, 6)
+                Ag, Bg, core, _ = g.get_params()
+                out.append(list(Ag) + list(Bg) + [core])
+        for x, y in zip(out[0], out[1]):
+            assert np.array_equal(x, y)
+
+
 # ---------------------------------------------------------------------------
 # The library's declared limits: order STD_MAX_ORDER = 6, rank and R_core
 # STD_MAX_RANK = 32, core size STD_MAX_CORE = 16,384 entries.
