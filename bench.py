@@ -816,6 +816,7 @@ def batched_record(a, nnz_scale, warmup, steps):
             st = B.std_batch_epoch(bt, lr, lr, lam, lam, M)
             secs.append(st["seconds"])
         sizes = B.std_batch_groups(bt, len(ctxs))
+        tile = B.std_batch_tile(bt)
         B.std_batch_destroy(bt)
         # test RMSE over all members (weighted by test entries)
         se, cnt = 0.0, 0
@@ -845,6 +846,7 @@ def batched_record(a, nnz_scale, warmup, steps):
         for g in sizes:
             hist[str(g)] = hist.get(str(g), 0) + 1
         lines[precision] = {"value": n_train / (ms * 1e-3), "ms_per_epoch": ms, "ctas_per_tensor": st["ctas_per_tensor"],
+                            "contraction_tile": tile,
                             "tensors_by_group_size": hist, "graph_replayed": st["graph_replayed"],
                             "test_rmse": (se / cnt) ** 0.5 if cnt else None, "sequential_value": seq}
     line = {"metric": "batched SGD_Tucker: sampled nonzeros/s per epoch over all tensors", "value": lines[0]["value"],
@@ -853,6 +855,7 @@ def batched_record(a, nnz_scale, warmup, steps):
             "config": {"workload": f"batched-{len(specs)}-tensors-{n_train}", "tensors": len(specs),
                        "nnz_train": n_train, "minibatch": M, "ranks": "J in {4, 8, 16}, R = min(5, J)",
                        "ctas_per_tensor": lines[0]["ctas_per_tensor"],
+                       "contraction_tile": lines[0]["contraction_tile"],
                        "tensors_by_group_size": lines[0]["tensors_by_group_size"],
                        "graph_replayed": lines[0]["graph_replayed"], "datagen_s": round(gen_s, 1),
                        "step": "one epoch of every tensor in one persistent launch (samplers and tilers before it)"},
